@@ -1,0 +1,210 @@
+"""FP64 CPU oracle of the PALM / DALM l1 solvers (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``l1_oracle.c`` (plain C, IEEE
+double, no BLAS) through ctypes.  It shares no code with the CUDA library in
+``paper_1007_3753_gb300``; the two meet only at the seeded input generators in
+``synthetic``.
+
+Every entry point cites the passage of the paper it restates; the readings of
+ambiguous passages (R1-R11) are listed at the top of ``l1_oracle.c``.
+
+Parity pins (tests/test_oracle_pins.py) tie each function to something other
+than itself: brute-force LP vertex enumeration and HiGHS on the LP of Eq. 10,
+brute-force lasso enumeration, KKT / subgradient certificates (Eq. 11),
+exact recovery (§VI-A), closed forms, invariances, and central finite
+differences plus the adjoint identity for the unrolled gradient.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "l1_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+MODE_P1, MODE_P12, MODE_QP, MODE_CAB = 0, 1, 2, 3
+ERR_ARG, ERR_NOT_SPD, ERR_NOMEM = -1, -2, -3
+
+_lock = threading.Lock()
+_lib = None
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("inner_total", C.c_int), ("converged", C.c_int),
+                ("rel_change", C.c_double), ("param", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PalmOpts(C.Structure):
+    _fields_ = [("mode", C.c_int), ("tol", C.c_double), ("max_outer", C.c_int),
+                ("inner_max", C.c_int), ("inner_tol", C.c_double), ("xi0", C.c_double),
+                ("xi_growth", C.c_double), ("xi_max", C.c_double), ("L", C.c_double),
+                ("epsilon", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``l1_oracle.c`` into ``_build/liboracle.so`` with gcc."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib() -> C.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            dp = C.POINTER(C.c_double)
+            ip = C.POINTER(C.c_int)
+            L.orc_lipschitz.restype = C.c_double
+            L.orc_lipschitz.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, ip]
+            L.orc_fista_qp.restype = C.c_int
+            L.orc_fista_qp.argtypes = [dp, C.c_int, C.c_int, dp, C.c_double, C.c_double,
+                                       C.c_double, C.c_int, dp, C.POINTER(Stats)]
+            L.orc_palm.restype = C.c_int
+            L.orc_palm.argtypes = [dp, C.c_int, C.c_int, dp, C.POINTER(PalmOpts), dp, dp, dp,
+                                   C.POINTER(Stats)]
+            L.orc_dalm.restype = C.c_int
+            L.orc_dalm.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_double,
+                                   C.c_int, dp, dp, C.POINTER(Stats)]
+            L.orc_classify.restype = C.c_int
+            L.orc_classify.argtypes = [dp, C.c_int, C.c_int, ip, C.c_int, dp, dp, dp, dp, dp,
+                                       ip, ip]
+            L.orc_unrolled_palm.restype = C.c_int
+            L.orc_unrolled_palm.argtypes = [dp, C.c_int, C.c_int, dp, C.c_double, C.c_double,
+                                            C.c_int, C.c_int, dp, dp, dp, dp, dp]
+            _lib = L
+    return _lib
+
+
+def _f64(a, fortran: bool = False) -> np.ndarray:
+    return np.asfortranarray(a, dtype=np.float64) if fortran else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(rc: int, what: str):
+    if rc == ERR_NOT_SPD:
+        raise np.linalg.LinAlgError(f"{what}: B B^T is not positive definite")
+    if rc != 0:
+        raise RuntimeError(f"{what}: oracle error {rc}")
+
+
+def lipschitz(A, max_iter: int = 1000, rtol: float = 1e-10, safety: float = 1.01) -> float:
+    """Power-iteration bound of ||A||_2^2 (reading R4 of §IV-A / Algorithm 1)."""
+    A = _f64(A, True)
+    it = C.c_int(0)
+    return float(lib().orc_lipschitz(_p(A), A.shape[0], A.shape[1], max_iter, rtol, safety,
+                                     C.byref(it)))
+
+
+def fista_qp(A, b, lam: float, L: float | None = None, tol: float = 1e-10,
+             max_iter: int = 100000):
+    """FISTA, Eq. 18 (§IV-A), on (QP_lambda) of Eq. 3.  Returns (x, stats)."""
+    A = _f64(A, True)
+    b = _f64(b)
+    m, n = A.shape
+    if L is None:
+        L = lipschitz(A)
+    x = np.zeros(n)
+    st = Stats()
+    _check(lib().orc_fista_qp(_p(A), m, n, _p(b), lam, L, tol, max_iter, _p(x), C.byref(st)),
+           "fista_qp")
+    return x, st.as_dict()
+
+
+def palm(A, b, mode: int = MODE_CAB, tol: float = 1e-10, max_outer: int = 10000,
+         inner_max: int = 50, inner_tol: float | None = None, xi0: float = 0.0,
+         xi_growth: float = 1.2, xi_max: float = 1e4, L: float | None = None,
+         epsilon: float = 0.0):
+    """Primal ALM: Algorithm 1 (CAB), Eq. 33 + FISTA (P1), reading R10 (P1,2).
+
+    Returns (x, e, theta, stats); e is None in P1 mode."""
+    A = _f64(A, True)
+    b = _f64(b)
+    m, n = A.shape
+    if L is None:
+        L = lipschitz(A)
+    o = PalmOpts(mode=mode, tol=tol, max_outer=max_outer, inner_max=inner_max,
+                 inner_tol=(0.1 * tol if inner_tol is None else inner_tol), xi0=xi0,
+                 xi_growth=xi_growth, xi_max=xi_max, L=L, epsilon=epsilon)
+    x = np.zeros(n)
+    e = np.zeros(m) if mode != MODE_P1 else None
+    th = np.zeros(m)
+    st = Stats()
+    _check(lib().orc_palm(_p(A), m, n, _p(b), C.byref(o), _p(x), _p(e), _p(th), C.byref(st)),
+           "palm")
+    return x, e, th, st.as_dict()
+
+
+def dalm(A, b, cab: bool = True, beta: float = 0.0, tol: float = 1e-10,
+         max_iter: int = 100000):
+    """Dual ALM, Algorithm 2 (§V-B) with reading R1.
+
+    Returns (w, y, stats); w = [x; e] for CAB, w = x for P1."""
+    A = _f64(A, True)
+    b = _f64(b)
+    m, n = A.shape
+    w = np.zeros(n + m if cab else n)
+    y = np.zeros(m)
+    st = Stats()
+    _check(lib().orc_dalm(_p(A), m, n, int(bool(cab)), _p(b), beta, tol, max_iter, _p(w), _p(y),
+                          C.byref(st)), "dalm")
+    return w, y, st.as_dict()
+
+
+def classify(A, offsets, b, x, e=None):
+    """Per-class residual argmin and SCI argmax (§II-A, Eq. 40).
+
+    Returns (label, sci_label, residuals, sci)."""
+    A = _f64(A, True)
+    m, n = A.shape
+    off = np.ascontiguousarray(offsets, dtype=np.int32)
+    Cn = len(off) - 1
+    b = _f64(b)
+    x = _f64(x)
+    e = None if e is None else _f64(e)
+    resid = np.zeros(Cn)
+    sci = np.zeros(Cn)
+    lab = C.c_int(-1)
+    slab = C.c_int(-1)
+    _check(lib().orc_classify(_p(A), m, n, off.ctypes.data_as(C.POINTER(C.c_int)), Cn, _p(b),
+                              _p(x), _p(e), _p(resid), _p(sci), C.byref(lab), C.byref(slab)),
+           "classify")
+    return lab.value, slab.value, resid, sci
+
+
+def unrolled_palm(A, b, xi: float, L: float, K: int, J: int, x_target, grad: bool = True):
+    """Unrolled PALM (reading R11) for one right-hand side and its reverse sweep.
+
+    Returns (x_K, loss, grad_A, grad_b); the gradients are None if grad=False."""
+    A = _f64(A, True)
+    b = _f64(b)
+    xt = _f64(x_target)
+    m, n = A.shape
+    x = np.zeros(n)
+    loss = C.c_double(0.0)
+    gA = np.zeros((m, n), order="F") if grad else None
+    gb = np.zeros(m) if grad else None
+    _check(lib().orc_unrolled_palm(_p(A), m, n, _p(b), xi, L, K, J, _p(xt), _p(x),
+                                   C.byref(loss), _p(gA), _p(gb)), "unrolled_palm")
+    return x, loss.value, gA, gb

@@ -1,0 +1,388 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself or with a retyped formula: each
+check uses an independent route to the same answer -- vertex enumeration of
+the LP of Eq. 10 (primal and dual), the HiGHS LP solver, enumeration of lasso
+supports and signs, subgradient certificates (Eq. 11), exact recovery
+(§VI-A), closed forms, invariances, hand-computed fixtures, and finite
+differences for the unrolled gradient.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _bf_lp(B, b):
+    """min ||w||_1 s.t. B w = b by enumerating the basic solutions of
+    [B, -B] u = b, u >= 0 (footnote and LP of Eq. 10).  Returns (opt, w, unique)."""
+    m, nb = B.shape
+    BB = np.hstack([B, -B])
+    best, sols = np.inf, []
+    for cols in itertools.combinations(range(2 * nb), m):
+        M = BB[:, cols]
+        if abs(np.linalg.det(M)) < 1e-10:
+            continue
+        u = np.linalg.solve(M, b)
+        if np.min(u) < -1e-12:
+            continue
+        full = np.zeros(2 * nb)
+        full[list(cols)] = u
+        w = full[:nb] - full[nb:]
+        val = np.abs(w).sum()
+        sols.append((val, w))
+        best = min(best, val)
+    opt_ws = [w for v, w in sols if v <= best * (1 + 1e-9) + 1e-12]
+    unique = all(np.allclose(w, opt_ws[0], atol=1e-9) for w in opt_ws)
+    return best, opt_ws[0], unique
+
+
+def _bf_dual(B, b):
+    """max b^T y s.t. ||B^T y||_inf <= 1 by enumerating polytope vertices (dual of Eq. 10)."""
+    m, nb = B.shape
+    G = np.vstack([B.T, -B.T])
+    best = -np.inf
+    for rows in itertools.combinations(range(2 * nb), m):
+        M = G[list(rows)]
+        if abs(np.linalg.det(M)) < 1e-10:
+            continue
+        y = np.linalg.solve(M, np.ones(m))
+        if np.max(np.abs(B.T @ y)) > 1 + 1e-9:
+            continue
+        best = max(best, b @ y)
+    return best
+
+
+def _tiny(seed, m, n):
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((m, n))
+    A /= np.linalg.norm(A, axis=0)
+    x0 = np.zeros(n)
+    x0[g.choice(n, 1, replace=False)] = g.standard_normal(1)
+    b = A @ x0 + 0.3 * g.standard_normal(m)
+    return np.asfortranarray(A), b
+
+
+# ----------------------------------------------------------------- LP pins
+
+@pytest.mark.parametrize("seed", range(40))
+def test_p1_matches_lp_vertex_enumeration(seed):
+    A, b = _tiny(seed, 3, 6)
+    opt, w_opt, unique = _bf_lp(A, b)
+    dual = _bf_dual(A, b)
+    assert abs(dual - opt) <= 1e-9 * opt  # strong duality of Eq. 10
+    # tol = 0 runs a fixed number of steps: on these tiny, nearly degenerate
+    # instances the relative-change rule (§VI-C) can stop both methods while
+    # an iterate lingers near a non-optimal point (PALM: x stalls while theta
+    # accumulates).  A fixed xi keeps PALM's inner subproblem well
+    # conditioned (§V-A).
+    w, y, st = oracle.dalm(A, b, cab=False, tol=0.0, max_iter=20000)
+    x, _, th, st2 = oracle.palm(A, b, mode=oracle.MODE_P1, tol=0.0, max_outer=3000,
+                                xi_growth=1.0)
+    for sol in (w, x):
+        assert abs(np.abs(sol).sum() - opt) <= 1e-7 * opt
+        assert np.linalg.norm(A @ sol - b) <= 1e-7 * np.linalg.norm(b)
+        if unique:
+            assert np.linalg.norm(sol - w_opt) <= 1e-6 * np.linalg.norm(w_opt)
+    # dual certificate from DALM: feasible and optimal (Eq. 10 dual)
+    assert np.max(np.abs(A.T @ y)) <= 1 + 1e-7
+    assert abs(b @ y - opt) <= 1e-7 * opt
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_cab_matches_lp_vertex_enumeration(seed):
+    A, b = _tiny(100 + seed, 3, 3)
+    m, n = A.shape
+    B = np.hstack([A, np.eye(m)])
+    opt, w_opt, unique = _bf_lp(B, b)
+    assert abs(_bf_dual(B, b) - opt) <= 1e-9 * opt
+    w, y, st = oracle.dalm(A, b, cab=True, tol=0.0, max_iter=100000)
+    x, e, th, _ = oracle.palm(A, b, mode=oracle.MODE_CAB, tol=0.0, max_outer=4000,
+                              inner_max=50)
+    for sol in (w, np.concatenate([x, e])):
+        assert abs(np.abs(sol).sum() - opt) <= 1e-6 * opt
+        assert np.linalg.norm(B @ sol - b) <= 1e-6 * np.linalg.norm(b)
+        if unique:
+            assert np.linalg.norm(sol - w_opt) <= 1e-5 * np.linalg.norm(w_opt)
+    assert np.max(np.abs(B.T @ y)) <= 1 + 1e-7
+
+
+def test_p1_and_cab_match_highs():
+    from scipy.optimize import linprog
+    for cab, (m, n), seed in [(False, (30, 60), 7), (True, (20, 30), 8)]:
+        g = np.random.default_rng(seed)
+        A = g.standard_normal((m, n))
+        A = np.asfortranarray(A / np.linalg.norm(A, axis=0))
+        x0 = np.zeros(n)
+        x0[g.choice(n, 4, replace=False)] = g.standard_normal(4)
+        b = A @ x0 + (0.05 * g.standard_normal(m) if cab else 0)
+        B = np.hstack([A, np.eye(m)]) if cab else A
+        nb = B.shape[1]
+        res = linprog(np.ones(2 * nb), A_eq=np.hstack([B, -B]), b_eq=b, bounds=(0, None),
+                      method="highs")
+        assert res.status == 0
+        w, y, st = oracle.dalm(A, b, cab=cab, tol=1e-13, max_iter=500000)
+        assert abs(np.abs(w).sum() - res.fun) <= 1e-7 * res.fun
+        assert abs(b @ y - res.fun) <= 1e-7 * res.fun
+
+
+# ------------------------------------------------------- KKT certificates
+
+def test_dalm_kkt_certificate_p1():
+    """Eq. 11 / §III-B: B^T y in the subdifferential of ||w||_1 at w."""
+    p = synthetic.p1_instance(60, 120, 6, seed=3)
+    A, b = p["A"], p["b"]
+    w, y, st = oracle.dalm(A, b, cab=False, tol=1e-13, max_iter=100000)
+    assert st["converged"]
+    s = A.T @ y
+    supp = np.abs(w) > 1e-8
+    assert np.linalg.norm(b - A @ w) <= 1e-9 * np.linalg.norm(b)
+    assert np.max(np.abs(s)) <= 1 + 1e-9
+    assert np.max(np.abs(s[supp] - np.sign(w[supp]))) <= 1e-8
+    gap = np.abs(w).sum() - b @ (y / max(1.0, np.max(np.abs(s))))
+    assert -1e-9 <= gap <= 1e-9 * np.abs(w).sum()
+
+
+def test_fista_qp_matches_lasso_enumeration_and_kkt():
+    g = np.random.default_rng(11)
+    for trial in range(15):
+        m, n = 4, 6
+        A = g.standard_normal((m, n))
+        A = np.asfortranarray(A / np.linalg.norm(A, axis=0))
+        b = g.standard_normal(m)
+        lam = 0.2 * np.max(np.abs(A.T @ b))
+        best, xbest = np.inf, None
+        for k in range(0, m + 1):
+            for S in itertools.combinations(range(n), k):
+                S = list(S)
+                for sgn in itertools.product([-1.0, 1.0], repeat=k):
+                    x = np.zeros(n)
+                    if k:
+                        AS = A[:, S]
+                        xs = np.linalg.solve(AS.T @ AS, AS.T @ b - lam * np.array(sgn))
+                        if np.any(np.sign(xs) != np.array(sgn)):
+                            continue
+                        x[S] = xs
+                    F = 0.5 * np.sum((b - A @ x) ** 2) + lam * np.abs(x).sum()
+                    if F < best:
+                        best, xbest = F, x
+        x, st = oracle.fista_qp(A, b, lam, tol=1e-14, max_iter=200000)
+        F = 0.5 * np.sum((b - A @ x) ** 2) + lam * np.abs(x).sum()
+        assert F <= best * (1 + 1e-10) + 1e-14
+        assert np.linalg.norm(x - xbest) <= 1e-7 * max(1.0, np.linalg.norm(xbest))
+        c = A.T @ (b - A @ x)  # Eq. 12: c(x) in lambda * subdifferential
+        supp = x != 0
+        assert np.max(np.abs(c)) <= lam * (1 + 1e-7)
+        assert np.max(np.abs(c[supp] - lam * np.sign(x[supp])), initial=0) <= 1e-7 * lam
+
+
+def test_p12_kkt_and_lasso_equivalence():
+    """(P1,2) via reading R10: ||b - Ax|| = eps at the optimum, and x solves
+    (QP_lambda) with lambda = ||A^T r||_inf (the KKT multiplier)."""
+    g = np.random.default_rng(5)
+    m, n = 20, 40
+    A = g.standard_normal((m, n))
+    A = np.asfortranarray(A / np.linalg.norm(A, axis=0))
+    x0 = np.zeros(n)
+    x0[g.choice(n, 3, replace=False)] = 1.0 + g.random(3)
+    b = A @ x0 + 0.05 * g.standard_normal(m)
+    eps = 0.5 * np.linalg.norm(b - A @ x0) + 0.05
+    x, e, th, st = oracle.palm(A, b, mode=oracle.MODE_P12, tol=1e-12, epsilon=eps,
+                               max_outer=5000)
+    r = b - A @ x
+    assert abs(np.linalg.norm(r) - eps) <= 1e-6 * eps
+    lam = np.max(np.abs(A.T @ r))
+    xq, _ = oracle.fista_qp(A, b, lam, tol=1e-14, max_iter=500000)
+    assert np.linalg.norm(x - xq) <= 1e-5 * np.linalg.norm(xq)
+
+
+# --------------------------------------------------------- exact recovery
+
+def test_exact_recovery_configuration_200x400():
+    """§VI-A claim: PALM and DALM reach r_k <= 1e-10 on noise-free (P1);
+    200 x 400 Gaussian unit columns, 20-sparse +-1 x0, 20 trials."""
+    claim = json.load(open(os.path.join(GOLD, "paper_claims.json")))["exact_recovery"]["rel_err"]
+    for seed in range(20):
+        p = synthetic.p1_instance(200, 400, 20, seed=seed)
+        A, b, x0 = p["A"], p["b"], p["x0"]
+        w, y, st = oracle.dalm(A, b, cab=False, tol=1e-13, max_iter=20000)
+        assert np.linalg.norm(w - x0) / np.linalg.norm(x0) <= claim, seed
+        x, _, _, st2 = oracle.palm(A, b, mode=oracle.MODE_P1, tol=1e-13)
+        assert np.linalg.norm(x - x0) / np.linalg.norm(x0) <= claim, seed
+
+
+# ------------------------------------------------------------ closed forms
+
+def test_closed_forms():
+    g = np.random.default_rng(2)
+    I5 = np.asfortranarray(np.eye(5))
+    b = g.standard_normal(5)
+    w, y, _ = oracle.dalm(I5, b, cab=False, tol=1e-14)
+    assert np.allclose(w, b, atol=1e-12)  # A = I: the only feasible x is b
+    x, _, _, _ = oracle.palm(I5, b, mode=oracle.MODE_P1, tol=1e-14)
+    assert np.allclose(x, b, atol=1e-10)
+    lam = 0.4
+    xq, _ = oracle.fista_qp(I5, b, lam, tol=1e-15)
+    assert np.allclose(xq, np.sign(b) * np.maximum(np.abs(b) - lam, 0), atol=1e-13)
+    A, bb = _tiny(9, 6, 12)
+    xz, st = oracle.fista_qp(A, bb, 1.01 * np.max(np.abs(A.T @ bb)), tol=1e-12)
+    assert np.all(xz == 0.0)
+    z = np.zeros(6)
+    for cab in (False, True):
+        w, y, st = oracle.dalm(A, z, cab=cab, tol=1e-12)
+        assert np.all(w == 0.0) and st["iters"] == 1
+    x, e, th, st = oracle.palm(A, z, mode=oracle.MODE_CAB, tol=1e-12)
+    assert np.all(x == 0.0) and np.all(e == 0.0)
+    # CAB with A = I: the optimum value is ||b||_1 (any sign-consistent split)
+    w, y, st = oracle.dalm(I5, b, cab=True, tol=1e-14, max_iter=100000)
+    assert abs(np.abs(w).sum() - np.abs(b).sum()) <= 1e-9 * np.abs(b).sum()
+
+
+def test_lipschitz_is_spectral_norm_squared():
+    for seed in range(3):
+        A, _ = _tiny(seed, 30, 50)
+        L = oracle.lipschitz(A, safety=1.0)
+        assert abs(L - np.linalg.norm(A, 2) ** 2) <= 1e-8 * L
+    cab = synthetic.cab_problem(64, 4, 8, 1, seed=3)
+    L = oracle.lipschitz(cab["A"], safety=1.01)
+    assert abs(L / 1.01 - np.linalg.norm(cab["A"], 2) ** 2) <= 1e-8 * L
+
+
+def test_dalm_rejects_singular_aat():
+    A, b = _tiny(4, 6, 12)
+    A2 = np.asfortranarray(np.vstack([A, A[:1]]))  # duplicated row: A A^T singular
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.dalm(A2, np.append(b, b[0]), cab=False, tol=1e-10)
+    w, y, st = oracle.dalm(A2, np.append(b, b[0]), cab=True, tol=1e-8, max_iter=10)
+    assert st["iters"] == 10  # A A^T + I is always SPD
+
+
+# -------------------------------------------------------------- invariances
+
+def test_invariances():
+    p = synthetic.p1_instance(40, 80, 4, seed=21)
+    A, b = p["A"], p["b"]
+    w, _, _ = oracle.dalm(A, b, cab=False, tol=1e-13)
+    ws, _, _ = oracle.dalm(A, 3.5 * b, cab=False, tol=1e-13)
+    assert np.linalg.norm(ws - 3.5 * w) <= 1e-9 * np.linalg.norm(ws)
+    perm = np.random.default_rng(0).permutation(80)
+    wp, _, _ = oracle.dalm(np.asfortranarray(A[:, perm]), b, cab=False, tol=1e-13)
+    assert np.linalg.norm(wp - w[perm]) <= 1e-9 * np.linalg.norm(w)
+    flip = np.ones(80)
+    flip[::3] = -1
+    wf, _, _ = oracle.dalm(np.asfortranarray(A * flip), b, cab=False, tol=1e-13)
+    assert np.linalg.norm(wf - flip * w) <= 1e-9 * np.linalg.norm(w)
+    Ad = np.asfortranarray(np.hstack([A, A[:, :1]]))  # duplicate column: same optimum value
+    wd, _, _ = oracle.dalm(Ad, b, cab=False, tol=1e-13)
+    assert abs(np.abs(wd).sum() - np.abs(w).sum()) <= 1e-8 * np.abs(w).sum()
+    # PALM on CAB is equivariant under b -> alpha b (xi = 2m/||b||_1 scales as 1/alpha)
+    cab = synthetic.cab_problem(32, 3, 4, 1, seed=4)
+    A, b = cab["A"], cab["B"][:, 0]
+    x, e, _, _ = oracle.palm(A, b, mode=oracle.MODE_CAB, tol=1e-6, max_outer=50)
+    x2, e2, _, _ = oracle.palm(A, 2.0 * b, mode=oracle.MODE_CAB, tol=1e-6, max_outer=50)
+    assert np.linalg.norm(x2 - 2 * x) <= 1e-9 * np.linalg.norm(x2)
+    assert np.linalg.norm(e2 - 2 * e) <= 1e-9 * np.linalg.norm(e2)
+
+
+# ----------------------------------------------------------- classification
+
+def test_classify_hand_fixture():
+    fx = json.load(open(os.path.join(GOLD, "classify_hand.json")))
+    A = np.asfortranarray(np.array(fx["A_columns"], dtype=float).T)
+    lab, slab, resid, sci = oracle.classify(A, fx["offsets"], fx["b"], fx["x"], fx["e"])
+    assert lab == fx["label"] and slab == fx["sci_label"]
+    assert np.allclose(resid, fx["residuals"], rtol=1e-15)
+    assert np.allclose(sci, fx["sci"], rtol=1e-15)
+
+
+def test_classify_recovers_planted_class():
+    cab = synthetic.cab_problem(96, 4, 10, 4, corrupt=0.0, noise=0.0, seed=6)
+    A = cab["A"]
+    for j in range(4):
+        c = int(cab["labels"][j])
+        x = np.zeros(A.shape[1])
+        x[cab["offsets"][c]:cab["offsets"][c + 1]] = 1.0
+        b = A @ x  # exactly in class c's span
+        lab, slab, resid, _ = oracle.classify(A, cab["offsets"], b, x)
+        assert lab == c and slab == c and resid[c] <= 1e-12
+
+
+# ------------------------------------------------------- unrolled gradient
+
+def _unrolled_setup(seed=0, m=12, n=24, K=12, J=4):
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((m, n))
+    A = np.asfortranarray(A / np.linalg.norm(A, axis=0))
+    xt = np.zeros(n)
+    xt[g.choice(n, 3, replace=False)] = g.standard_normal(3)
+    b = A @ xt + 0.01 * g.standard_normal(m)
+    L = oracle.lipschitz(A)
+    xi = 2.0 * m / np.abs(b).sum()
+    return A, b, xt, L, xi, K, J
+
+
+def _fd(A, b, xi, L, K, J, xt, dA, db, h):
+    lp = oracle.unrolled_palm(A + h * dA, b + h * db, xi, L, K, J, xt, grad=False)[1]
+    lm = oracle.unrolled_palm(A - h * dA, b - h * db, xi, L, K, J, xt, grad=False)[1]
+    return (lp - lm) / (2 * h)
+
+
+def test_unrolled_gradient_finite_differences():
+    """Central differences in FP64 (h = 1e-3, unit-norm directions) on the
+    loss 1/2||x_K - x_t||^2.  A direction counts only when the estimates at h
+    and h/2 agree (no soft-threshold kink crossed inside +-h)."""
+    checked = 0
+    for seed in range(6):
+        A, b, xt, L, xi, K, J = _unrolled_setup(seed)
+        x, loss, gA, gb = oracle.unrolled_palm(A, b, xi, L, K, J, xt)
+        g = np.random.default_rng(100 + seed)
+        h = 1e-3
+        for _ in range(3):
+            dA = np.asfortranarray(g.standard_normal(A.shape))
+            db = g.standard_normal(b.shape)
+            nrm = np.sqrt(np.sum(dA * dA) + db @ db)
+            dA, db = dA / nrm, db / nrm
+            f1 = _fd(A, b, xi, L, K, J, xt, dA, db, h)
+            f2 = _fd(A, b, xi, L, K, J, xt, dA, db, h / 2)
+            if abs(f1 - f2) > 1e-6 * max(1e-8, abs(f2)):
+                continue
+            an = np.sum(gA * dA) + gb @ db
+            assert abs(f2 - an) <= 1e-5 * max(1e-8, abs(an)), (seed, f2, an)
+            checked += 1
+    assert checked >= 8
+
+
+def _b_linear(A, b, xi, L, K, J, xt, v, h):
+    """x_K is piecewise linear in b (xi, L frozen): equal one-sided slopes
+    mean no kink is crossed inside +-h."""
+    x0 = oracle.unrolled_palm(A, b, xi, L, K, J, xt, grad=False)[0]
+    xp = oracle.unrolled_palm(A, b + h * v, xi, L, K, J, xt, grad=False)[0]
+    xm = oracle.unrolled_palm(A, b - h * v, xi, L, K, J, xt, grad=False)[0]
+    ok = np.linalg.norm((xp - x0) - (x0 - xm)) <= 1e-9 * max(1e-30, np.linalg.norm(xp - x0))
+    return ok, (xp - xm) / (2 * h), x0
+
+
+def test_unrolled_adjoint_identity():
+    """<J v, u> = <v, J^T u> for the map b -> x_K (piecewise linear in b with
+    xi and L frozen, so the central difference is exact inside a region)."""
+    checked = 0
+    for seed in range(6):
+        A, b, xt, L, xi, K, J = _unrolled_setup(10 + seed)
+        g = np.random.default_rng(seed)
+        u = g.standard_normal(A.shape[1])
+        v = g.standard_normal(A.shape[0])
+        ok, Jv, x0 = _b_linear(A, b, xi, L, K, J, xt, v, 1e-6)
+        if not ok:
+            continue
+        # J^T u: gradient of <x_K, u> = gradient of 1/2||x - x_t||^2 with x_t = x - u
+        _, _, _, JTu = oracle.unrolled_palm(A, b, xi, L, K, J, x0 - u)
+        assert abs(Jv @ u - v @ JTu) <= 1e-8 * max(1.0, abs(v @ JTu))
+        checked += 1
+    assert checked >= 3
