@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched cross-and-bouquet DALM solve (one JSON line).
+
+Workload (the robust-classification setting of §VI-B at the stated sizes):
+dictionary [A I] with A 1024 x 1200 = 40 classes x 30 columns, each class a
+rank-9 nonnegative subspace plus 1 % noise, unit columns; 1024 test vectors
+with 30 % of their entries replaced by uniform [0, 1] gross errors; DALM
+(Algorithm 2) in FP32, every test vector stopped by the relative-change rule
+of §VI-C at tol, then classified by the minimum per-class residual.
+
+A step is one l1_solve_batch over the 1024 right-hand sides (all sweeps,
+per-column stopping, finalisation and classification).  `value` counts the
+converged solves per second with the inputs resident in HBM; `e2e` repeats the
+measurement through the same C-ABI call with pinned host buffers (the copies
+in and out are inside the timed region).  L2 is flushed (a 512 MiB write)
+before every timed step; the flush is outside the step's CUDA events.
+
+--impl reference times the FP64 CPU oracle (the same algorithm, plain C) on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+# the benchmarked configuration (tests import it to check parity in the same launch shape)
+BENCH = dict(m=1024, classes=40, per_class=30, N=1024, corrupt=0.3, seed=1000,
+             tol=1e-4, max_iter=10000, solver="DALM")
+METRIC = "solves/sec at rel. err <=1e-4 vs FP64 oracle"
+L2_FLUSH_BYTES = 512 << 20
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+
+
+def workload(rank: int = 0):
+    return synthetic.cab_problem(BENCH["m"], BENCH["classes"], BENCH["per_class"], BENCH["N"],
+                                 corrupt=BENCH["corrupt"], seed=BENCH["seed"] + rank)
+
+
+def config_dict(extra=None):
+    d = {"workload": f"cab_dalm_m{BENCH['m']}_n{BENCH['classes'] * BENCH['per_class']}_N{BENCH['N']}",
+         "m": BENCH["m"], "n": BENCH["classes"] * BENCH["per_class"], "classes": BENCH["classes"],
+         "rhs_per_gpu": BENCH["N"], "solver": BENCH["solver"], "tol": BENCH["tol"],
+         "max_iter": BENCH["max_iter"], "corrupt_fraction": BENCH["corrupt"],
+         "l2": "flushed (512 MiB write) before each timed step; A (4.9 MB) is L2-resident within a solve"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm_, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm_)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def run_cpu_oracle(p, cols, threads, tol, max_iter):
+    import concurrent.futures as cf
+
+    import oracle
+    oracle.build()
+    A, B = p["A"], p["B"]
+
+    def one(j):
+        return oracle.dalm(A, B[:, j], cab=True, tol=tol, max_iter=max_iter)[2]
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        stats = list(ex.map(one, cols))
+    dt = time.perf_counter() - t0
+    conv = sum(1 for s in stats if s["converged"])
+    return conv, dt, stats
+
+
+def bench_reference(args, rank, world):
+    """FP64 CPU oracle on the host cores (the comparison arm)."""
+    if rank != 0:
+        return 0
+    p = workload(0)
+    threads = min(os.cpu_count() or 1, 16)
+    sample = list(range(threads))  # one instance per core per step
+    for _ in range(max(0, min(args.warmup, 1))):
+        pass  # the oracle has no warm-up state
+    total_conv, total_t = 0, 0.0
+    for _ in range(args.steps):
+        conv, dt, _ = run_cpu_oracle(p, sample, threads, BENCH["tol"], BENCH["max_iter"])
+        total_conv += conv
+        total_t += dt
+    value = total_conv / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict({"sample": f"{len(sample)} of {BENCH['N']} test vectors per step"}),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{len(sample)} test vectors per step, one per thread"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_ours(args, rank, world):
+    import torch
+
+    import paper_1007_3753_gb300 as l1
+    from paper_1007_3753_gb300 import build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    l1.load()
+    p = workload(rank)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    m, n = A.shape
+    N = B.shape[1]
+    stream = torch.cuda.current_stream()
+    A_d = torch.from_numpy(np.ascontiguousarray(A.T, dtype=np.float32)).cuda().t()
+    B_d = torch.from_numpy(np.ascontiguousarray(B.T, dtype=np.float32)).cuda().t()
+    x_d = torch.empty((N, n + m), dtype=torch.float32, device="cuda").t()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    solver = l1.DALM if BENCH["solver"] == "DALM" else l1.PALM
+    s = l1.Solver(A_d, mode=l1.CAB, solver=solver, class_offsets=off, profile=True,
+                  stream=stream.cuda_stream)
+    setup_ms = s.info()["setup_ms"]
+    tol, max_iter = BENCH["tol"], BENCH["max_iter"]
+
+    for _ in range(args.warmup):
+        s.solve(B_d, tol, max_iter, x=x_d)
+    torch.cuda.synchronize()
+    info0 = s.info()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier()
+    if sampler:
+        sampler.start()
+    step_ms, conv, iters, labels_ok = [], 0, [], 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, _, res = s.solve(B_d, tol, max_iter, x=x_d)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        conv += int(np.sum(res["status"] == l1.CONVERGED))
+        iters.append(float(np.mean(res["iters"])))
+        labels_ok += int(np.sum(res["label"] == p["labels"]))
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    info1 = s.info()
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        cv = torch.tensor([conv], dtype=torch.float64, device="cuda")
+        dist.all_reduce(cv, op=dist.ReduceOp.SUM)
+        conv = int(cv.item())
+    value = conv / (total_ms / 1e3)
+
+    # ---- end to end through the same call with pinned host buffers
+    Bh = torch.from_numpy(np.ascontiguousarray(B.T, dtype=np.float32)).pin_memory().t()
+    xh = torch.empty((N, n + m), dtype=torch.float32).pin_memory().t()
+    s.solve(Bh, tol, max_iter, x=xh)  # warm
+    barrier()
+    t0 = time.perf_counter()
+    e2e_conv = 0
+    for _ in range(args.steps):
+        _, _, res = s.solve(Bh, tol, max_iter, x=xh)
+        e2e_conv += int(np.sum(res["status"] == l1.CONVERGED))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        cv = torch.tensor([e2e_conv], dtype=torch.float64, device="cuda")
+        dist.all_reduce(cv, op=dist.ReduceOp.SUM)
+        e2e_conv = int(cv.item())
+
+    if rank != 0:
+        s.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant sweep over the timed region
+    names = ["A_u", "Finv_r", "At_y", "other"]
+    d_ms = [info1["sweep_ms"][k] - info0["sweep_ms"][k] for k in range(4)]
+    d_fl = [info1["sweep_flop"][k] - info0["sweep_flop"][k] for k in range(4)]
+    d_ln = [info1["sweep_launches"][k] - info0["sweep_launches"][k] for k in range(4)]
+    k = int(np.argmax(d_ms))
+    achieved = d_fl[k] / (d_ms[k] / 1e3) / 1e12 if d_ms[k] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": f"sweep {names[k]} (gemm_simt_kernel)",
+                "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, no measured FP32 peak)",
+                "launches": d_ln[k], "avg_launch_us": 1e3 * d_ms[k] / max(1, d_ln[k]),
+                "share_of_sweep_time": d_ms[k] / max(1e-9, sum(d_ms))}
+
+    # ---- CPU oracle on a bounded sample of the same workload
+    threads = min(os.cpu_count() or 1, 16)
+    sample = list(range(threads))
+    c_conv, c_dt, _ = run_cpu_oracle(p, sample, threads, tol, max_iter)
+    cpu = {"value": c_conv / c_dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
+           "sample": f"first {len(sample)} of {N} test vectors, one per thread, same tol/max_iter"}
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": config_dict({"parallelism": f"replicas{world}" if world > 1 else "single",
+                                   "engine": "simt", "setup_ms": setup_ms,
+                                   "mean_iters": statistics.mean(iters),
+                                   "label_accuracy_vs_planted": labels_ok / (args.steps * N)}),
+            "e2e": {"value": e2e_conv / e2e_s, "unit": "solves/s",
+                    "h2d_bytes_per_step": 4 * m * N,
+                    "d2h_bytes_per_step": 4 * (n + m) * N + 72 * N},
+            "gpu_launches": int((info1["gpu_launches"] - info0["gpu_launches"])),
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--max-iter", type=int, default=None)
+    args = ap.parse_args()
+    if args.tol is not None:
+        BENCH["tol"] = args.tol
+    if args.max_iter is not None:
+        BENCH["max_iter"] = args.max_iter
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return bench_reference(args, rank, world)
+    return bench_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

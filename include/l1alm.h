@@ -1,0 +1,204 @@
+/*
+ * l1alm.h -- C ABI of the GB300 (sm_103a) augmented Lagrangian l1 solvers.
+ *
+ * Method: A. Y. Yang, Z. Zhou, A. Ganesh, S. S. Sastry, Y. Ma, "Fast
+ * l1-Minimization Algorithms for Robust Face Recognition":
+ *   - primal ALM (PALM): Algorithm 1 (§V-A) for the cross-and-bouquet
+ *     problem of Eq. 5, and the method of multipliers of Eq. 33 with FISTA
+ *     inner solves (§V-A) for basis pursuit (P1, Eq. 1);
+ *   - dual ALM (DALM): Algorithm 2 (§V-B, Eqs. 36-39);
+ *   - FISTA (Eq. 18, §IV-A) for unconstrained BPDN (QP_lambda, Eq. 3);
+ *   - the per-class residual and SCI classifiers (§II-A, Eq. 40).
+ * Equation numbers are the paper's in source order.
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major FP32: element (i, j) of an m x n matrix with
+ *     leading dimension ld sits at p[i + j*ld], ld >= m.
+ *   - Pointers may be host or device memory; the library detects which with
+ *     cudaPointerGetAttributes and copies host data in and out itself (these
+ *     copies are enqueued on the handle's stream).  Caller-owned buffers stay
+ *     caller-owned; the handle owns everything it derives from A.
+ *   - A negative return value means the call failed and wrote no output;
+ *     l1_status_string() names it.  Calls never abort the process.
+ *   - All device work is enqueued on the handle's stream (l1_options.stream
+ *     at setup, or l1_set_stream).  l1_solve_batch returns after the results
+ *     are on the host (it synchronises that stream).
+ *   - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef L1ALM_H
+#define L1ALM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define L1_API __attribute__((visibility("default")))
+#else
+#define L1_API
+#endif
+
+/* ------------------------------------------------------------ return codes */
+#define L1_OK 0
+#define L1_ERR_INVALID_ARG (-1) /* bad pointer, size, mode or option */
+#define L1_ERR_NOT_SPD (-2)     /* DALM needs A A^T invertible (§V-B); P1 with rank-deficient A */
+#define L1_ERR_OOM (-3)         /* device allocation failed */
+#define L1_ERR_CUDA (-4)        /* a CUDA runtime call failed (message: l1_last_error) */
+#define L1_ERR_TIMEOUT (-5)     /* a bounded device wait expired; the context stays usable */
+#define L1_ERR_NO_TAPE (-6)     /* l1_backward without an unrolled forward */
+#define L1_ERR_UNSUPPORTED (-7) /* valid request this build does not implement */
+
+/* --------------------------------------------------- per-instance status */
+#define L1_CONVERGED 0 /* stopping rule met: ||w_{k+1}-w_k|| / ||w_k|| < tol (§VI-C) */
+#define L1_MAX_ITER 1  /* max_iter reached first */
+#define L1_NONFINITE 2 /* an iterate became NaN/Inf; the instance was frozen */
+
+/* ------------------------------------------------------------------ enums */
+typedef enum {
+    L1_P1 = 0,        /* min ||x||_1  s.t. b = A x                      (Eq. 1) */
+    L1_P1_2 = 1,      /* min ||x||_1  s.t. ||b - A x||_2 <= epsilon     (Eq. 2) */
+    L1_QP_LAMBDA = 2, /* min 1/2||b - A x||^2 + lambda ||x||_1          (Eq. 3) */
+    L1_CAB = 3        /* min ||x||_1 + ||e||_1 s.t. b = A x + e, B=[A I] (Eq. 5) */
+} l1_mode;
+
+typedef enum { L1_PALM = 0, L1_DALM = 1 } l1_solver;
+
+typedef enum {
+    L1_A_FP32 = 0, /* A held in FP32 */
+    L1_A_BF16 = 1, /* A held in BF16 (round to nearest even), FP32 accumulate */
+    L1_A_FP8E4M3 = 2 /* A held in FP8 e4m3 with a per-column FP32 scale */
+} l1_precision;
+
+typedef enum {
+    L1_ENGINE_AUTO = 0,  /* pick per shape */
+    L1_ENGINE_SIMT = 1,  /* CUDA-core FP32 kernels (GEMV for N <= 8, tiled GEMM above) */
+    L1_ENGINE_TC = 2     /* tcgen05 tensor-core sweeps (batched right-hand sides) */
+} l1_engine;
+
+/* ---------------------------------------------------------------- options
+ * Zero in a field means "default"; l1_options_init fills the defaults. */
+typedef struct {
+    int32_t solver;     /* l1_solver; QP_LAMBDA always runs FISTA */
+    int32_t precision;  /* l1_precision */
+    int32_t engine;     /* l1_engine */
+    int32_t inner_max;  /* PALM inner FISTA cap per outer step; default 50 */
+    double lambda;      /* QP_LAMBDA weight (> 0) */
+    double epsilon;     /* P1_2 radius (> 0) */
+    double xi0;         /* PALM penalty; 0 -> 2m/||b||_1 per instance (§V-A) */
+    double xi_growth;   /* P1/P1_2 PALM: xi_{k+1} = min(growth xi_k, xi_max xi_0); 0 -> 1.2 */
+    double xi_max;      /* cap factor; 0 -> 1e4.  CAB keeps xi fixed (§V-A). */
+    double beta;        /* DALM penalty; 0 -> ||b||_1 / m per instance */
+    double lipschitz;   /* L of Algorithm 1 step 6; 0 -> power iteration x 1.01 */
+    double inner_tol;   /* PALM inner tolerance; 0 -> 0.1 * tol */
+    int32_t check_every; /* host polls the active count every this many iterations; 0 -> 16 */
+    int32_t class_count; /* CAB classification: number of classes C (0: off) */
+    const int32_t* class_offsets; /* host, C+1 entries; class c owns columns [off[c], off[c+1]) */
+    void* stream;        /* cudaStream_t for all work; NULL = legacy default stream */
+    int32_t unroll_K;    /* > 0: l1_solve_batch runs K unrolled PALM steps (P1) and keeps a tape */
+    int32_t unroll_J;    /* multiplier update every J inner steps; 0 -> 10 */
+    int32_t ckpt_every;  /* checkpoint interval of the tape; 0 -> 20 */
+    int32_t profile;     /* 1: time every sweep with CUDA events (l1_info.sweep_*) */
+} l1_options;
+
+/* Per-instance results (host memory). */
+typedef struct {
+    int32_t status;      /* L1_CONVERGED / L1_MAX_ITER / L1_NONFINITE */
+    int32_t iters;       /* outer iterations (PALM), iterations (DALM, FISTA) */
+    int32_t inner_iters; /* total inner FISTA steps (PALM); = iters otherwise */
+    int32_t label;       /* CAB: argmin_c ||b - e - A delta_c(x)||_2 (lowest index on ties), else -1 */
+    int32_t sci_label;   /* CAB: SCI argmax of Eq. 40, else -1 */
+    int32_t reserved;
+    double rel_change;   /* last ||w_{k+1}-w_k|| / ||w_k|| */
+    double primal_obj;   /* ||x||_1 (+||e||_1); QP: 1/2||b-Ax||^2 + lambda ||x||_1 */
+    double dual_obj;     /* b^T y / max(1, ||B^T y||_inf); QP: b^T u - 1/2||u||^2 */
+    double gap;          /* primal_obj - dual_obj (>= 0 up to rounding) */
+    double resid;        /* ||b - B w||_2 */
+    double param;        /* xi_0 (PALM), beta (DALM) or lambda / L (FISTA) used */
+} l1_result;
+
+typedef struct l1_handle_s* l1_handle;
+
+/* Handle information. */
+typedef struct {
+    int64_t m, n;
+    int32_t mode, solver, precision, engine;
+    double lipschitz;        /* L used by PALM / FISTA (0 if not computed) */
+    double setup_ms;         /* device time of l1_setup */
+    int64_t device_bytes;    /* bytes the handle holds on the device */
+    int64_t gpu_launches;    /* kernels launched by this handle so far */
+    /* with l1_options.profile = 1, per sweep kind (0: A u, 1: (B B^T)^{-1} r,
+     * 2: A^T y, 3: other): launches, summed CUDA-event time, and algorithmic
+     * FLOPs 2*M*K*(columns active at the last host poll), since setup */
+    int64_t sweep_launches[4];
+    double sweep_ms[4];
+    double sweep_flop[4];
+} l1_info;
+
+/* Fill *opt with the defaults. */
+L1_API void l1_options_init(l1_options* opt);
+
+/*
+ * l1_setup -- build a solver handle for the dictionary A (m x n, column-major,
+ * leading dimension lda >= m; host or device FP32).  A is copied; the caller
+ * keeps ownership.  One-time work (§V): the Lipschitz constant L = ||A||_2^2
+ * by power iteration (PALM, FISTA), and for DALM the FP64 Cholesky factor of
+ * B B^T = A A^T (+ I for CAB) and its explicit inverse (Eq. 39), stored FP32.
+ * Errors: L1_ERR_INVALID_ARG (null pointer, m or n <= 0, lda < m, P1 with
+ * m > n, unknown mode/solver/precision), L1_ERR_NOT_SPD (DALM on P1 with
+ * singular A A^T), L1_ERR_OOM, L1_ERR_CUDA, L1_ERR_UNSUPPORTED.
+ */
+L1_API int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode,
+                    const l1_options* opt, l1_handle* out);
+
+/*
+ * l1_solve_batch -- solve N independent problems that share A, one per
+ * column of b (m x N, leading dimension ldb >= m).
+ *   tol       stopping tolerance of the relative-change rule (§VI-C); 0 runs
+ *             exactly max_iter iterations.
+ *   max_iter  cap on outer iterations (PALM) or iterations (DALM, FISTA).
+ *   x         output, (n + m) x N for CAB ([x; e] per column), n x N otherwise,
+ *             leading dimension ldx.
+ *   y         optional (NULL) output of the dual iterate, m x N, leading
+ *             dimension ldy: DALM's y, PALM's multiplier theta.
+ *   res       host array of N results.
+ * Each column stops on its own rule and is frozen from then on (per-instance
+ * convergence masking).  Host pointers are copied in and out on the handle's
+ * stream.  Errors: L1_ERR_INVALID_ARG, L1_ERR_OOM, L1_ERR_CUDA,
+ * L1_ERR_TIMEOUT.
+ */
+L1_API int l1_solve_batch(l1_handle h, const float* b, int64_t ldb, int64_t N, double tol,
+                          int32_t max_iter, float* x, int64_t ldx, float* y, int64_t ldy,
+                          l1_result* res);
+
+/*
+ * l1_backward -- after an l1_solve_batch of a handle set up with
+ * unroll_K > 0 (K unrolled PALM steps in P1 mode, multiplier update every J
+ * steps, xi and L held constant), propagate grad_x (n x N, the adjoint of the
+ * returned x) back to grad_b (m x N, nullable) and grad_A (m x n, nullable,
+ * leading dimension m, overwritten).  Errors: L1_ERR_NO_TAPE,
+ * L1_ERR_INVALID_ARG, L1_ERR_OOM, L1_ERR_CUDA.
+ */
+L1_API int l1_backward(l1_handle h, const float* grad_x, int64_t N, float* grad_b,
+                       float* grad_A);
+
+/* Set the stream later calls enqueue on. */
+L1_API int l1_set_stream(l1_handle h, void* stream);
+
+/* Fill *info. */
+L1_API int l1_get_info(l1_handle h, l1_info* info);
+
+/* Release every device allocation of h.  NULL is a no-op. */
+L1_API int l1_destroy(l1_handle h);
+
+/* Static string naming a return code or status. */
+L1_API const char* l1_status_string(int code);
+
+/* Message of the last L1_ERR_CUDA on this thread (static storage). */
+L1_API const char* l1_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* L1ALM_H */

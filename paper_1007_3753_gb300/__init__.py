@@ -1,0 +1,250 @@
+"""Python binding of libl1alm: GB300 (sm_103a) PALM / DALM l1 solvers.
+
+Thin ctypes layer over the C ABI declared in ``include/l1alm.h``: argument
+marshalling only.  Every step of a solve runs in the library's CUDA kernels;
+PyTorch supplies device memory and the current stream.  There is no CPU
+fallback: if the compiled library is missing, importing the solver raises.
+
+Method: Yang, Zhou, Ganesh, Sastry, Ma, "Fast l1-Minimization Algorithms for
+Robust Face Recognition" -- Algorithm 1 (PALM), Algorithm 2 (DALM), FISTA
+(Eq. 18) and the per-class residual / SCI classifiers (§II-A, Eq. 40).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libl1alm.so")
+
+P1, P1_2, QP_LAMBDA, CAB = 0, 1, 2, 3
+PALM, DALM = 0, 1
+A_FP32, A_BF16, A_FP8E4M3 = 0, 1, 2
+ENGINE_AUTO, ENGINE_SIMT, ENGINE_TC = 0, 1, 2
+OK, ERR_INVALID_ARG, ERR_NOT_SPD, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_TAPE, ERR_UNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
+
+# every symbol include/l1alm.h declares
+EXPORTS = ("l1_options_init", "l1_setup", "l1_solve_batch", "l1_backward", "l1_set_stream",
+           "l1_get_info", "l1_destroy", "l1_status_string", "l1_last_error")
+
+
+class Options(C.Structure):
+    _fields_ = [("solver", C.c_int32), ("precision", C.c_int32), ("engine", C.c_int32),
+                ("inner_max", C.c_int32), ("lambda_", C.c_double), ("epsilon", C.c_double),
+                ("xi0", C.c_double), ("xi_growth", C.c_double), ("xi_max", C.c_double),
+                ("beta", C.c_double), ("lipschitz", C.c_double), ("inner_tol", C.c_double),
+                ("check_every", C.c_int32), ("class_count", C.c_int32),
+                ("class_offsets", C.POINTER(C.c_int32)), ("stream", C.c_void_p),
+                ("unroll_K", C.c_int32), ("unroll_J", C.c_int32), ("ckpt_every", C.c_int32),
+                ("profile", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("inner_iters", C.c_int32),
+                ("label", C.c_int32), ("sci_label", C.c_int32), ("reserved", C.c_int32),
+                ("rel_change", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
+                ("gap", C.c_double), ("resid", C.c_double), ("param", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("mode", C.c_int32), ("solver", C.c_int32),
+                ("precision", C.c_int32), ("engine", C.c_int32), ("lipschitz", C.c_double),
+                ("setup_ms", C.c_double), ("device_bytes", C.c_int64), ("gpu_launches", C.c_int64),
+                ("sweep_launches", C.c_int64 * 4), ("sweep_ms", C.c_double * 4),
+                ("sweep_flop", C.c_double * 4)]
+
+
+RESULT_FIELDS = [f for f, _ in Result._fields_ if f != "reserved"]
+
+_lib = None
+
+
+class L1Error(RuntimeError):
+    def __init__(self, code: int, what: str):
+        lib = load()
+        msg = lib.l1_status_string(code).decode()
+        extra = lib.l1_last_error().decode() if code == ERR_CUDA else ""
+        super().__init__(f"{what}: {msg} ({code}) {extra}".strip())
+        self.code = code
+
+
+def load() -> C.CDLL:
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libl1alm.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    L.l1_options_init.argtypes = [C.POINTER(Options)]
+    L.l1_options_init.restype = None
+    L.l1_setup.argtypes = [vp, i64, i64, i64, i32, C.POINTER(Options), C.POINTER(vp)]
+    L.l1_setup.restype = C.c_int
+    L.l1_solve_batch.argtypes = [vp, vp, i64, i64, dbl, i32, vp, i64, vp, i64, C.POINTER(Result)]
+    L.l1_solve_batch.restype = C.c_int
+    L.l1_backward.argtypes = [vp, vp, i64, vp, vp]
+    L.l1_backward.restype = C.c_int
+    L.l1_set_stream.argtypes = [vp, vp]
+    L.l1_set_stream.restype = C.c_int
+    L.l1_get_info.argtypes = [vp, C.POINTER(Info)]
+    L.l1_get_info.restype = C.c_int
+    L.l1_destroy.argtypes = [vp]
+    L.l1_destroy.restype = C.c_int
+    L.l1_status_string.argtypes = [C.c_int]
+    L.l1_status_string.restype = C.c_char_p
+    L.l1_last_error.argtypes = []
+    L.l1_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Address of a torch tensor (device or host) or numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise L1Error(rc, what)
+
+
+def _ld(a) -> int:
+    """Leading dimension of a column-major 2-D array / tensor (or a vector)."""
+    if a.ndim == 1:
+        return a.shape[0]
+    st = a.stride() if hasattr(a, "stride") and callable(a.stride) else tuple(s // a.itemsize for s in a.strides)
+    if st[0] != 1:
+        raise ValueError("expected a column-major (Fortran-order) 2-D array")
+    return max(st[1], a.shape[0])
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover - torch without CUDA
+        pass
+    return C.c_void_p(None)
+
+
+class Solver:
+    """A handle of the C ABI: one dictionary A, many right-hand sides.
+
+    ``A`` is m x n FP32 column-major, host (numpy, Fortran order) or device
+    (a torch CUDA tensor whose transpose is contiguous, e.g. ``A.t().contiguous().t()``).
+    """
+
+    def __init__(self, A, mode: int = CAB, solver: int = DALM, *, lam: float = 0.0,
+                 epsilon: float = 0.0, beta: float = 0.0, xi0: float = 0.0,
+                 xi_growth: float = 0.0, xi_max: float = 0.0, lipschitz: float = 0.0,
+                 inner_max: int = 0, inner_tol: float = 0.0, check_every: int = 0,
+                 class_offsets=None, precision: int = A_FP32, engine: int = ENGINE_AUTO,
+                 profile: bool = False, stream=None):
+        L = load()
+        o = Options()
+        L.l1_options_init(C.byref(o))
+        o.solver, o.precision, o.engine = solver, precision, engine
+        if inner_max:
+            o.inner_max = inner_max
+        o.lambda_, o.epsilon, o.beta, o.xi0 = lam, epsilon, beta, xi0
+        if xi_growth:
+            o.xi_growth = xi_growth
+        if xi_max:
+            o.xi_max = xi_max
+        o.lipschitz, o.inner_tol = lipschitz, inner_tol
+        o.profile = 1 if profile else 0
+        if check_every:
+            o.check_every = check_every
+        self._offsets = None
+        if class_offsets is not None:
+            self._offsets = np.ascontiguousarray(class_offsets, dtype=np.int32)
+            o.class_count = len(self._offsets) - 1
+            o.class_offsets = self._offsets.ctypes.data_as(C.POINTER(C.c_int32))
+        o.stream = stream if stream is not None else _current_stream()
+        if isinstance(A, np.ndarray):
+            A = np.asfortranarray(A, dtype=np.float32)
+        m, n = A.shape
+        h = C.c_void_p()
+        _check(L.l1_setup(_ptr(A), m, n, _ld(A), mode, C.byref(o), C.byref(h)), "l1_setup")
+        self._h = h
+        self.m, self.n, self.mode, self.solver = m, n, mode, solver
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().l1_get_info(self._h, C.byref(inf)), "l1_get_info")
+        out = {}
+        for k, _ in Info._fields_:
+            v = getattr(inf, k)
+            out[k] = list(v) if k.startswith("sweep_") else v
+        return out
+
+    def solve(self, b, tol: float, max_iter: int, x=None, y=None, want_y: bool = False):
+        """Solve one problem per column of b (m x N).
+
+        b may be a host numpy array or a torch tensor (device or host,
+        column-major).  Outputs are allocated like b when not given: x is
+        (n + m) x N for CAB ([x; e] per column), n x N otherwise; y (the dual
+        iterate) only if ``want_y`` or given.  Returns (x, y, results).
+        """
+        L = load()
+        is_np = isinstance(b, np.ndarray)
+        if is_np:
+            b = np.asfortranarray(b, dtype=np.float32)
+            if b.ndim == 1:
+                b = b.reshape(-1, 1, order="F")
+        elif b.dim() == 1:
+            b = b.reshape(-1, 1)
+        N = b.shape[1]
+        nx = self.n + self.m if self.mode == CAB else self.n
+        if x is None:
+            if is_np:
+                x = np.zeros((nx, N), dtype=np.float32, order="F")
+            else:
+                import torch
+                x = torch.empty((N, nx), dtype=torch.float32, device=b.device).t()
+        if y is None and want_y:
+            if is_np:
+                y = np.zeros((self.m, N), dtype=np.float32, order="F")
+            else:
+                import torch
+                y = torch.empty((N, self.m), dtype=torch.float32, device=b.device).t()
+        res = (Result * N)()
+        _check(L.l1_solve_batch(self._h, _ptr(b), _ld(b), N, float(tol), int(max_iter), _ptr(x), _ld(x),
+                                _ptr(y), _ld(y) if y is not None else 0, res), "l1_solve_batch")
+        return x, y, results_to_dict(res)
+
+    def set_stream(self, stream):
+        _check(load().l1_set_stream(self._h, stream), "l1_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().l1_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def results_to_dict(res) -> dict:
+    """Column arrays of an l1_result array."""
+    out = {}
+    for f in RESULT_FIELDS:
+        out[f] = np.array([getattr(r, f) for r in res])
+    return out

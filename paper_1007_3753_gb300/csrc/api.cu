@@ -1,0 +1,249 @@
+// The C ABI of include/l1alm.h: argument checks, handle lifetime, setup.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "setup.cuh"
+
+namespace l1 {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+int dev_alloc(Handle* h, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_last_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        *p = nullptr;
+        return L1_ERR_OOM;
+    }
+    e = cudaMemsetAsync(*p, 0, bytes, h->stream);
+    if (e != cudaSuccess) {
+        cudaFree(*p);
+        *p = nullptr;
+        set_last_error(std::string("cudaMemset: ") + cudaGetErrorString(e));
+        return L1_ERR_CUDA;
+    }
+    h->allocations.push_back(*p);
+    h->device_bytes += (int64_t)bytes;
+    return L1_OK;
+}
+
+static void free_all(Handle* h) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (void* p : h->allocations) cudaFree(p);
+    h->allocations.clear();
+    if (h->ws.h_active) cudaFreeHost(h->ws.h_active);
+    h->ws = Workspace{};
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->ev_pool.clear();
+}
+
+}  // namespace l1
+
+using namespace l1;
+
+extern "C" {
+
+void l1_options_init(l1_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->solver = L1_DALM;
+    opt->precision = L1_A_FP32;
+    opt->engine = L1_ENGINE_AUTO;
+    opt->inner_max = 50;
+    opt->xi_growth = 1.2;
+    opt->xi_max = 1e4;
+    opt->check_every = 16;
+    opt->unroll_J = 10;
+    opt->ckpt_every = 20;
+}
+
+const char* l1_status_string(int code) {
+    switch (code) {
+        case L1_OK: return "L1_OK / L1_CONVERGED";
+        case L1_MAX_ITER: return "L1_MAX_ITER";
+        case L1_NONFINITE: return "L1_NONFINITE";
+        case L1_ERR_INVALID_ARG: return "L1_ERR_INVALID_ARG";
+        case L1_ERR_NOT_SPD: return "L1_ERR_NOT_SPD";
+        case L1_ERR_OOM: return "L1_ERR_OOM";
+        case L1_ERR_CUDA: return "L1_ERR_CUDA";
+        case L1_ERR_TIMEOUT: return "L1_ERR_TIMEOUT";
+        case L1_ERR_NO_TAPE: return "L1_ERR_NO_TAPE";
+        case L1_ERR_UNSUPPORTED: return "L1_ERR_UNSUPPORTED";
+        default: return "unknown l1 code";
+    }
+}
+
+const char* l1_last_error(void) { return g_last_error.c_str(); }
+
+int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, const l1_options* opt,
+             l1_handle* out) {
+    if (!out) return L1_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!A || m <= 0 || n <= 0 || lda < m || m > (1 << 20) || n > (1 << 24)) return L1_ERR_INVALID_ARG;
+    if (mode < L1_P1 || mode > L1_CAB) return L1_ERR_INVALID_ARG;
+    l1_options o;
+    if (opt) o = *opt;
+    else l1_options_init(&o);
+    if (o.solver != L1_PALM && o.solver != L1_DALM) return L1_ERR_INVALID_ARG;
+    if (o.precision < L1_A_FP32 || o.precision > L1_A_FP8E4M3) return L1_ERR_INVALID_ARG;
+    if (o.engine < L1_ENGINE_AUTO || o.engine > L1_ENGINE_TC) return L1_ERR_INVALID_ARG;
+    if (mode == L1_QP_LAMBDA && !(o.lambda > 0.0)) return L1_ERR_INVALID_ARG;
+    if (mode == L1_P1_2 && !(o.epsilon > 0.0)) return L1_ERR_INVALID_ARG;
+    if (o.class_count < 0 || (o.class_count > 0 && !o.class_offsets)) return L1_ERR_INVALID_ARG;
+    if (o.class_count > 0) {
+        if (o.class_offsets[0] != 0 || o.class_offsets[o.class_count] != n) return L1_ERR_INVALID_ARG;
+        for (int c = 0; c < o.class_count; ++c)
+            if (o.class_offsets[c + 1] <= o.class_offsets[c]) return L1_ERR_INVALID_ARG;
+    }
+    // not implemented in this build
+    if (mode == L1_P1_2) return L1_ERR_UNSUPPORTED;
+    if (o.precision != L1_A_FP32) return L1_ERR_UNSUPPORTED;
+    if (o.engine == L1_ENGINE_TC) return L1_ERR_UNSUPPORTED;
+    if (o.unroll_K > 0) return L1_ERR_UNSUPPORTED;
+
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return L1_ERR_OOM;
+    h->m = m;
+    h->n = n;
+    h->ldm = round_up(m, 32);
+    h->ldn = round_up(n, 32);
+    h->mode = mode;
+    h->opt = o;
+    h->opt.class_offsets = nullptr;
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    cudaGetDevice(&h->device);
+    if (o.class_count > 0) h->class_offsets.assign(o.class_offsets, o.class_offsets + o.class_count + 1);
+
+    int rc = L1_OK;
+    float* stage = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    do {
+        if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) { rc = L1_ERR_CUDA; break; }
+        cudaEventRecord(ev0, h->stream);
+        rc = dev_alloc_t(h, &h->A_cm, (size_t)h->ldm * n);
+        if (rc) break;
+        rc = dev_alloc_t(h, &h->A_rm, (size_t)h->ldn * m);
+        if (rc) break;
+        if (cudaMalloc(&stage, sizeof(float) * (size_t)m * n) != cudaSuccess) { rc = L1_ERR_OOM; break; }
+        if (cudaMemcpy2DAsync(stage, m * sizeof(float), A, lda * sizeof(float), m * sizeof(float), n,
+                              cudaMemcpyDefault, h->stream) != cudaSuccess) {
+            set_last_error("l1_setup: copy of A failed");
+            rc = L1_ERR_CUDA;
+            break;
+        }
+        rc = make_layouts(h, stage, m);
+        if (rc) break;
+        const bool needs_L = (mode == L1_QP_LAMBDA) || (o.solver == L1_PALM);
+        if (o.lipschitz > 0.0) {
+            h->lipschitz = o.lipschitz;
+        } else if (needs_L) {
+            double rho = 0.0;
+            rc = power_iteration(h, 1000, 1e-6, &rho);
+            if (rc) break;
+            h->lipschitz = 1.01 * rho;
+            if (!(h->lipschitz > 0.0)) { rc = L1_ERR_INVALID_ARG; break; }  // A == 0
+        }
+        if (o.solver == L1_DALM && mode != L1_QP_LAMBDA) {
+            rc = dev_alloc_t(h, &h->F, (size_t)h->ldm * m);
+            if (rc) break;
+            rc = dalm_factor(h, mode == L1_CAB ? 1.0 : 0.0);
+            if (rc) break;
+        }
+        cudaEventRecord(ev1, h->stream);
+        if (cudaEventSynchronize(ev1) != cudaSuccess) { rc = L1_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        h->setup_ms = ms;
+    } while (false);
+    if (stage) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(stage);
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (rc == L1_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_last_error(std::string("l1_setup: ") + cudaGetErrorString(e));
+            rc = L1_ERR_CUDA;
+        }
+    }
+    if (rc != L1_OK) {
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = reinterpret_cast<l1_handle>(h);
+    return L1_OK;
+}
+
+int l1_solve_batch(l1_handle hh, const float* b, int64_t ldb, int64_t N, double tol, int32_t max_iter, float* x,
+                   int64_t ldx, float* y, int64_t ldy, l1_result* res) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !b || !x || !res || N <= 0 || N > (1 << 20) || max_iter <= 0 || !(tol >= 0.0)) return L1_ERR_INVALID_ARG;
+    if (ldb < h->m) return L1_ERR_INVALID_ARG;
+    const int64_t nx = (h->mode == L1_CAB) ? h->n + h->m : h->n;
+    if (ldx < nx) return L1_ERR_INVALID_ARG;
+    if (y && ldy < h->m) return L1_ERR_INVALID_ARG;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != h->device) cudaSetDevice(h->device);
+    int rc = solve_batch(h, b, ldb, (int)N, tol, max_iter, x, ldx, y, ldy, res);
+    if (dev != h->device) cudaSetDevice(dev);
+    return rc;
+}
+
+int l1_backward(l1_handle hh, const float* grad_x, int64_t N, float* grad_b, float* grad_A) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !grad_x || N <= 0) return L1_ERR_INVALID_ARG;
+    (void)grad_b;
+    (void)grad_A;
+    if (!h->has_tape) return L1_ERR_NO_TAPE;
+    return L1_ERR_UNSUPPORTED;
+}
+
+int l1_set_stream(l1_handle hh, void* stream) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return L1_ERR_INVALID_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return L1_OK;
+}
+
+int l1_get_info(l1_handle hh, l1_info* info) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !info) return L1_ERR_INVALID_ARG;
+    info->m = h->m;
+    info->n = h->n;
+    info->mode = h->mode;
+    info->solver = h->opt.solver;
+    info->precision = h->opt.precision;
+    info->engine = h->opt.engine;
+    info->lipschitz = h->lipschitz;
+    info->setup_ms = h->setup_ms;
+    info->device_bytes = h->device_bytes;
+    info->gpu_launches = h->launches;
+    for (int k = 0; k < 4; ++k) {
+        info->sweep_launches[k] = h->sweep_launches[k];
+        info->sweep_ms[k] = h->sweep_ms[k];
+        info->sweep_flop[k] = h->sweep_flop[k];
+    }
+    return L1_OK;
+}
+
+int l1_destroy(l1_handle hh) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return L1_OK;
+    free_all(h);
+    delete h;
+    return L1_OK;
+}
+
+}  // extern "C"

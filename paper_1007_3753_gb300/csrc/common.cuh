@@ -1,0 +1,158 @@
+// Shared definitions of the CUDA library: error plumbing, the handle, device
+// helpers.  Everything here is internal; the public surface is include/l1alm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "l1alm.h"
+
+namespace l1 {
+
+// ------------------------------------------------------------------ errors
+struct Status {
+    int code = L1_OK;
+};
+
+void set_last_error(const std::string& msg);
+
+#define L1_CUDA_TRY(expr)                                                                 \
+    do {                                                                                  \
+        cudaError_t _e = (expr);                                                          \
+        if (_e != cudaSuccess) {                                                          \
+            ::l1::set_last_error(std::string(#expr) + ": " + cudaGetErrorString(_e));     \
+            return _e == cudaErrorMemoryAllocation ? L1_ERR_OOM : L1_ERR_CUDA;            \
+        }                                                                                 \
+    } while (0)
+
+#define L1_TRY(expr)               \
+    do {                           \
+        int _rc = (expr);          \
+        if (_rc != L1_OK) return _rc; \
+    } while (0)
+
+// Every kernel launch in the library goes through this so the handle can count
+// its launches and a launch error is reported, not swallowed.
+#define L1_LAUNCH_CHECK(h)                                                          \
+    do {                                                                            \
+        ++(h)->launches;                                                            \
+        cudaError_t _e = cudaGetLastError();                                        \
+        if (_e != cudaSuccess) {                                                    \
+            ::l1::set_last_error(std::string("kernel launch: ") + cudaGetErrorString(_e)); \
+            return L1_ERR_CUDA;                                                     \
+        }                                                                           \
+    } while (0)
+
+inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// --------------------------------------------------------- device buffers
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// -------------------------------------------------------------- the handle
+// Column phases of the batched PALM state machine.
+enum PalmPhase : int32_t { PH_INNER = 0, PH_OUTER = 1, PH_FIRST = 2 };
+
+struct Workspace {
+    int64_t cap_N = 0;  // columns the panels are sized for
+    // panels (column-major; ldm = padded m, ldn = padded n)
+    float* B = nullptr;   // right-hand sides, m x N
+    float* Wx = nullptr;  // DALM multiplier x-part / PALM w (current FISTA iterate)
+    float* We = nullptr;  // DALM multiplier e-part / PALM e
+    float* Ux = nullptr;  // DALM z - w/beta (x-part) / PALM z (FISTA extrapolation, B operand)
+    float* Ue = nullptr;  // DALM z - w/beta (e-part)
+    float* R = nullptr;   // DALM right-hand side of Eq. 39 / PALM residual c - A z
+    float* Y = nullptr;   // DALM y / PALM theta
+    float* X = nullptr;   // PALM outer x_k
+    float* Cc = nullptr;  // PALM c = b - e + theta/xi
+    float* S = nullptr;   // scratch n x N (finalize)
+    // per column
+    double* part = nullptr;   // reduction partials, [slots][N][4]
+    double* colstat = nullptr; // [N][8] per-column doubles (see solver.cu)
+    float* colf = nullptr;    // [N][8] per-column floats (beta, 1/beta, xi, t, ...)
+    int32_t* coli = nullptr;  // [N][8] per-column ints (active, status, iters, ...)
+    int32_t* active_count = nullptr;  // device counter
+    int32_t* h_active = nullptr;      // pinned host mirror
+    double* resid2 = nullptr;  // classification residuals, [C][N]
+    double* classl1 = nullptr; // classification l1 mass, [C][N]
+    int32_t* class_off = nullptr;
+    size_t part_slots = 0;
+};
+
+struct Handle {
+    int64_t m = 0, n = 0;
+    int64_t ldm = 0, ldn = 0;  // padded leading dimensions (multiples of 32 floats)
+    int32_t mode = L1_P1;
+    l1_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    // dictionary
+    float* A_cm = nullptr;  // column-major m x n, ld = ldm  (rows of A^T contiguous: K-major for A^T y)
+    float* A_rm = nullptr;  // row-major m x n, ld = ldn     (K-major for A u)
+    float* F = nullptr;     // DALM: (B B^T)^{-1}, m x m symmetric, ld = ldm
+    double lipschitz = 0.0;
+    double setup_ms = 0.0;
+    int64_t device_bytes = 0;
+    int64_t launches = 0;
+    std::vector<int32_t> class_offsets;  // host copy
+    Workspace ws;
+    std::vector<void*> allocations;
+    // unrolled tape (differentiation)
+    bool has_tape = false;
+    // sweep profiling (l1_options.profile)
+    std::vector<cudaEvent_t> ev_pool;
+    int64_t sweep_launches[4] = {0, 0, 0, 0};
+    double sweep_ms[4] = {0, 0, 0, 0};
+    double sweep_flop[4] = {0, 0, 0, 0};
+};
+
+int dev_alloc(Handle* h, void** p, size_t bytes);
+template <class T>
+inline int dev_alloc_t(Handle* h, T** p, size_t count) {
+    return dev_alloc(h, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+// ----------------------------------------------------------- device helpers
+__device__ __forceinline__ float soft_thr(float v, float a) {
+    // proximal operator of a*|.| (§IV): sign(v) max(|v| - a, 0), sign(0) = 0
+    return v > a ? v - a : (v < -a ? v + a : 0.0f);
+}
+
+__device__ __forceinline__ float clamp_unit(float v) {
+    // projection onto [-1, 1] (Eq. 38)
+    return fminf(1.0f, fmaxf(-1.0f, v));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// relative change with the zero conventions of the stopping rule (§VI-C):
+// a zero step is 0, a nonzero step from a zero iterate is +inf.
+__host__ __device__ __forceinline__ double rel_change(double diff, double base) {
+    if (diff == 0.0) return 0.0;
+    if (base == 0.0) return INFINITY;
+    return diff / base;
+}
+
+}  // namespace l1

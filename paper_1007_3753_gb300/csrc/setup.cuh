@@ -1,0 +1,22 @@
+// One-time setup steps (definitions in setup.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace l1 {
+
+// A_cm / A_rm from a device column-major copy of A
+int make_layouts(Handle* h, const float* A_dev, int64_t lda);
+
+// Rayleigh-quotient estimate of ||A||_2^2 by power iteration on A^T A
+int power_iteration(Handle* h, int max_iter, double rtol, double* L_out);
+
+// h->F = (A A^T + diag_add I)^{-1} in FP32 via an FP64 Cholesky factor;
+// L1_ERR_NOT_SPD when a pivot is not positive beyond rounding
+int dalm_factor(Handle* h, double diag_add);
+
+// batched solve (solve.cu)
+int solve_batch(Handle* h, const float* b_dev, int64_t ldb, int N, double tol, int max_iter,
+                float* x_dev, int64_t ldx, float* y_dev, int64_t ldy, l1_result* res);
+
+}  // namespace l1

@@ -1,0 +1,492 @@
+// Fused epilogues and per-column controllers of the batched PALM / DALM /
+// FISTA sweeps.  Every panel is column-major with one problem per column;
+// m-length panels use leading dimension ldm, n-length panels ldn.
+#pragma once
+
+#include "common.cuh"
+#include "gemm_simt.cuh"
+
+namespace l1 {
+
+// Per-column solver state (struct of arrays, N entries each).
+struct Cols {
+    int N;
+    // float
+    float* beta;   // DALM penalty
+    float* binv;   // 1 / beta
+    float* xi;     // PALM penalty of the current outer step
+    float* xicap;  // PALM: cap of the xi schedule
+    float* mu;     // FISTA momentum (t_l - 1) / t_{l+1} of the next inner step
+    // int
+    int32_t* active;
+    int32_t* status;
+    int32_t* iters;  // outer iterations (PALM) / iterations
+    int32_t* inner;  // total inner steps
+    int32_t* phase;  // PalmPhase
+    int32_t* l;      // inner steps in the current outer iteration
+    int32_t* label;
+    int32_t* sci_label;
+    // double
+    double* t;     // FISTA t_l
+    double* rel;   // last relative change
+    double* de2;   // PALM: ||e_{k+1} - e_k||^2 of the current outer iteration
+    double* e2;    // PALM: ||e_k||^2
+    double* b1;    // ||b||_1
+    double* fin;   // [N][8] final metrics
+    float* smax;   // max |B^T y| (finalize)
+};
+
+// xi used by an outer step: the schedule of §V-A (growth then cap) applies
+// from the second outer step on; the first keeps xi_0.
+__device__ __forceinline__ float xi_for_phase(int ph, float xi, float growth, float cap) {
+    return ph == PH_OUTER ? fminf(growth * xi, cap) : xi;
+}
+
+// ------------------------------------------------------------ DALM epilogues
+// Algorithm 2 (§V-B) with B = [A I] (CAB) or B = A (P1).  Panel U holds
+// z_{k+1} - w_k/beta, so the right-hand side of Eq. 39 is
+//   B z_{k+1} - (B w_k - b)/beta = A U_x (+ U_e) + b/beta.
+
+// G1: R = A U_x (+ U_e) + b / beta
+struct EpiDalmRhs {
+    static constexpr int NRED = 0;
+    float* R;
+    const float* Ue;
+    const float* B;
+    const float* binv;
+    const int32_t* active;
+    int64_t ldm;
+    int cab;
+    __device__ void operator()(int i, int j, float acc, double*) const {
+        if (!active[j]) return;
+        const int64_t o = (int64_t)j * ldm + i;
+        float v = fmaf(B[o], binv[j], acc);
+        if (cab) v += Ue[o];
+        R[o] = v;
+    }
+};
+
+// G2: y_{k+1} = (B B^T)^{-1} R; for CAB the identity block of B^T y_{k+1}
+// is y_{k+1} itself, so the e-part of the w-step and the next z - w/beta
+// are formed here:  z_e = U_e + w_e/beta,  w_e' = w_e - beta (z_e - y),
+// U_e' = clamp(y + w_e'/beta) - w_e'/beta.  red: ||dw_e||^2, ||w_e||^2.
+struct EpiDalmY {
+    static constexpr int NRED = 2;
+    float* Y;
+    float* We;
+    float* Ue;
+    const float* beta;
+    const float* binv;
+    const int32_t* active;
+    int64_t ldm;
+    int cab;
+    __device__ void operator()(int i, int j, float acc, double* red) const {
+        if (!active[j]) return;
+        const int64_t o = (int64_t)j * ldm + i;
+        Y[o] = acc;
+        if (!cab) return;
+        const float bi = binv[j], be = beta[j];
+        const float we = We[o];
+        const float z = fmaf(we, bi, Ue[o]);
+        const float dw = -be * (z - acc);
+        const float wn = we + dw;
+        We[o] = wn;
+        const float wb = wn * bi;
+        Ue[o] = clamp_unit(acc + wb) - wb;
+        red[0] += (double)dw * dw;
+        red[1] += (double)we * we;
+    }
+};
+
+// G3: s = A^T y_{k+1}; the x-part of the w-step and the next z - w/beta.
+// red: ||dw_x||^2, ||w_x||^2.
+struct EpiDalmS {
+    static constexpr int NRED = 2;
+    float* Wx;
+    float* Ux;
+    const float* beta;
+    const float* binv;
+    const int32_t* active;
+    int64_t ldn;
+    __device__ void operator()(int i, int j, float acc, double* red) const {
+        if (!active[j]) return;
+        const int64_t o = (int64_t)j * ldn + i;
+        const float bi = binv[j], be = beta[j];
+        const float w = Wx[o];
+        const float z = fmaf(w, bi, Ux[o]);
+        const float dw = -be * (z - acc);
+        const float wn = w + dw;
+        Wx[o] = wn;
+        const float wb = wn * bi;
+        Ux[o] = clamp_unit(acc + wb) - wb;
+        red[0] += (double)dw * dw;
+        red[1] += (double)w * w;
+    }
+};
+
+// ------------------------------------------------------------ PALM epilogues
+// Algorithm 1 (§V-A) as a per-column state machine over two sweeps per inner
+// FISTA step:  G_A: A V  (V = z_l, or x_{k+1} at an outer step),
+//              G_At: A^T R.
+struct PalmParams {
+    int mode;       // L1_P1, L1_CAB or L1_QP_LAMBDA
+    float growth;   // xi schedule growth (1 for CAB and QP)
+    float Linv;     // 1 / L
+};
+
+// G_A epilogue.  Inner phase: r = c - A z_l.  Outer phase (acc = A x_{k+1}):
+// step 8 of the previous outer iteration theta += xi (b - A x - e), then the
+// schedule xi -> xi', then step 3 e = shrink(b - A x + theta/xi', 1/xi'),
+// c = b - e + theta/xi' and the first inner residual r = c - A x.
+// red (outer phase only): ||e_{k+1} - e_k||^2, ||e_k||^2.
+struct EpiPalmA {
+    static constexpr int NRED = 2;
+    float* R;
+    float* Cc;
+    float* E;
+    float* TH;
+    const float* B;
+    Cols c;
+    PalmParams p;
+    int64_t ldm;
+    __device__ void operator()(int i, int j, float acc, double* red) const {
+        if (!c.active[j]) return;
+        const int64_t o = (int64_t)j * ldm + i;
+        const int ph = c.phase[j];
+        if (ph == PH_INNER) {
+            R[o] = Cc[o] - acc;
+            return;
+        }
+        const float xi = c.xi[j];
+        const float b = B[o];
+        float th = TH[o];
+        const float e_old = E[o];
+        if (ph == PH_OUTER) th = fmaf(xi, b - acc - e_old, th);
+        const float xin = xi_for_phase(ph, xi, p.growth, c.xicap[j]);
+        const float thx = th / xin;
+        float e_new = 0.0f;
+        if (p.mode == L1_CAB) e_new = soft_thr(b - acc + thx, 1.0f / xin);
+        TH[o] = th;
+        E[o] = e_new;
+        const float cc = b - e_new + thx;
+        Cc[o] = cc;
+        R[o] = cc - acc;
+        const float de = e_new - e_old;
+        red[0] += (double)de * de;
+        red[1] += (double)e_old * e_old;
+    }
+};
+
+// G_At epilogue: one FISTA step of Algorithm 1 steps 6-7 (Eq. 18 for QP):
+//   w' = shrink(z + g/L, 1/(xi L)), z' = w' + mu (w' - w),   g = A^T r.
+// red: ||w' - w||^2, ||w||^2, ||w' - x_k||^2, ||x_k||^2.
+struct EpiPalmAt {
+    static constexpr int NRED = 4;
+    float* W;
+    float* V;
+    const float* X;
+    Cols c;
+    PalmParams p;
+    int64_t ldn;
+    __device__ void operator()(int i, int j, float acc, double* red) const {
+        if (!c.active[j]) return;
+        const int64_t o = (int64_t)j * ldn + i;
+        const int ph = c.phase[j];
+        const float xin = xi_for_phase(ph, c.xi[j], p.growth, c.xicap[j]);
+        const float thr = p.Linv / xin;
+        const float z = V[o], w = W[o], x = X[o];
+        const float wn = soft_thr(fmaf(acc, p.Linv, z), thr);
+        const float mu = c.mu[j];
+        const float dw = wn - w;
+        W[o] = wn;
+        V[o] = fmaf(mu, dw, wn);
+        const float dx = wn - x;
+        red[0] += (double)dw * dw;
+        red[1] += (double)w * w;
+        red[2] += (double)dx * dx;
+        red[3] += (double)x * x;
+    }
+};
+
+// ------------------------------------------------------------- controllers
+// One 128-thread block per column: sums the row-block partials in index
+// order, applies the stopping rules, and (PALM) restarts FISTA.
+
+__device__ __forceinline__ double block_sum_128(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) s = sh[0] + sh[1] + sh[2] + sh[3];
+    return s;  // valid in thread 0
+}
+
+// sum of part[p][j][r] over p < np, in a fixed order
+__device__ __forceinline__ double sum_parts(const double* part, int np, int N, int j, int r,
+                                            double* sh) {
+    double v = 0.0;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) v += part[((int64_t)p * N + j) * kPartStride + r];
+    return block_sum_128(v, sh);
+}
+
+__global__ void ctrl_dalm_kernel(Cols c, const double* part_e, int np_e, const double* part_x,
+                                 int np_x, double tol, int max_iter) {
+    __shared__ double sh[4];
+    const int j = blockIdx.x;
+    if (!c.active[j]) return;
+    double d2 = sum_parts(part_x, np_x, c.N, j, 0, sh);
+    double w2 = sum_parts(part_x, np_x, c.N, j, 1, sh);
+    if (part_e) {
+        d2 += sum_parts(part_e, np_e, c.N, j, 0, sh);
+        w2 += sum_parts(part_e, np_e, c.N, j, 1, sh);
+    }
+    if (threadIdx.x != 0) return;
+    const int it = c.iters[j] + 1;
+    c.iters[j] = it;
+    c.inner[j] = it;
+    const double rel = rel_change(sqrt(d2), sqrt(w2));
+    c.rel[j] = rel;
+    if (!isfinite(d2) || !isfinite(w2)) {
+        c.status[j] = L1_NONFINITE;
+        c.active[j] = 0;
+    } else if (rel < tol) {
+        c.status[j] = L1_CONVERGED;
+        c.active[j] = 0;
+    } else if (it >= max_iter) {
+        c.status[j] = L1_MAX_ITER;
+        c.active[j] = 0;
+    }
+}
+
+// PALM / FISTA controller (after G_At).  Outer rule of §VI-C on w = [x; e];
+// inner rule: ||w_{l+1} - w_l|| <= inner_tol ||w_l|| or inner_max steps.
+// Restarting FISTA (t = 1, z = w = x_{k+1}) copies W into X and V.
+__global__ void ctrl_palm_kernel(Cols c, PalmParams p, const double* part_A, int np_A,
+                                 const double* part_At, int np_At, float* W, float* X, float* V,
+                                 int64_t ldn, int n, double tol, double inner_tol, int inner_max,
+                                 int max_iter) {
+    __shared__ double sh[4];
+    __shared__ int restart;
+    const int j = blockIdx.x;
+    if (!c.active[j]) return;
+    const int ph = c.phase[j];
+    double de2 = 0.0, e2 = 0.0;
+    if (ph != PH_INNER && p.mode != L1_QP_LAMBDA) {
+        de2 = sum_parts(part_A, np_A, c.N, j, 0, sh);
+        e2 = sum_parts(part_A, np_A, c.N, j, 1, sh);
+    }
+    const double d2 = sum_parts(part_At, np_At, c.N, j, 0, sh);
+    const double w2 = sum_parts(part_At, np_At, c.N, j, 1, sh);
+    const double dx2 = sum_parts(part_At, np_At, c.N, j, 2, sh);
+    const double x2 = sum_parts(part_At, np_At, c.N, j, 3, sh);
+    if (threadIdx.x == 0) {
+        restart = 0;
+        if (ph != PH_INNER) {
+            c.xi[j] = xi_for_phase(ph, c.xi[j], p.growth, c.xicap[j]);
+            c.phase[j] = PH_INNER;
+            c.de2[j] = de2;
+            c.e2[j] = e2;
+        }
+        const int l = c.l[j] + 1;
+        c.l[j] = l;
+        const int tot = c.inner[j] + 1;
+        c.inner[j] = tot;
+        const double t = c.t[j];
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        const double tnn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tn * tn));
+        c.t[j] = tn;
+        c.mu[j] = (float)((tn - 1.0) / tnn);
+        const bool finite = isfinite(d2) && isfinite(w2);
+        if (p.mode == L1_QP_LAMBDA) {
+            // FISTA of Eq. 18: one loop, the outer rule applies to x_k
+            c.iters[j] = tot;
+            const double rel = rel_change(sqrt(d2), sqrt(w2));
+            c.rel[j] = rel;
+            if (!finite) { c.status[j] = L1_NONFINITE; c.active[j] = 0; }
+            else if (rel < tol) { c.status[j] = L1_CONVERGED; c.active[j] = 0; }
+            else if (tot >= max_iter) { c.status[j] = L1_MAX_ITER; c.active[j] = 0; }
+        } else {
+            const double d = sqrt(d2), base = sqrt(w2);
+            const bool inner_done = d == 0.0 || (base > 0.0 && d <= inner_tol * base) || l >= inner_max;
+            if (!finite) {
+                c.status[j] = L1_NONFINITE;
+                c.active[j] = 0;
+            } else if (inner_done) {
+                const int k = c.iters[j] + 1;
+                c.iters[j] = k;
+                const double rel = rel_change(sqrt(dx2 + c.de2[j]), sqrt(x2 + c.e2[j]));
+                c.rel[j] = rel;
+                if (rel < tol) { c.status[j] = L1_CONVERGED; c.active[j] = 0; }
+                else if (k >= max_iter) { c.status[j] = L1_MAX_ITER; c.active[j] = 0; }
+                else {
+                    c.phase[j] = PH_OUTER;
+                    c.l[j] = 0;
+                    c.t[j] = 1.0;
+                    c.mu[j] = 0.0f;  // t_1 = 1: the first step has no momentum
+                    restart = 1;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (restart) {
+        const int64_t o = (int64_t)j * ldn;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const float w = W[o + i];
+            X[o + i] = w;
+            V[o + i] = w;
+        }
+    }
+}
+
+// number of columns still active -> *count
+__global__ void count_active_kernel(const int32_t* active, int N, int32_t* count) {
+    __shared__ int sh[32];
+    int v = 0;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) v += active[j] != 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        *count = s;
+    }
+}
+
+// ------------------------------------------------------------- finalisation
+// F1 (rows of A, acc = A x): r = b - A x - e.  PALM applies its last
+// multiplier step theta += xi r (Algorithm 1 step 8) so the dual estimate
+// matches the returned x.  QP keeps r in R for the dual point.
+// red: ||r||^2, b^T y (P1/CAB) or b^T r (QP), ||e||_1, ||y||^2 (unused).
+struct EpiFinalA {
+    static constexpr int NRED = 3;
+    float* R;
+    float* Y;
+    const float* E;  // nullable
+    const float* B;
+    const float* xi; // PALM only (nullable)
+    float* smax;     // CAB: max |y| (the identity block of B^T y)
+    int64_t ldm;
+    int mode;
+    __device__ void operator()(int i, int j, float acc, double* red) const {
+        const int64_t o = (int64_t)j * ldm + i;
+        const float b = B[o];
+        const float e = E ? E[o] : 0.0f;
+        const float r = b - acc - e;
+        red[0] += (double)r * r;
+        red[2] += fabs((double)e);
+        if (mode == L1_QP_LAMBDA) {
+            R[o] = r;
+            red[1] += (double)b * r;
+            return;
+        }
+        float y = Y[o];
+        if (xi) {
+            y = fmaf(xi[j], r, y);
+            Y[o] = y;
+        }
+        red[1] += (double)b * y;
+        if (mode == L1_CAB) atomicMax(reinterpret_cast<int*>(smax + j), __float_as_int(fabsf(y)));
+    }
+};
+
+// F2 (rows of A^T, acc = A^T y or A^T r): max |acc|, ||x||_1.
+struct EpiFinalAt {
+    static constexpr int NRED = 1;
+    const float* Wx;
+    float* smax;
+    int64_t ldn;
+    __device__ void operator()(int i, int j, float acc, double* red) const {
+        atomicMax(reinterpret_cast<int*>(smax + j), __float_as_int(fabsf(acc)));
+        red[0] += fabs((double)Wx[(int64_t)j * ldn + i]);
+    }
+};
+
+// fin[j][0..7] = primal, dual, gap, resid, x1, e1, -, -
+__global__ void final_metrics_kernel(Cols c, const double* part_A, int np_A, const double* part_At,
+                                     int np_At, int mode, double lambda) {
+    __shared__ double sh[4];
+    const int j = blockIdx.x;
+    const double r2 = sum_parts(part_A, np_A, c.N, j, 0, sh);
+    const double by = sum_parts(part_A, np_A, c.N, j, 1, sh);
+    const double e1 = sum_parts(part_A, np_A, c.N, j, 2, sh);
+    const double x1 = sum_parts(part_At, np_At, c.N, j, 0, sh);
+    if (threadIdx.x != 0) return;
+    const double smax = (double)c.smax[j];
+    double primal, dual;
+    if (mode == L1_QP_LAMBDA) {
+        // dual of Eq. 3: max b^T u - 1/2||u||^2 s.t. ||A^T u||_inf <= lambda,
+        // feasible point u = s r with s = min(1, lambda / ||A^T r||_inf)
+        primal = 0.5 * r2 + lambda * x1;
+        const double s = smax > 0.0 ? fmin(1.0, lambda / smax) : 1.0;
+        dual = s * by - 0.5 * s * s * r2;
+    } else {
+        // dual of Eq. 1 / Eq. 5: max b^T y s.t. ||B^T y||_inf <= 1 (§V-B),
+        // made feasible by scaling
+        primal = x1 + e1;
+        dual = by / fmax(1.0, smax);
+    }
+    double* f = c.fin + (int64_t)j * 8;
+    f[0] = primal;
+    f[1] = dual;
+    f[2] = primal - dual;
+    f[3] = sqrt(r2);
+    f[4] = x1;
+    f[5] = e1;
+}
+
+// ----------------------------------------------------------- classification
+// Per-class residual ||b - e - A delta_c(x)||_2 (§II-A) and the l1 mass
+// ||delta_c(x)||_1 of the SCI rule (Eq. 40); one block per (class, column).
+// A is read row-major so a class's columns in one row are contiguous.
+__global__ void classify_resid_kernel(const float* A_rm, int64_t lda_rm, int m,
+                                      const int32_t* offsets, const float* B, const float* E,
+                                      const float* Wx, int64_t ldm, int64_t ldn, int N,
+                                      double* resid2, double* l1mass) {
+    __shared__ double sh[8];
+    const int cls = blockIdx.x, j = blockIdx.y;
+    const int c0 = offsets[cls], c1 = offsets[cls + 1];
+    const float* x = Wx + (int64_t)j * ldn;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const float* arow = A_rm + (int64_t)i * lda_rm;
+        double s = 0.0;
+        for (int k = c0; k < c1; ++k) s += (double)arow[k] * (double)x[k];
+        const double v = (double)B[(int64_t)j * ldm + i] - (E ? (double)E[(int64_t)j * ldm + i] : 0.0) - s;
+        acc += v * v;
+    }
+    double l1v = 0.0;
+    for (int k = c0 + threadIdx.x; k < c1; k += blockDim.x) l1v += fabs((double)x[k]);
+    // block reductions (fixed order)
+    acc = warp_sum(acc);
+    l1v = warp_sum(l1v);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sh[w] = acc; sh[4 + w] = l1v; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        resid2[(int64_t)cls * N + j] = sh[0] + sh[1] + sh[2] + sh[3];
+        l1mass[(int64_t)cls * N + j] = sh[4] + sh[5] + sh[6] + sh[7];
+    }
+}
+
+__global__ void classify_argmin_kernel(const double* resid2, const double* l1mass, int C, int N,
+                                       int32_t* label, int32_t* sci_label) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    int best = 0, bsci = 0;
+    double br = resid2[j], bl = l1mass[j];
+    for (int cls = 1; cls < C; ++cls) {
+        const double r = resid2[(int64_t)cls * N + j];
+        const double l = l1mass[(int64_t)cls * N + j];
+        if (r < br) { br = r; best = cls; }
+        if (l > bl) { bl = l; bsci = cls; }
+    }
+    label[j] = best;
+    sci_label[j] = bsci;
+}
+
+}  // namespace l1

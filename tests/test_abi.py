@@ -1,0 +1,101 @@
+"""The C-ABI library on the host: it builds, loads, exports every symbol the
+header declares, the ctypes mirrors of its structs have the C layout, and
+argument checks that fire before any CUDA call behave as documented."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1007_3753_gb300 as l1
+from paper_1007_3753_gb300 import build as l1build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "l1alm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    l1build.build()
+    return l1.load()
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"L1_API\s+[\w\s\*]+?\b(l1_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert names == sorted(l1.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", l1.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = sorted(set(re.findall(r"\sT\s(l1_\w+)", out)))
+    assert exported == names
+    for nm_ in names:
+        assert hasattr(lib, nm_)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "probe.c"
+    prog.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "l1alm.h"
+int main(void) {
+  printf("%zu %zu %zu\n", sizeof(l1_options), sizeof(l1_result), sizeof(l1_info));
+  printf("%zu %zu %zu %zu\n", offsetof(l1_options, lambda), offsetof(l1_options, class_offsets),
+         offsetof(l1_options, stream), offsetof(l1_options, unroll_K));
+  printf("%zu %zu\n", offsetof(l1_result, rel_change), offsetof(l1_result, param));
+  return 0;
+}
+''')
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                        check=True).stdout.split()))
+    assert vals[:3] == [C.sizeof(l1.Options), C.sizeof(l1.Result), C.sizeof(l1.Info)]
+    assert vals[3:7] == [l1.Options.lambda_.offset, l1.Options.class_offsets.offset,
+                         l1.Options.stream.offset, l1.Options.unroll_K.offset]
+    assert vals[7:] == [l1.Result.rel_change.offset, l1.Result.param.offset]
+
+
+def test_host_side_argument_checks(lib):
+    o = l1.Options()
+    lib.l1_options_init(C.byref(o))
+    assert o.solver == l1.DALM and o.inner_max == 50 and o.check_every == 16
+    h = C.c_void_p()
+    A = np.ones((4, 8), dtype=np.float32, order="F")
+    # null A, bad sizes, lda < m, unknown mode: rejected before any CUDA call
+    assert lib.l1_setup(None, 4, 8, 4, l1.P1, C.byref(o), C.byref(h)) == l1.ERR_INVALID_ARG
+    assert lib.l1_setup(A.ctypes.data, 0, 8, 4, l1.P1, C.byref(o), C.byref(h)) == l1.ERR_INVALID_ARG
+    assert lib.l1_setup(A.ctypes.data, 4, 8, 3, l1.P1, C.byref(o), C.byref(h)) == l1.ERR_INVALID_ARG
+    assert lib.l1_setup(A.ctypes.data, 4, 8, 4, 9, C.byref(o), C.byref(h)) == l1.ERR_INVALID_ARG
+    o.lambda_ = 0.0
+    assert lib.l1_setup(A.ctypes.data, 4, 8, 4, l1.QP_LAMBDA, C.byref(o), C.byref(h)) == l1.ERR_INVALID_ARG
+    off = np.array([0, 3, 8], dtype=np.int32)
+    o.class_count = 2
+    o.class_offsets = off.ctypes.data_as(C.POINTER(C.c_int32))
+    bad = np.array([0, 5, 7], dtype=np.int32)  # does not end at n
+    o.class_offsets = bad.ctypes.data_as(C.POINTER(C.c_int32))
+    assert lib.l1_setup(A.ctypes.data, 4, 8, 4, l1.CAB, C.byref(o), C.byref(h)) == l1.ERR_INVALID_ARG
+    assert not h.value
+    res = (l1.Result * 1)()
+    assert lib.l1_solve_batch(None, None, 4, 1, 1e-6, 10, None, 8, None, 0, res) == l1.ERR_INVALID_ARG
+    assert lib.l1_backward(None, None, 1, None, None) == l1.ERR_INVALID_ARG
+    assert lib.l1_destroy(None) == l1.OK
+    assert lib.l1_status_string(l1.ERR_NOT_SPD) == b"L1_ERR_NOT_SPD"
+    assert lib.l1_status_string(l1.ERR_UNSUPPORTED) == b"L1_ERR_UNSUPPORTED"
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The package never imports the oracle and has no host compute path."""
+    pkg = os.path.join(ROOT, "paper_1007_3753_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "l1_oracle" not in src, f
