@@ -154,7 +154,7 @@ L1_API int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t m
 
 /*
  * l1_solve_batch -- solve N independent problems that share A, one per
- * column of b (m x N, leading dimension ldb >= m).
+ * column of b (m x N, leading dimension ldb >= m), 1 <= N <= 65535.
  *   tol       stopping tolerance of the relative-change rule (§VI-C); 0 runs
  *             exactly max_iter iterations.
  *   max_iter  cap on outer iterations (PALM) or iterations (DALM, FISTA).

@@ -39,7 +39,7 @@ static void free_all(Handle* h) {
     else cudaDeviceSynchronize();
     for (void* p : h->allocations) cudaFree(p);
     h->allocations.clear();
-    if (h->ws.h_active) cudaFreeHost(h->ws.h_active);
+    if (h->ws.h_count) cudaFreeHost(h->ws.h_count);
     h->ws = Workspace{};
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
@@ -154,6 +154,8 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
         if (o.solver == L1_DALM && mode != L1_QP_LAMBDA) {
             rc = dev_alloc_t(h, &h->F, (size_t)h->ldm * m);
             if (rc) break;
+            rc = dev_alloc_t(h, &h->F_lo, (size_t)h->ldm * m);
+            if (rc) break;
             rc = dalm_factor(h, mode == L1_CAB ? 1.0 : 0.0);
             if (rc) break;
         }
@@ -188,7 +190,7 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
 int l1_solve_batch(l1_handle hh, const float* b, int64_t ldb, int64_t N, double tol, int32_t max_iter, float* x,
                    int64_t ldx, float* y, int64_t ldy, l1_result* res) {
     Handle* h = reinterpret_cast<Handle*>(hh);
-    if (!h || !b || !x || !res || N <= 0 || N > (1 << 20) || max_iter <= 0 || !(tol >= 0.0)) return L1_ERR_INVALID_ARG;
+    if (!h || !b || !x || !res || N <= 0 || N > 65535 || max_iter <= 0 || !(tol >= 0.0)) return L1_ERR_INVALID_ARG;
     if (ldb < h->m) return L1_ERR_INVALID_ARG;
     const int64_t nx = (h->mode == L1_CAB) ? h->n + h->m : h->n;
     if (ldx < nx) return L1_ERR_INVALID_ARG;

@@ -59,26 +59,39 @@ struct DevBuf {
 // Column phases of the batched PALM state machine.
 enum PalmPhase : int32_t { PH_INNER = 0, PH_OUTER = 1, PH_FIRST = 2 };
 
-struct Workspace {
-    int64_t cap_N = 0;  // columns the panels are sized for
-    // panels (column-major; ldm = padded m, ldn = padded n)
+// Iteration state carried from one sweep to the next, one problem per
+// column ("slot"); compaction moves the active slots to the front of the
+// other set of the double buffer.
+struct PanelSet {
     float* B = nullptr;   // right-hand sides, m x N
     float* Wx = nullptr;  // DALM multiplier x-part / PALM w (current FISTA iterate)
     float* We = nullptr;  // DALM multiplier e-part / PALM e
-    float* Ux = nullptr;  // DALM z - w/beta (x-part) / PALM z (FISTA extrapolation, B operand)
+    float* Ux = nullptr;  // DALM z - w/beta (x-part) / PALM z (FISTA extrapolation)
     float* Ue = nullptr;  // DALM z - w/beta (e-part)
-    float* R = nullptr;   // DALM right-hand side of Eq. 39 / PALM residual c - A z
     float* Y = nullptr;   // DALM y / PALM theta
     float* X = nullptr;   // PALM outer x_k
     float* Cc = nullptr;  // PALM c = b - e + theta/xi
-    float* S = nullptr;   // scratch n x N (finalize)
-    // per column
-    double* part = nullptr;   // reduction partials, [slots][N][4]
-    double* colstat = nullptr; // [N][8] per-column doubles (see solver.cu)
-    float* colf = nullptr;    // [N][8] per-column floats (beta, 1/beta, xi, t, ...)
-    int32_t* coli = nullptr;  // [N][8] per-column ints (active, status, iters, ...)
-    int32_t* active_count = nullptr;  // device counter
-    int32_t* h_active = nullptr;      // pinned host mirror
+    float* colf = nullptr;     // per-slot floats  [8][cap]
+    int32_t* coli = nullptr;   // per-slot ints    [16][cap]
+    double* cold = nullptr;    // per-slot doubles [8][cap]
+};
+
+struct Workspace {
+    int64_t cap_N = 0;  // columns the buffers are sized for
+    PanelSet ps[2];
+    float* R = nullptr;   // DALM right-hand side of Eq. 39 / PALM residual c - A z (scratch)
+    // results in the caller's column order ("home")
+    float* hB = nullptr;
+    float* hWx = nullptr;
+    float* hWe = nullptr;
+    float* hY = nullptr;
+    int32_t* hcoli = nullptr;  // [8][cap]: status, iters, inner, label, sci_label
+    double* hcold = nullptr;   // [10][cap]: rel, param, fin[8] (interleaved per column)
+    float* hcolf = nullptr;    // [2][cap]: xi, smax
+    double* part = nullptr;    // reduction partials, 2 x [slots][N][4]
+    int32_t* newpos = nullptr;
+    int32_t* count = nullptr;  // device counter
+    int32_t* h_count = nullptr;  // pinned host mirror
     double* resid2 = nullptr;  // classification residuals, [C][N]
     double* classl1 = nullptr; // classification l1 mass, [C][N]
     int32_t* class_off = nullptr;
@@ -95,7 +108,8 @@ struct Handle {
     // dictionary
     float* A_cm = nullptr;  // column-major m x n, ld = ldm  (rows of A^T contiguous: K-major for A^T y)
     float* A_rm = nullptr;  // row-major m x n, ld = ldn     (K-major for A u)
-    float* F = nullptr;     // DALM: (B B^T)^{-1}, m x m symmetric, ld = ldm
+    float* F = nullptr;     // DALM: (B B^T)^{-1}, m x m symmetric, ld = ldm (high FP32 part)
+    float* F_lo = nullptr;  // low FP32 part: F + F_lo = (B B^T)^{-1} to ~48 bits
     double lipschitz = 0.0;
     double setup_ms = 0.0;
     int64_t device_bytes = 0;

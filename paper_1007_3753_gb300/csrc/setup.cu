@@ -225,12 +225,18 @@ __global__ void trinv_scale_kernel(const double* Lf, double* X, int m) {
     X[idx] = (r >= c) ? X[idx] / Lf[r * m + r] : 0.0;
 }
 
-__global__ void to_f32_kernel(const double* src, int m, float* dst, int64_t ldd) {
+// FP64 -> FP32 pair: hi = fl32(v), lo = fl32(v - hi), so hi + lo carries
+// about 48 bits of v.  The y-step of DALM multiplies by (B B^T)^{-1}, whose
+// condition number amplifies the rounding of a plain FP32 copy.
+__global__ void to_f32_split_kernel(const double* src, int m, float* hi, float* lo, int64_t ldd) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = ldd * m;
     if (idx >= total) return;
     const int64_t c = idx / ldd, r = idx % ldd;
-    dst[idx] = (r < m) ? (float)src[c * m + r] : 0.0f;
+    const double v = (r < m) ? src[c * m + r] : 0.0;
+    const float h = (float)v;
+    hi[idx] = h;
+    lo[idx] = (float)(v - (double)h);
 }
 
 int dalm_factor(Handle* h, double diag_add) {
@@ -278,7 +284,7 @@ int dalm_factor(Handle* h, double diag_add) {
         // F(i, k) = sum_j Linv(j, i) Linv(j, k): X(i, j) = Linv(j, i) = X[i*m + j]
         syrk64_kernel<double><<<g16, dim3(16, 16), 0, s>>>(X, m, 1, m, m, G, m, 0.0);
         ++h->launches;
-        to_f32_kernel<<<(unsigned)((h->ldm * m + 255) / 256), 256, 0, s>>>(G, m, h->F, h->ldm);
+        to_f32_split_kernel<<<(unsigned)((h->ldm * m + 255) / 256), 256, 0, s>>>(G, m, h->F, h->F_lo, h->ldm);
         ++h->launches;
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -1,5 +1,6 @@
 // Host driver of l1_solve_batch: per-column state, the PALM / DALM / FISTA
-// sweep sequences, finalisation and classification.
+// sweep sequences, convergence masking and compaction, finalisation and
+// classification.
 #include <algorithm>
 #include <cstring>
 
@@ -12,10 +13,9 @@ namespace l1 {
 
 namespace {
 
-// l1_result as written by the device (identical layout)
 static_assert(sizeof(l1_result) == 6 * 4 + 6 * 8, "l1_result layout");
 
-__global__ void init_cols_kernel(Cols c, const float* B, int64_t ldm, int m, int mode, int solver,
+__global__ void init_cols_kernel(Cols c, const float* B, int64_t ldm, int m, int mode,
                                  double beta_opt, double xi0_opt, double xi_max, double lambda) {
     __shared__ double sh[4];
     const int j = blockIdx.x;
@@ -43,53 +43,54 @@ __global__ void init_cols_kernel(Cols c, const float* B, int64_t ldm, int m, int
     c.inner[j] = 0;
     c.phase[j] = PH_FIRST;
     c.l[j] = 0;
-    c.label[j] = -1;
-    c.sci_label[j] = -1;
     c.rel[j] = INFINITY;
     c.de2[j] = 0.0;
     c.e2[j] = 0.0;
-    c.smax[j] = 0.0f;
-    (void)solver;
+    c.orig[j] = j;
 }
 
-__global__ void pack_results_kernel(Cols c, l1_result* out, int solver, int mode, double Linv,
-                                    double lambda) {
+struct HomeRes {
+    int32_t* status;
+    int32_t* iters;
+    int32_t* inner;
+    int32_t* label;
+    int32_t* sci_label;
+    double* rel;
+    double* param;
+    double* fin;  // [N][8]
+    float* xi;
+    float* smax;
+};
+
+__global__ void pack_results_kernel(HomeRes hr, int N, l1_result* out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= c.N) return;
+    if (j >= N) return;
     l1_result r;
-    r.status = c.status[j];
-    r.iters = c.iters[j];
-    r.inner_iters = c.inner[j];
-    r.label = c.label[j];
-    r.sci_label = c.sci_label[j];
+    r.status = hr.status[j];
+    r.iters = hr.iters[j];
+    r.inner_iters = hr.inner[j];
+    r.label = hr.label[j];
+    r.sci_label = hr.sci_label[j];
     r.reserved = 0;
-    r.rel_change = c.rel[j];
-    const double* f = c.fin + (int64_t)j * 8;
+    r.rel_change = hr.rel[j];
+    const double* f = hr.fin + (int64_t)j * 8;
     r.primal_obj = f[0];
     r.dual_obj = f[1];
     r.gap = f[2];
     r.resid = f[3];
-    if (mode == L1_QP_LAMBDA) r.param = lambda * Linv;
-    else if (solver == L1_DALM) r.param = c.beta[j];
-    else r.param = 0.0;  // filled from xi0 below
+    r.param = hr.param[j];
     out[j] = r;
 }
 
-__global__ void store_xi0_kernel(Cols c, l1_result* out, const float* xi0) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < c.N) out[j].param = xi0[j];
+__global__ void fill_i32_kernel(int32_t* p, int n, int32_t v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
 }
 
-bool is_device_ptr(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+__global__ void set_param_kernel(double* param, int n, double v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) param[i] = v;
 }
-
-}  // namespace
 
 // CUDA-event timing of each sweep (l1_options.profile): the events of one
 // polling chunk are read back after the chunk's host synchronisation.
@@ -136,43 +137,58 @@ struct SweepProf {
     }
 };
 
+}  // namespace
+
 static int ensure_workspace(Handle* h, int N) {
     Workspace& w = h->ws;
     if (w.cap_N >= N) return L1_OK;
-    // release the old panels (they are recorded in h->allocations)
-    auto release = [&](void* p) {
-        if (!p) return;
+    // release the old buffers (recorded in h->allocations)
+    std::vector<void*> old;
+    for (int q = 0; q < 2; ++q) {
+        PanelSet& p = w.ps[q];
+        old.insert(old.end(), {p.B, p.Wx, p.We, p.Ux, p.Ue, p.Y, p.X, p.Cc, p.colf, p.coli, p.cold});
+    }
+    old.insert(old.end(), {w.R, w.hB, w.hWx, w.hWe, w.hY, w.hcoli, w.hcold, w.hcolf, w.part, w.newpos,
+                           w.count, w.resid2, w.classl1, w.class_off});
+    for (void* p : old) {
+        if (!p) continue;
         cudaFree(p);
         auto it = std::find(h->allocations.begin(), h->allocations.end(), p);
         if (it != h->allocations.end()) h->allocations.erase(it);
-    };
-    release(w.B); release(w.Wx); release(w.We); release(w.Ux); release(w.Ue); release(w.R);
-    release(w.Y); release(w.X); release(w.Cc); release(w.part); release(w.colstat);
-    release(w.colf); release(w.coli); release(w.active_count); release(w.resid2);
-    release(w.classl1); release(w.class_off);
-    if (w.h_active) { cudaFreeHost(w.h_active); w.h_active = nullptr; }
+    }
+    if (w.h_count) cudaFreeHost(w.h_count);
     w = Workspace{};
     const int64_t ldm = h->ldm, ldn = h->ldn;
     const int m = (int)h->m, n = (int)h->n;
-    L1_TRY(dev_alloc_t(h, &w.B, ldm * N));
-    L1_TRY(dev_alloc_t(h, &w.Wx, ldn * N));
-    L1_TRY(dev_alloc_t(h, &w.We, ldm * N));
-    L1_TRY(dev_alloc_t(h, &w.Ux, ldn * N));
-    L1_TRY(dev_alloc_t(h, &w.Ue, ldm * N));
+    for (int q = 0; q < 2; ++q) {
+        PanelSet& p = w.ps[q];
+        L1_TRY(dev_alloc_t(h, &p.B, ldm * N));
+        L1_TRY(dev_alloc_t(h, &p.Wx, ldn * N));
+        L1_TRY(dev_alloc_t(h, &p.We, ldm * N));
+        L1_TRY(dev_alloc_t(h, &p.Ux, ldn * N));
+        L1_TRY(dev_alloc_t(h, &p.Ue, ldm * N));
+        L1_TRY(dev_alloc_t(h, &p.Y, ldm * N));
+        L1_TRY(dev_alloc_t(h, &p.X, ldn * N));
+        L1_TRY(dev_alloc_t(h, &p.Cc, ldm * N));
+        L1_TRY(dev_alloc_t(h, &p.colf, (size_t)8 * N));
+        L1_TRY(dev_alloc_t(h, &p.coli, (size_t)16 * N));
+        L1_TRY(dev_alloc_t(h, &p.cold, (size_t)8 * N));
+    }
     L1_TRY(dev_alloc_t(h, &w.R, ldm * N));
-    L1_TRY(dev_alloc_t(h, &w.Y, ldm * N));
-    L1_TRY(dev_alloc_t(h, &w.X, ldn * N));
-    L1_TRY(dev_alloc_t(h, &w.Cc, ldm * N));
+    L1_TRY(dev_alloc_t(h, &w.hB, ldm * N));
+    L1_TRY(dev_alloc_t(h, &w.hWx, ldn * N));
+    L1_TRY(dev_alloc_t(h, &w.hWe, ldm * N));
+    L1_TRY(dev_alloc_t(h, &w.hY, ldm * N));
+    L1_TRY(dev_alloc_t(h, &w.hcoli, (size_t)8 * N));
+    L1_TRY(dev_alloc_t(h, &w.hcold, (size_t)10 * N));
+    L1_TRY(dev_alloc_t(h, &w.hcolf, (size_t)2 * N));
     const int np = std::max(std::max(sweep_row_blocks(m, N), sweep_row_blocks(n, N)),
                             std::max(sweep_row_blocks(m, 1), sweep_row_blocks(n, 1)));
     w.part_slots = (size_t)np;
-    // two partial buffers: one for sweeps over the m rows, one over the n rows
     L1_TRY(dev_alloc_t(h, &w.part, 2 * (size_t)np * N * kPartStride));
-    L1_TRY(dev_alloc_t(h, &w.colstat, (size_t)N * 16));
-    L1_TRY(dev_alloc_t(h, &w.colf, (size_t)N * 8));
-    L1_TRY(dev_alloc_t(h, &w.coli, (size_t)N * 16));
-    L1_TRY(dev_alloc_t(h, &w.active_count, 1));
-    if (cudaMallocHost(&w.h_active, sizeof(int32_t)) != cudaSuccess) return L1_ERR_OOM;
+    L1_TRY(dev_alloc_t(h, &w.newpos, (size_t)N));
+    L1_TRY(dev_alloc_t(h, &w.count, 1));
+    if (cudaMallocHost(&w.h_count, sizeof(int32_t)) != cudaSuccess) return L1_ERR_OOM;
     const int C = (int)h->class_offsets.size() - 1;
     if (C > 0) {
         L1_TRY(dev_alloc_t(h, &w.resid2, (size_t)C * N));
@@ -185,32 +201,98 @@ static int ensure_workspace(Handle* h, int N) {
     return L1_OK;
 }
 
-static Cols make_cols(Handle* h, int N) {
-    Workspace& w = h->ws;
+static Cols make_cols(Handle* h, int q, int N) {
+    PanelSet& p = h->ws.ps[q];
+    const int64_t cap = h->ws.cap_N;
     Cols c{};
     c.N = N;
-    const int64_t cap = w.cap_N;
-    c.beta = w.colf + 0 * cap;
-    c.binv = w.colf + 1 * cap;
-    c.xi = w.colf + 2 * cap;
-    c.xicap = w.colf + 3 * cap;
-    c.mu = w.colf + 4 * cap;
-    c.smax = w.colf + 5 * cap;
-    c.active = w.coli + 0 * cap;
-    c.status = w.coli + 1 * cap;
-    c.iters = w.coli + 2 * cap;
-    c.inner = w.coli + 3 * cap;
-    c.phase = w.coli + 4 * cap;
-    c.l = w.coli + 5 * cap;
-    c.label = w.coli + 6 * cap;
-    c.sci_label = w.coli + 7 * cap;
-    c.t = w.colstat + 0 * cap;
-    c.rel = w.colstat + 1 * cap;
-    c.de2 = w.colstat + 2 * cap;
-    c.e2 = w.colstat + 3 * cap;
-    c.b1 = w.colstat + 4 * cap;
-    c.fin = w.colstat + 8 * cap;  // [N][8]
+    c.beta = p.colf + 0 * cap;
+    c.binv = p.colf + 1 * cap;
+    c.xi = p.colf + 2 * cap;
+    c.xicap = p.colf + 3 * cap;
+    c.mu = p.colf + 4 * cap;
+    c.active = p.coli + 0 * cap;
+    c.status = p.coli + 1 * cap;
+    c.iters = p.coli + 2 * cap;
+    c.inner = p.coli + 3 * cap;
+    c.phase = p.coli + 4 * cap;
+    c.l = p.coli + 5 * cap;
+    c.orig = p.coli + 6 * cap;
+    c.t = p.cold + 0 * cap;
+    c.rel = p.cold + 1 * cap;
+    c.de2 = p.cold + 2 * cap;
+    c.e2 = p.cold + 3 * cap;
+    c.b1 = p.cold + 4 * cap;
     return c;
+}
+
+static HomeRes make_home_res(Handle* h) {
+    Workspace& w = h->ws;
+    const int64_t cap = w.cap_N;
+    HomeRes r{};
+    r.status = w.hcoli + 0 * cap;
+    r.iters = w.hcoli + 1 * cap;
+    r.inner = w.hcoli + 2 * cap;
+    r.label = w.hcoli + 3 * cap;
+    r.sci_label = w.hcoli + 4 * cap;
+    r.rel = w.hcold + 0 * cap;
+    r.param = w.hcold + 1 * cap;
+    r.fin = w.hcold + 2 * cap;  // [cap][8]
+    r.xi = w.hcolf + 0 * cap;
+    r.smax = w.hcolf + 1 * cap;
+    return r;
+}
+
+static Home make_home(Handle* h) {
+    Workspace& w = h->ws;
+    HomeRes r = make_home_res(h);
+    Home hm{};
+    hm.N = (int)w.cap_N;
+    hm.Wx = w.hWx;
+    hm.We = w.hWe;
+    hm.Y = w.hY;
+    hm.status = r.status;
+    hm.iters = r.iters;
+    hm.inner = r.inner;
+    hm.rel = r.rel;
+    hm.param = r.param;
+    hm.xi = r.xi;
+    return hm;
+}
+
+// Move the active slots of set q to the front of set q^1 and write the
+// results of the others home; *n_out = number of active slots.
+static int compact(Handle* h, int q, int N_cur, int solver, double xi_max, int* n_out) {
+    Workspace& w = h->ws;
+    cudaStream_t s = h->stream;
+    Cols src = make_cols(h, q, N_cur), dst = make_cols(h, q ^ 1, N_cur);
+    Home hm = make_home(h);
+    compact_scan_kernel<<<1, 1024, 0, s>>>(src.active, N_cur, w.newpos, w.count);
+    L1_LAUNCH_CHECK(h);
+    const PanelSet &a = w.ps[q], &b = w.ps[q ^ 1];
+    struct P {
+        const float* src;
+        float* dst;
+        float* home;
+        int64_t ld;
+        int rows;
+    };
+    const int m = (int)h->m, n = (int)h->n;
+    const P panels[] = {{a.B, b.B, nullptr, h->ldm, m},  {a.Wx, b.Wx, w.hWx, h->ldn, n},
+                        {a.We, b.We, w.hWe, h->ldm, m},  {a.Ux, b.Ux, nullptr, h->ldn, n},
+                        {a.Ue, b.Ue, nullptr, h->ldm, m}, {a.Y, b.Y, w.hY, h->ldm, m},
+                        {a.X, b.X, nullptr, h->ldn, n},   {a.Cc, b.Cc, nullptr, h->ldm, m}};
+    for (const P& p : panels) {
+        dim3 grid((unsigned)std::min(8, (p.rows + 255) / 256), (unsigned)N_cur);
+        compact_panel_kernel<<<grid, 256, 0, s>>>(p.src, p.dst, p.home, p.ld, p.rows, N_cur, w.newpos, src.orig);
+        L1_LAUNCH_CHECK(h);
+    }
+    compact_cols_kernel<<<(N_cur + 255) / 256, 256, 0, s>>>(src, dst, hm, N_cur, w.newpos, solver, xi_max);
+    L1_LAUNCH_CHECK(h);
+    L1_CUDA_TRY(cudaMemcpyAsync(w.h_count, w.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    L1_CUDA_TRY(cudaStreamSynchronize(s));
+    *n_out = *w.h_count;
+    return L1_OK;
 }
 
 int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int max_iter,
@@ -224,158 +306,165 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     const int solver = (mode == L1_QP_LAMBDA) ? L1_PALM : h->opt.solver;
     const bool cab = mode == L1_CAB;
     const l1_options& o = h->opt;
-    Cols c = make_cols(h, N);
+    const double xi_max = o.xi_max > 0.0 ? o.xi_max : 1e4;
     double* part_m = w.part;
-    double* part_n = w.part + w.part_slots * (size_t)N * kPartStride;
+    double* part_n = w.part + w.part_slots * (size_t)w.cap_N * kPartStride;
 
-    // ---- inputs and initial state
-    L1_CUDA_TRY(cudaMemcpy2DAsync(w.B, ldm * sizeof(float), b, ldb * sizeof(float), m * sizeof(float),
+    // ---- inputs and initial state (set 0, slot j = column j)
+    int q = 0;
+    PanelSet* P = &w.ps[0];
+    L1_CUDA_TRY(cudaMemcpy2DAsync(w.hB, ldm * sizeof(float), b, ldb * sizeof(float), m * sizeof(float),
                                   N, cudaMemcpyDefault, s));
     const size_t pm = sizeof(float) * ldm * N, pn = sizeof(float) * ldn * N;
-    L1_CUDA_TRY(cudaMemsetAsync(w.Wx, 0, pn, s));
-    L1_CUDA_TRY(cudaMemsetAsync(w.Ux, 0, pn, s));
-    L1_CUDA_TRY(cudaMemsetAsync(w.X, 0, pn, s));
-    L1_CUDA_TRY(cudaMemsetAsync(w.Ue, 0, pm, s));
-    L1_CUDA_TRY(cudaMemsetAsync(w.Y, 0, pm, s));
-    L1_CUDA_TRY(cudaMemsetAsync(w.R, 0, pm, s));
-    L1_CUDA_TRY(cudaMemsetAsync(w.Cc, 0, pm, s));
+    L1_CUDA_TRY(cudaMemcpyAsync(P->B, w.hB, pm, cudaMemcpyDeviceToDevice, s));
+    L1_CUDA_TRY(cudaMemsetAsync(P->Wx, 0, pn, s));
+    L1_CUDA_TRY(cudaMemsetAsync(P->Ux, 0, pn, s));
+    L1_CUDA_TRY(cudaMemsetAsync(P->X, 0, pn, s));
+    L1_CUDA_TRY(cudaMemsetAsync(P->Ue, 0, pm, s));
+    L1_CUDA_TRY(cudaMemsetAsync(P->Y, 0, pm, s));
+    L1_CUDA_TRY(cudaMemsetAsync(P->Cc, 0, pm, s));
     if (solver == L1_PALM && cab) {
         // Algorithm 1 input: e_1 = b
-        L1_CUDA_TRY(cudaMemcpyAsync(w.We, w.B, pm, cudaMemcpyDeviceToDevice, s));
+        L1_CUDA_TRY(cudaMemcpyAsync(P->We, P->B, pm, cudaMemcpyDeviceToDevice, s));
     } else {
-        L1_CUDA_TRY(cudaMemsetAsync(w.We, 0, pm, s));
+        L1_CUDA_TRY(cudaMemsetAsync(P->We, 0, pm, s));
     }
-    const double xi_max = o.xi_max > 0.0 ? o.xi_max : 1e4;
-    init_cols_kernel<<<N, 128, 0, s>>>(c, w.B, ldm, m, mode, solver, o.beta, o.xi0, xi_max, o.lambda);
+    Cols c = make_cols(h, 0, N);
+    init_cols_kernel<<<N, 128, 0, s>>>(c, P->B, ldm, m, mode, o.beta, o.xi0, xi_max, o.lambda);
     L1_LAUNCH_CHECK(h);
 
     const int check_every = o.check_every > 0 ? o.check_every : 16;
-    int done_iters = 0;
     SweepProf prof{h, o.profile != 0};
     L1_TRY(prof.reserve(3 * check_every));
-    double n_act = N;  // columns active at the last poll (algorithmic FLOP count)
-    if (solver == L1_DALM) {
-        // Algorithm 2: three sweeps per iteration
-        while (true) {
-            for (int r = 0; r < check_every; ++r) {
-                prof.start(0, 2.0 * m * n * n_act);
-                int rc = launch_sweep(h, m, N, n, h->A_rm, ldn, w.Ux, ldn,
-                                      EpiDalmRhs{w.R, w.Ue, w.B, c.binv, c.active, ldm, cab ? 1 : 0},
+    int N_cur = N;  // slots in the current set; every active slot is < N_cur
+    PalmParams pp;
+    pp.mode = mode;
+    pp.growth = (mode == L1_CAB || mode == L1_QP_LAMBDA) ? 1.0f : (float)(o.xi_growth > 0.0 ? o.xi_growth : 1.2);
+    pp.Linv = h->lipschitz > 0.0 ? (float)(1.0 / h->lipschitz) : 0.0f;
+    const int inner_max = o.inner_max > 0 ? o.inner_max : 50;
+    const double inner_tol = o.inner_tol > 0.0 ? o.inner_tol : 0.1 * tol;
+    // host budget of sweep rounds: every column has stopped by then (max_iter)
+    const int64_t round_cap = (solver == L1_DALM || mode == L1_QP_LAMBDA) ? (int64_t)max_iter
+                                                                          : (int64_t)max_iter * inner_max;
+    int64_t rounds = 0;
+    while (true) {
+        P = &w.ps[q];
+        c = make_cols(h, q, N_cur);
+        const double na = N_cur;
+        for (int r = 0; r < check_every; ++r) {
+            if (solver == L1_DALM) {
+                // Algorithm 2: three sweeps per iteration
+                prof.start(0, 2.0 * m * n * na);
+                int rc = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Ux, ldn,
+                                      EpiDalmRhs{w.R, P->Ue, P->B, c.binv, c.active, ldm, cab ? 1 : 0},
                                       part_m, c.active);
                 prof.stop();
                 if (rc < 0) return rc;
-                prof.start(1, 2.0 * m * m * n_act);
-                const int np_e = launch_sweep(h, m, N, m, h->F, ldm, w.R, ldm,
-                                              EpiDalmY{w.Y, w.We, w.Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0},
-                                              part_m, c.active);
+                prof.start(1, 4.0 * m * m * na);  // F_hi and F_lo products
+                const int np_e = launch_sweep(h, m, N_cur, m, h->F, ldm, w.R, ldm,
+                                              EpiDalmY{P->Y, P->We, P->Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0},
+                                              part_m, c.active, h->F_lo);
                 prof.stop();
                 if (np_e < 0) return np_e;
-                prof.start(2, 2.0 * m * n * n_act);
-                const int np_x = launch_sweep(h, n, N, m, h->A_cm, ldm, w.Y, ldm,
-                                              EpiDalmS{w.Wx, w.Ux, c.beta, c.binv, c.active, ldn}, part_n,
+                prof.start(2, 2.0 * m * n * na);
+                const int np_x = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, P->Y, ldm,
+                                              EpiDalmS{P->Wx, P->Ux, c.beta, c.binv, c.active, ldn}, part_n,
                                               c.active);
                 prof.stop();
                 if (np_x < 0) return np_x;
-                ctrl_dalm_kernel<<<N, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e, part_n, np_x, tol, max_iter);
+                ctrl_dalm_kernel<<<N_cur, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e, part_n, np_x, tol, max_iter);
                 L1_LAUNCH_CHECK(h);
-            }
-            done_iters += check_every;
-            count_active_kernel<<<1, 1024, 0, s>>>(c.active, N, w.active_count);
-            L1_LAUNCH_CHECK(h);
-            L1_CUDA_TRY(cudaMemcpyAsync(w.h_active, w.active_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            L1_CUDA_TRY(cudaStreamSynchronize(s));
-            prof.collect();
-            n_act = *w.h_active;
-            if (*w.h_active == 0 || done_iters >= max_iter) break;
-        }
-    } else {
-        // Algorithm 1 / Eq. 18: two sweeps per inner FISTA step
-        PalmParams p;
-        p.mode = mode;
-        p.growth = (mode == L1_CAB || mode == L1_QP_LAMBDA) ? 1.0f
-                   : (float)(o.xi_growth > 0.0 ? o.xi_growth : 1.2);
-        p.Linv = (float)(1.0 / h->lipschitz);
-        const int inner_max = o.inner_max > 0 ? o.inner_max : 50;
-        const double inner_tol = o.inner_tol > 0.0 ? o.inner_tol : 0.1 * tol;
-        const int64_t step_cap = (mode == L1_QP_LAMBDA) ? (int64_t)max_iter : (int64_t)max_iter * inner_max;
-        int64_t steps = 0;
-        while (true) {
-            for (int r = 0; r < check_every; ++r) {
-                prof.start(0, 2.0 * m * n * n_act);
-                const int np_A = launch_sweep(h, m, N, n, h->A_rm, ldn, w.Ux, ldn,
-                                              EpiPalmA{w.R, w.Cc, w.We, w.Y, w.B, c, p, ldm}, part_m, c.active);
+            } else {
+                // Algorithm 1 / Eq. 18: two sweeps per inner FISTA step
+                prof.start(0, 2.0 * m * n * na);
+                const int np_A = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Ux, ldn,
+                                              EpiPalmA{w.R, P->Cc, P->We, P->Y, P->B, c, pp, ldm}, part_m, c.active);
                 prof.stop();
                 if (np_A < 0) return np_A;
-                prof.start(2, 2.0 * m * n * n_act);
-                const int np_At = launch_sweep(h, n, N, m, h->A_cm, ldm, w.R, ldm,
-                                               EpiPalmAt{w.Wx, w.Ux, w.X, c, p, ldn}, part_n, c.active);
+                prof.start(2, 2.0 * m * n * na);
+                const int np_At = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, w.R, ldm,
+                                               EpiPalmAt{P->Wx, P->Ux, P->X, c, pp, ldn}, part_n, c.active);
                 prof.stop();
                 if (np_At < 0) return np_At;
-                ctrl_palm_kernel<<<N, 128, 0, s>>>(c, p, part_m, np_A, part_n, np_At, w.Wx, w.X, w.Ux, ldn, n,
-                                                   tol, inner_tol, inner_max, max_iter);
+                ctrl_palm_kernel<<<N_cur, 128, 0, s>>>(c, pp, part_m, np_A, part_n, np_At, P->Wx, P->X, P->Ux, ldn, n,
+                                                       tol, inner_tol, inner_max, max_iter);
                 L1_LAUNCH_CHECK(h);
             }
-            steps += check_every;
-            count_active_kernel<<<1, 1024, 0, s>>>(c.active, N, w.active_count);
-            L1_LAUNCH_CHECK(h);
-            L1_CUDA_TRY(cudaMemcpyAsync(w.h_active, w.active_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            L1_CUDA_TRY(cudaStreamSynchronize(s));
-            prof.collect();
-            n_act = *w.h_active;
-            if (*w.h_active == 0 || steps >= step_cap) break;
         }
+        rounds += check_every;
+        count_active_kernel<<<1, 1024, 0, s>>>(c.active, N_cur, w.count);
+        L1_LAUNCH_CHECK(h);
+        L1_CUDA_TRY(cudaMemcpyAsync(w.h_count, w.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        L1_CUDA_TRY(cudaStreamSynchronize(s));
+        prof.collect();
+        const int n_act = *w.h_count;
+        const bool done = n_act == 0 || rounds >= round_cap;
+        auto tiles = [](int v) { return (v + kBN - 1) / kBN; };
+        const bool shrink = n_act < N_cur && (tiles(n_act) < tiles(N_cur) || (n_act <= 8 && N_cur > 8));
+        if (done || shrink) {
+            if (done) {
+                // retire every slot
+                fill_i32_kernel<<<(N_cur + 255) / 256, 256, 0, s>>>(c.active, N_cur, 0);
+                L1_LAUNCH_CHECK(h);
+            }
+            int cnt = 0;
+            L1_TRY(compact(h, q, N_cur, solver, xi_max, &cnt));
+            q ^= 1;
+            N_cur = cnt;
+        }
+        if (done) break;
     }
-    (void)done_iters;
 
-    // ---- finalisation: objective, dual point, gap, residual
-    L1_CUDA_TRY(cudaMemsetAsync(c.smax, 0, sizeof(float) * N, s));
-    const float* E = (cab || mode == L1_P1_2) ? w.We : nullptr;
-    const float* xi_fin = (solver == L1_PALM && mode != L1_QP_LAMBDA) ? c.xi : nullptr;
-    const int np_F1 = launch_sweep(h, m, N, n, h->A_rm, ldn, w.Wx, ldn,
-                                   EpiFinalA{w.R, w.Y, E, w.B, xi_fin, c.smax, ldm, mode}, part_m, nullptr);
+    // ---- finalisation on the home panels: objective, dual point, gap, residual
+    HomeRes hr = make_home_res(h);
+    if (mode == L1_QP_LAMBDA) {
+        set_param_kernel<<<(N + 255) / 256, 256, 0, s>>>(hr.param, N, o.lambda / h->lipschitz);
+        L1_LAUNCH_CHECK(h);
+    }
+    L1_CUDA_TRY(cudaMemsetAsync(hr.smax, 0, sizeof(float) * N, s));
+    const float* E = (cab || mode == L1_P1_2) ? w.hWe : nullptr;
+    const float* xi_fin = (solver == L1_PALM && mode != L1_QP_LAMBDA) ? hr.xi : nullptr;
+    const int np_F1 = launch_sweep(h, m, N, n, h->A_rm, ldn, w.hWx, ldn,
+                                   EpiFinalA{w.R, w.hY, E, w.hB, xi_fin, hr.smax, ldm, mode}, part_m, nullptr);
     if (np_F1 < 0) return np_F1;
-    const int np_F2 = launch_sweep(h, n, N, m, h->A_cm, ldm, (mode == L1_QP_LAMBDA) ? w.R : w.Y, ldm,
-                                   EpiFinalAt{w.Wx, c.smax, ldn}, part_n, nullptr);
+    const int np_F2 = launch_sweep(h, n, N, m, h->A_cm, ldm, (mode == L1_QP_LAMBDA) ? w.R : w.hY, ldm,
+                                   EpiFinalAt{w.hWx, hr.smax, ldn}, part_n, nullptr);
     if (np_F2 < 0) return np_F2;
-    final_metrics_kernel<<<N, 128, 0, s>>>(c, part_m, np_F1, part_n, np_F2, mode, o.lambda);
+    final_metrics_kernel<<<N, 128, 0, s>>>(N, hr.smax, hr.fin, part_m, np_F1, part_n, np_F2, mode, o.lambda);
     L1_LAUNCH_CHECK(h);
 
     // ---- classification (CAB with classes)
     const int C = (int)h->class_offsets.size() - 1;
     if (cab && C > 0) {
-        classify_resid_kernel<<<dim3(C, N), 128, 0, s>>>(h->A_rm, ldn, m, w.class_off, w.B, w.We, w.Wx, ldm,
+        classify_resid_kernel<<<dim3(C, N), 128, 0, s>>>(h->A_rm, ldn, m, w.class_off, w.hB, w.hWe, w.hWx, ldm,
                                                           ldn, N, w.resid2, w.classl1);
         L1_LAUNCH_CHECK(h);
-        classify_argmin_kernel<<<(N + 127) / 128, 128, 0, s>>>(w.resid2, w.classl1, C, N, c.label, c.sci_label);
+        classify_argmin_kernel<<<(N + 127) / 128, 128, 0, s>>>(w.resid2, w.classl1, C, N, hr.label, hr.sci_label);
+        L1_LAUNCH_CHECK(h);
+    } else {
+        fill_i32_kernel<<<(N + 255) / 256, 256, 0, s>>>(hr.label, N, -1);
+        L1_LAUNCH_CHECK(h);
+        fill_i32_kernel<<<(N + 255) / 256, 256, 0, s>>>(hr.sci_label, N, -1);
         L1_LAUNCH_CHECK(h);
     }
 
     // ---- outputs
-    l1_result* res_dev = reinterpret_cast<l1_result*>(w.R);  // R is free now; N*72 B <= ldm*N*4
-    static_assert(sizeof(l1_result) <= 128, "result size");
+    l1_result* res_dev = reinterpret_cast<l1_result*>(w.R);  // R is free now
     if ((size_t)N * sizeof(l1_result) > sizeof(float) * (size_t)ldm * N) return L1_ERR_INVALID_ARG;
-    pack_results_kernel<<<(N + 127) / 128, 128, 0, s>>>(c, res_dev, solver, mode, 1.0 / h->lipschitz, o.lambda);
+    pack_results_kernel<<<(N + 127) / 128, 128, 0, s>>>(hr, N, res_dev);
     L1_LAUNCH_CHECK(h);
-    if (solver == L1_PALM && mode != L1_QP_LAMBDA) {
-        // report xi_0 (the first outer step's penalty); xicap / xi_max = xi_0
-        // is recomputed on the device to avoid keeping another array
-        store_xi0_kernel<<<(N + 127) / 128, 128, 0, s>>>(c, res_dev, c.xicap);
-        L1_LAUNCH_CHECK(h);
-    }
-    L1_CUDA_TRY(cudaMemcpy2DAsync(x, ldx * sizeof(float), w.Wx, ldn * sizeof(float), n * sizeof(float), N,
+    L1_CUDA_TRY(cudaMemcpy2DAsync(x, ldx * sizeof(float), w.hWx, ldn * sizeof(float), n * sizeof(float), N,
                                   cudaMemcpyDefault, s));
     if (cab) {
-        L1_CUDA_TRY(cudaMemcpy2DAsync(x + n, ldx * sizeof(float), w.We, ldm * sizeof(float), m * sizeof(float),
+        L1_CUDA_TRY(cudaMemcpy2DAsync(x + n, ldx * sizeof(float), w.hWe, ldm * sizeof(float), m * sizeof(float),
                                       N, cudaMemcpyDefault, s));
     }
     if (y) {
-        L1_CUDA_TRY(cudaMemcpy2DAsync(y, ldy * sizeof(float), w.Y, ldm * sizeof(float), m * sizeof(float), N,
+        L1_CUDA_TRY(cudaMemcpy2DAsync(y, ldy * sizeof(float), w.hY, ldm * sizeof(float), m * sizeof(float), N,
                                       cudaMemcpyDefault, s));
     }
     L1_CUDA_TRY(cudaMemcpyAsync(res, res_dev, sizeof(l1_result) * N, cudaMemcpyDefault, s));
     L1_CUDA_TRY(cudaStreamSynchronize(s));
-    if (solver == L1_PALM && mode != L1_QP_LAMBDA)
-        for (int j = 0; j < N; ++j) res[j].param /= xi_max;
     return L1_OK;
 }
 

@@ -34,6 +34,21 @@ struct Cols {
     double* b1;    // ||b||_1
     double* fin;   // [N][8] final metrics
     float* smax;   // max |B^T y| (finalize)
+    int32_t* orig; // original column of each slot (compaction)
+};
+
+// Results of retired columns, in the caller's column order.
+struct Home {
+    int N;
+    float* Wx;      // x (n x N, ldn)
+    float* We;      // e (m x N, ldm)
+    float* Y;       // dual iterate (m x N, ldm)
+    int32_t* status;
+    int32_t* iters;
+    int32_t* inner;
+    double* rel;
+    double* param;  // beta (DALM), xi_0 (PALM), lambda/L (FISTA)
+    float* xi;      // PALM: xi of the last outer step (final multiplier step)
 };
 
 // xi used by an outer step: the schedule of §V-A (growth then cap) applies
@@ -341,6 +356,99 @@ __global__ void ctrl_palm_kernel(Cols c, PalmParams p, const double* part_A, int
     }
 }
 
+// ------------------------------------------------------------- compaction
+// Stable partition of the slots: newpos[s] = rank of s among the active slots
+// (or -1), *count = number of active slots.  One block of 1024 threads.
+__global__ void compact_scan_kernel(const int32_t* active, int N, int32_t* newpos, int32_t* count) {
+    __shared__ int warp_tot[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < N; c0 += blockDim.x) {
+        const int s = c0 + threadIdx.x;
+        const int f = (s < N && active[s]) ? 1 : 0;
+        int incl = f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int t = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += v;
+            }
+            warp_tot[lane] = t;  // inclusive prefix over warps
+        }
+        __syncthreads();
+        const int warp_off = wid > 0 ? warp_tot[wid - 1] : 0;
+        if (s < N) newpos[s] = f ? base + warp_off + incl - 1 : -1;
+        __syncthreads();
+        if (threadIdx.x == 0) base += warp_tot[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base;
+}
+
+// Move the active slots of one panel to their new positions (dst is a
+// second buffer) and write retiring slots to the home panel (nullable).
+__global__ void compact_panel_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                     float* __restrict__ home, int64_t ld, int rows, int N,
+                                     const int32_t* __restrict__ newpos,
+                                     const int32_t* __restrict__ orig) {
+    const int s = blockIdx.y;
+    if (s >= N) return;
+    const int np = newpos[s];
+    const float* col = src + (int64_t)s * ld;
+    if (np >= 0) {
+        float* d = dst + (int64_t)np * ld;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) d[i] = col[i];
+    } else if (home) {
+        float* d = home + (int64_t)orig[s] * ld;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) d[i] = col[i];
+    }
+}
+
+// Same for the per-slot scalars; retiring slots write their results home.
+__global__ void compact_cols_kernel(Cols src, Cols dst, Home home, int N, const int32_t* newpos,
+                                    int solver, double xi_max) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const int np = newpos[s];
+    if (np >= 0) {
+        dst.beta[np] = src.beta[s];
+        dst.binv[np] = src.binv[s];
+        dst.xi[np] = src.xi[s];
+        dst.xicap[np] = src.xicap[s];
+        dst.mu[np] = src.mu[s];
+        dst.active[np] = src.active[s];
+        dst.status[np] = src.status[s];
+        dst.iters[np] = src.iters[s];
+        dst.inner[np] = src.inner[s];
+        dst.phase[np] = src.phase[s];
+        dst.l[np] = src.l[s];
+        dst.t[np] = src.t[s];
+        dst.rel[np] = src.rel[s];
+        dst.de2[np] = src.de2[s];
+        dst.e2[np] = src.e2[s];
+        dst.b1[np] = src.b1[s];
+        dst.orig[np] = src.orig[s];
+    } else {
+        const int o = src.orig[s];
+        home.status[o] = src.status[s];
+        home.iters[o] = src.iters[s];
+        home.inner[o] = src.inner[s];
+        home.rel[o] = src.rel[s];
+        home.xi[o] = src.xi[s];
+        home.param[o] = solver == L1_DALM ? (double)src.beta[s] : (double)src.xicap[s] / xi_max;
+    }
+}
+
 // number of columns still active -> *count
 __global__ void count_active_kernel(const int32_t* active, int N, int32_t* count) {
     __shared__ int sh[32];
@@ -407,16 +515,16 @@ struct EpiFinalAt {
 };
 
 // fin[j][0..7] = primal, dual, gap, resid, x1, e1, -, -
-__global__ void final_metrics_kernel(Cols c, const double* part_A, int np_A, const double* part_At,
-                                     int np_At, int mode, double lambda) {
+__global__ void final_metrics_kernel(int N, const float* smax_arr, double* fin, const double* part_A,
+                                     int np_A, const double* part_At, int np_At, int mode, double lambda) {
     __shared__ double sh[4];
     const int j = blockIdx.x;
-    const double r2 = sum_parts(part_A, np_A, c.N, j, 0, sh);
-    const double by = sum_parts(part_A, np_A, c.N, j, 1, sh);
-    const double e1 = sum_parts(part_A, np_A, c.N, j, 2, sh);
-    const double x1 = sum_parts(part_At, np_At, c.N, j, 0, sh);
+    const double r2 = sum_parts(part_A, np_A, N, j, 0, sh);
+    const double by = sum_parts(part_A, np_A, N, j, 1, sh);
+    const double e1 = sum_parts(part_A, np_A, N, j, 2, sh);
+    const double x1 = sum_parts(part_At, np_At, N, j, 0, sh);
     if (threadIdx.x != 0) return;
-    const double smax = (double)c.smax[j];
+    const double smax = (double)smax_arr[j];
     double primal, dual;
     if (mode == L1_QP_LAMBDA) {
         // dual of Eq. 3: max b^T u - 1/2||u||^2 s.t. ||A^T u||_inf <= lambda,
@@ -430,7 +538,7 @@ __global__ void final_metrics_kernel(Cols c, const double* part_A, int np_A, con
         primal = x1 + e1;
         dual = by / fmax(1.0, smax);
     }
-    double* f = c.fin + (int64_t)j * 8;
+    double* f = fin + (int64_t)j * 8;
     f[0] = primal;
     f[1] = dual;
     f[2] = primal - dual;
