@@ -42,6 +42,18 @@ BENCH = dict(m=1024, classes=40, per_class=30, N=1024, corrupt=0.3, seed=1000,
 METRIC = "solves/sec at rel. err <=1e-4 vs FP64 oracle"
 L2_FLUSH_BYTES = 512 << 20
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates of the part
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def measured_peaks() -> dict:
+    """Measured peaks of this machine's GPUs, else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {k: float(d[k]) for k in FALLBACK_PEAKS}
+    except (OSError, KeyError, ValueError):
+        return dict(FALLBACK_PEAKS)
 
 
 def workload(rank: int = 0):
@@ -187,7 +199,8 @@ def bench_ours(args, rank, world):
     x_d = torch.empty((N, n + m), dtype=torch.float32, device="cuda").t()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     solver = l1.DALM if BENCH["solver"] == "DALM" else l1.PALM
-    s = l1.Solver(A_d, mode=l1.CAB, solver=solver, class_offsets=off, profile=True,
+    engine = l1.ENGINE_TC if args.engine == "tc" else l1.ENGINE_SIMT
+    s = l1.Solver(A_d, mode=l1.CAB, solver=solver, class_offsets=off, profile=True, engine=engine,
                   stream=stream.cuda_stream)
     setup_ms = s.info()["setup_ms"]
     tol, max_iter = BENCH["tol"], BENCH["max_iter"]
@@ -264,12 +277,28 @@ def bench_ours(args, rank, world):
     d_ln = [info1["sweep_launches"][k] - info0["sweep_launches"][k] for k in range(4)]
     k = int(np.argmax(d_ms))
     achieved = d_fl[k] / (d_ms[k] / 1e3) / 1e12 if d_ms[k] > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": f"sweep {names[k]} (gemm_simt_kernel)",
-                "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, no measured FP32 peak)",
-                "launches": d_ln[k], "avg_launch_us": 1e3 * d_ms[k] / max(1, d_ln[k]),
-                "share_of_sweep_time": d_ms[k] / max(1e-9, sum(d_ms))}
+    if args.engine == "tc":
+        # split-TF32 tcgen05 sweeps: 3 TF32 products per FP32 product (6 for the
+        # y-step); peak = measured sustained BF16 x the nominal TF32/BF16 ratio
+        peaks = measured_peaks()
+        terms = [3, 6, 3, 1][k]
+        peak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
+        roofline = {"bound": "tensor", "kernel": f"sweep {names[k]} (gemm_tc_kernel, tcgen05 kind::tf32)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None,
+                    "peak_note": (f"of measured: bf16_tflops_sustained {peaks['bf16_tflops_sustained']} x "
+                                  f"{TF32_PER_BF16:.4f} (nominal TF32 1.1 / BF16 2.25 PFLOP/s); "
+                                  f"achieved counts algorithmic FP32 FLOPs 2*M*K*N"),
+                    "executed_tf32_tflops": achieved * terms, "executed_frac": achieved * terms / peak,
+                    "launches": d_ln[k], "avg_launch_us": 1e3 * d_ms[k] / max(1, d_ln[k]),
+                    "share_of_sweep_time": d_ms[k] / max(1e-9, sum(d_ms))}
+    else:
+        roofline = {"bound": "alu", "kernel": f"sweep {names[k]} (gemm_simt_kernel)",
+                    "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                    "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, no measured FP32 peak)",
+                    "launches": d_ln[k], "avg_launch_us": 1e3 * d_ms[k] / max(1, d_ln[k]),
+                    "share_of_sweep_time": d_ms[k] / max(1e-9, sum(d_ms))}
 
     # ---- CPU oracle on a bounded sample of the same workload
     threads = min(os.cpu_count() or 1, 16)
@@ -283,7 +312,7 @@ def bench_ours(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": config_dict({"parallelism": f"replicas{world}" if world > 1 else "single",
-                                   "engine": "simt", "setup_ms": setup_ms,
+                                   "engine": args.engine, "setup_ms": setup_ms,
                                    "mean_iters": statistics.mean(iters),
                                    "label_accuracy_vs_planted": labels_ok / (args.steps * N)}),
             "e2e": {"value": e2e_conv / e2e_s, "unit": "solves/s",
@@ -306,6 +335,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--max-iter", type=int, default=None)
+    ap.add_argument("--engine", choices=["tc", "simt"], default="tc")
     args = ap.parse_args()
     if args.tol is not None:
         BENCH["tol"] = args.tol

@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "setup.cuh"
+#include "tc.cuh"
 
 namespace l1 {
 
@@ -106,7 +107,7 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
     // not implemented in this build
     if (mode == L1_P1_2) return L1_ERR_UNSUPPORTED;
     if (o.precision != L1_A_FP32) return L1_ERR_UNSUPPORTED;
-    if (o.engine == L1_ENGINE_TC) return L1_ERR_UNSUPPORTED;
+    if (o.engine == L1_ENGINE_TC && (o.solver != L1_DALM || mode == L1_QP_LAMBDA)) return L1_ERR_UNSUPPORTED;
     if (o.unroll_K > 0) return L1_ERR_UNSUPPORTED;
 
     Handle* h = new (std::nothrow) Handle();
@@ -141,6 +142,17 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
         }
         rc = make_layouts(h, stage, m);
         if (rc) break;
+        // tensor-core engine (batched DALM): TF32 pieces of both layouts of A
+        h->use_tc = (o.engine == L1_ENGINE_TC) && o.solver == L1_DALM && mode != L1_QP_LAMBDA;
+        if (h->use_tc) {
+            for (int k = 0; k < 2 && !rc; ++k) rc = dev_alloc_t(h, &h->A_rm_p[k], (size_t)h->ldn * m);
+            for (int k = 0; k < 2 && !rc; ++k) rc = dev_alloc_t(h, &h->A_cm_p[k], (size_t)h->ldm * n);
+            for (int k = 0; k < 3 && !rc; ++k) rc = dev_alloc_t(h, &h->F_p[k], (size_t)h->ldm * m);
+            if (!rc) rc = dev_alloc_t(h, &h->tc_err, 1);
+            if (!rc) rc = tc::split_tf32(h, h->A_rm, h->ldn * m, h->A_rm_p[0], h->A_rm_p[1], nullptr);
+            if (!rc) rc = tc::split_tf32(h, h->A_cm, h->ldm * n, h->A_cm_p[0], h->A_cm_p[1], nullptr);
+            if (rc) break;
+        }
         const bool needs_L = (mode == L1_QP_LAMBDA) || (o.solver == L1_PALM);
         if (o.lipschitz > 0.0) {
             h->lipschitz = o.lipschitz;

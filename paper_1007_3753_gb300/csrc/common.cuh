@@ -2,10 +2,13 @@
 // helpers.  Everything here is internal; the public surface is include/l1alm.h.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -80,6 +83,10 @@ struct Workspace {
     int64_t cap_N = 0;  // columns the buffers are sized for
     PanelSet ps[2];
     float* R = nullptr;   // DALM right-hand side of Eq. 39 / PALM residual c - A z (scratch)
+    // TF32 pieces of the panels the tensor-core sweeps read (scratch)
+    float* Up[2] = {nullptr, nullptr};         // of U_x (n x N)
+    float* Rp[3] = {nullptr, nullptr, nullptr}; // of R (m x N)
+    float* Yp[2] = {nullptr, nullptr};          // of y (m x N)
     // results in the caller's column order ("home")
     float* hB = nullptr;
     float* hWx = nullptr;
@@ -110,6 +117,18 @@ struct Handle {
     float* A_rm = nullptr;  // row-major m x n, ld = ldn     (K-major for A u)
     float* F = nullptr;     // DALM: (B B^T)^{-1}, m x m symmetric, ld = ldm (high FP32 part)
     float* F_lo = nullptr;  // low FP32 part: F + F_lo = (B B^T)^{-1} to ~48 bits
+    // tensor-core engine: TF32 pieces (p1 + p2 (+ p3) == value) of the operands
+    bool use_tc = false;
+    float* A_rm_p[2] = {nullptr, nullptr};
+    float* A_cm_p[2] = {nullptr, nullptr};
+    float* F_p[3] = {nullptr, nullptr, nullptr};
+    int* tc_err = nullptr;  // device: first bounded-wait failure of a tcgen05 sweep
+    // encoded TMA tensor maps, keyed by the operand pointers and shapes
+    struct MapCacheEntry {
+        std::array<uint64_t, 16> key;
+        std::vector<CUtensorMap> maps;  // a[0..T), x[0..T)
+    };
+    std::vector<MapCacheEntry> map_cache;
     double lipschitz = 0.0;
     double setup_ms = 0.0;
     int64_t device_bytes = 0;

@@ -8,6 +8,7 @@
 #include "gemm_simt.cuh"
 #include "setup.cuh"
 #include "solver_kernels.cuh"
+#include "tc.cuh"
 
 namespace l1 {
 
@@ -149,7 +150,8 @@ static int ensure_workspace(Handle* h, int N) {
         old.insert(old.end(), {p.B, p.Wx, p.We, p.Ux, p.Ue, p.Y, p.X, p.Cc, p.colf, p.coli, p.cold});
     }
     old.insert(old.end(), {w.R, w.hB, w.hWx, w.hWe, w.hY, w.hcoli, w.hcold, w.hcolf, w.part, w.newpos,
-                           w.count, w.resid2, w.classl1, w.class_off});
+                           w.count, w.resid2, w.classl1, w.class_off, w.Up[0], w.Up[1], w.Rp[0], w.Rp[1],
+                           w.Rp[2], w.Yp[0], w.Yp[1]});
     for (void* p : old) {
         if (!p) continue;
         cudaFree(p);
@@ -175,6 +177,11 @@ static int ensure_workspace(Handle* h, int N) {
         L1_TRY(dev_alloc_t(h, &p.cold, (size_t)8 * N));
     }
     L1_TRY(dev_alloc_t(h, &w.R, ldm * N));
+    if (h->use_tc) {
+        for (int k = 0; k < 2; ++k) L1_TRY(dev_alloc_t(h, &w.Up[k], ldn * N));
+        for (int k = 0; k < 3; ++k) L1_TRY(dev_alloc_t(h, &w.Rp[k], ldm * N));
+        for (int k = 0; k < 2; ++k) L1_TRY(dev_alloc_t(h, &w.Yp[k], ldm * N));
+    }
     L1_TRY(dev_alloc_t(h, &w.hB, ldm * N));
     L1_TRY(dev_alloc_t(h, &w.hWx, ldn * N));
     L1_TRY(dev_alloc_t(h, &w.hWe, ldm * N));
@@ -188,7 +195,7 @@ static int ensure_workspace(Handle* h, int N) {
     L1_TRY(dev_alloc_t(h, &w.part, 2 * (size_t)np * N * kPartStride));
     L1_TRY(dev_alloc_t(h, &w.newpos, (size_t)N));
     L1_TRY(dev_alloc_t(h, &w.count, 1));
-    if (cudaMallocHost(&w.h_count, sizeof(int32_t)) != cudaSuccess) return L1_ERR_OOM;
+    if (cudaMallocHost(&w.h_count, 2 * sizeof(int32_t)) != cudaSuccess) return L1_ERR_OOM;
     const int C = (int)h->class_offsets.size() - 1;
     if (C > 0) {
         L1_TRY(dev_alloc_t(h, &w.resid2, (size_t)C * N));
@@ -347,12 +354,49 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     const int64_t round_cap = (solver == L1_DALM || mode == L1_QP_LAMBDA) ? (int64_t)max_iter
                                                                           : (int64_t)max_iter * inner_max;
     int64_t rounds = 0;
+    bool pieces_valid = false;  // TF32 pieces of U_x match the current set
     while (true) {
         P = &w.ps[q];
         c = make_cols(h, q, N_cur);
         const double na = N_cur;
+        // tensor-core sweeps while the batch fills at least half a 64-column tile
+        const bool tc_now = h->use_tc && solver == L1_DALM && N_cur >= 32;
+        if (tc_now && !pieces_valid) {
+            L1_TRY(tc::split_tf32(h, P->Ux, ldn * (int64_t)N_cur, w.Up[0], w.Up[1], nullptr));
+            pieces_valid = true;
+        }
         for (int r = 0; r < check_every; ++r) {
-            if (solver == L1_DALM) {
+            if (solver == L1_DALM && tc_now) {
+                // Algorithm 2 on tcgen05: split-TF32 products, the y-step with
+                // a 33-bit inverse (six terms), see tc.cuh
+                const tc::Term g1[3] = {{h->A_rm_p[0], w.Up[0]}, {h->A_rm_p[0], w.Up[1]}, {h->A_rm_p[1], w.Up[0]}};
+                const tc::Term g2[6] = {{h->F_p[0], w.Rp[0]}, {h->F_p[0], w.Rp[1]}, {h->F_p[1], w.Rp[0]},
+                                        {h->F_p[0], w.Rp[2]}, {h->F_p[1], w.Rp[1]}, {h->F_p[2], w.Rp[0]}};
+                const tc::Term g3[3] = {{h->A_cm_p[0], w.Yp[0]}, {h->A_cm_p[0], w.Yp[1]}, {h->A_cm_p[1], w.Yp[0]}};
+                prof.start(0, 2.0 * m * n * na);
+                int rc = tc::launch(h, m, N_cur, n, g1, 3, ldn, ldn,
+                                    EpiDalmRhs{w.R, P->Ue, P->B, c.binv, c.active, ldm, cab ? 1 : 0,
+                                               Pieces{{w.Rp[0], w.Rp[1], w.Rp[2]}}},
+                                    part_m, c.active);
+                prof.stop();
+                if (rc < 0) return rc;
+                prof.start(1, 2.0 * m * m * na);
+                const int np_e = tc::launch(h, m, N_cur, m, g2, 6, ldm, ldm,
+                                            EpiDalmY{P->Y, P->We, P->Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0,
+                                                     Pieces{{w.Yp[0], w.Yp[1], nullptr}}},
+                                            part_m, c.active);
+                prof.stop();
+                if (np_e < 0) return np_e;
+                prof.start(2, 2.0 * m * n * na);
+                const int np_x = tc::launch(h, n, N_cur, m, g3, 3, ldm, ldm,
+                                            EpiDalmS{P->Wx, P->Ux, c.beta, c.binv, c.active, ldn,
+                                                     Pieces{{w.Up[0], w.Up[1], nullptr}}},
+                                            part_n, c.active);
+                prof.stop();
+                if (np_x < 0) return np_x;
+                ctrl_dalm_kernel<<<N_cur, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e, part_n, np_x, tol, max_iter);
+                L1_LAUNCH_CHECK(h);
+            } else if (solver == L1_DALM) {
                 // Algorithm 2: three sweeps per iteration
                 prof.start(0, 2.0 * m * n * na);
                 int rc = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Ux, ldn,
@@ -395,8 +439,16 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
         count_active_kernel<<<1, 1024, 0, s>>>(c.active, N_cur, w.count);
         L1_LAUNCH_CHECK(h);
         L1_CUDA_TRY(cudaMemcpyAsync(w.h_count, w.count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        if (h->tc_err) L1_CUDA_TRY(cudaMemcpyAsync(w.h_count + 1, h->tc_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         L1_CUDA_TRY(cudaStreamSynchronize(s));
         prof.collect();
+        if (h->tc_err && w.h_count[1] != 0) {
+            // a bounded wait inside a tensor-core sweep ran out: report it and
+            // leave the context usable
+            set_last_error("tcgen05 sweep: bounded wait expired (code " + std::to_string(w.h_count[1]) + ")");
+            L1_CUDA_TRY(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+            return L1_ERR_TIMEOUT;
+        }
         const int n_act = *w.h_count;
         const bool done = n_act == 0 || rounds >= round_cap;
         auto tiles = [](int v) { return (v + kBN - 1) / kBN; };
@@ -411,6 +463,7 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
             L1_TRY(compact(h, q, N_cur, solver, xi_max, &cnt));
             q ^= 1;
             N_cur = cnt;
+            pieces_valid = false;
         }
         if (done) break;
     }

@@ -62,6 +62,21 @@ __device__ __forceinline__ float xi_for_phase(int ph, float xi, float growth, fl
 // z_{k+1} - w_k/beta, so the right-hand side of Eq. 39 is
 //   B z_{k+1} - (B w_k - b)/beta = A U_x (+ U_e) + b/beta.
 
+// TF32 pieces of a value for the tensor-core sweeps that read the panel
+// next (see tc.cuh); p[k] may be null (pieces not needed).
+struct Pieces {
+    float* p[3];
+    __device__ __forceinline__ void store(int64_t o, float v) const {
+        if (!p[0]) return;
+        const float a = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        const float r = v - a;
+        const float b = __uint_as_float(__float_as_uint(r) & 0xFFFFE000u);
+        p[0][o] = a;
+        p[1][o] = b;
+        if (p[2]) p[2][o] = r - b;
+    }
+};
+
 // G1: R = A U_x (+ U_e) + b / beta
 struct EpiDalmRhs {
     static constexpr int NRED = 0;
@@ -72,12 +87,14 @@ struct EpiDalmRhs {
     const int32_t* active;
     int64_t ldm;
     int cab;
+    Pieces pc;
     __device__ void operator()(int i, int j, float acc, double*) const {
         if (!active[j]) return;
         const int64_t o = (int64_t)j * ldm + i;
         float v = fmaf(B[o], binv[j], acc);
         if (cab) v += Ue[o];
         R[o] = v;
+        pc.store(o, v);
     }
 };
 
@@ -95,10 +112,12 @@ struct EpiDalmY {
     const int32_t* active;
     int64_t ldm;
     int cab;
+    Pieces pc;
     __device__ void operator()(int i, int j, float acc, double* red) const {
         if (!active[j]) return;
         const int64_t o = (int64_t)j * ldm + i;
         Y[o] = acc;
+        pc.store(o, acc);
         if (!cab) return;
         const float bi = binv[j], be = beta[j];
         const float we = We[o];
@@ -123,6 +142,7 @@ struct EpiDalmS {
     const float* binv;
     const int32_t* active;
     int64_t ldn;
+    Pieces pc;
     __device__ void operator()(int i, int j, float acc, double* red) const {
         if (!active[j]) return;
         const int64_t o = (int64_t)j * ldn + i;
@@ -133,7 +153,9 @@ struct EpiDalmS {
         const float wn = w + dw;
         Wx[o] = wn;
         const float wb = wn * bi;
-        Ux[o] = clamp_unit(acc + wb) - wb;
+        const float u = clamp_unit(acc + wb) - wb;
+        Ux[o] = u;
+        pc.store(o, u);
         red[0] += (double)dw * dw;
         red[1] += (double)w * w;
     }

@@ -261,3 +261,56 @@ def test_bench_configuration_sampled_against_oracle(l1):
         assert res["label"][j] == lab and res["sci_label"][j] == slab
     ex.check()
     s.close()
+
+
+# ------------------------------------------------ tensor-core (tcgen05) engine
+
+@pytest.mark.parametrize("N", [40, 100])
+def test_cab_dalm_tensor_core_engine_matches_oracle(l1, N):
+    """Split-TF32 tcgen05 sweeps (ragged M tiles: 256 and 300 rows; ragged
+    64-column N tiles) against the FP64 oracle after a fixed iteration count."""
+    p = synthetic.cab_problem(256, 10, 30, N, seed=21)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    n = A.shape[1]
+    iters = 300
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=l1.ENGINE_TC)
+    x, y, res = s.solve(_dev(B), tol=0.0, max_iter=iters, want_y=True)
+    x = x.cpu().numpy()
+    y = y.cpu().numpy()
+    assert np.all(res["iters"] == iters)
+    cols = list(range(0, N, max(1, N // 12)))
+    outs = _pmap(lambda j: oracle.dalm(A, B[:, j], cab=True, tol=0.0, max_iter=iters), cols)
+    ex, ey = Errs(f"TC CAB DALM N={N} x"), Errs(f"TC CAB DALM N={N} y")
+    for j, (w, yo, st) in zip(cols, outs):
+        ex.add(x[:, j], w, res["primal_obj"][j])
+        ey.add(y[:, j], yo)
+        lab, slab, r, _ = oracle.classify(A, off, B[:, j], w[:n], w[n:])
+        assert res["label"][j] == lab and res["sci_label"][j] == slab
+    ex.check()
+    ey.check()
+    s.close()
+
+
+def test_bench_configuration_tensor_core_engine(l1):
+    import bench
+    cfg = bench.BENCH
+    p = bench.workload(0)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    n = A.shape[1]
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=l1.ENGINE_TC)
+    x, _, res = s.solve(_dev(B), tol=cfg["tol"], max_iter=cfg["max_iter"])
+    x = x.cpu().numpy()
+    assert np.mean(res["status"] == l1.CONVERGED) >= 0.99
+    assert np.mean(res["label"] == p["labels"]) >= 0.99
+    sample = [0, 5, 600, 1023]
+    outs = _pmap(lambda j: oracle.dalm(A, B[:, j], cab=True, tol=cfg["tol"], max_iter=cfg["max_iter"]),
+                 sample)
+    ex = Errs("TC bench configuration sample")
+    for j, (w, yo, st) in zip(sample, outs):
+        assert abs(res["iters"][j] - st["iters"]) <= 2, (j, res["iters"][j], st["iters"])
+        if res["iters"][j] == st["iters"]:
+            ex.add(x[:, j], w, res["primal_obj"][j])
+        lab, slab, r, _ = oracle.classify(A, off, B[:, j], w[:n], w[n:])
+        assert res["label"][j] == lab
+    ex.check()
+    s.close()
