@@ -100,6 +100,12 @@ typedef struct {
     int32_t unroll_J;    /* multiplier update every J inner steps; 0 -> 10 */
     int32_t ckpt_every;  /* checkpoint interval of the tape; 0 -> 20 */
     int32_t profile;     /* 1: time every sweep with CUDA events (l1_info.sweep_*) */
+    int32_t tc_sweeps;   /* L1_ENGINE_TC: bit 0 A u, bit 1 y-step, bit 2 A^T y on tcgen05; 0 -> 5.
+                          * The y-step multiplies by (B B^T)^{-1}; its tensor-core
+                          * accumulation rounds with a bias that the iteration
+                          * accumulates, so by default it stays on the compensated
+                          * CUDA-core sweep. */
+    int32_t reserved;
 } l1_options;
 
 /* Per-instance results (host memory). */

@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("check_every", C.c_int32), ("class_count", C.c_int32),
                 ("class_offsets", C.POINTER(C.c_int32)), ("stream", C.c_void_p),
                 ("unroll_K", C.c_int32), ("unroll_J", C.c_int32), ("ckpt_every", C.c_int32),
-                ("profile", C.c_int32)]
+                ("profile", C.c_int32), ("tc_sweeps", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -149,7 +149,7 @@ class Solver:
                  xi_growth: float = 0.0, xi_max: float = 0.0, lipschitz: float = 0.0,
                  inner_max: int = 0, inner_tol: float = 0.0, check_every: int = 0,
                  class_offsets=None, precision: int = A_FP32, engine: int = ENGINE_AUTO,
-                 profile: bool = False, stream=None):
+                 profile: bool = False, tc_sweeps: int = 0, stream=None):
         L = load()
         o = Options()
         L.l1_options_init(C.byref(o))
@@ -163,6 +163,7 @@ class Solver:
             o.xi_max = xi_max
         o.lipschitz, o.inner_tol = lipschitz, inner_tol
         o.profile = 1 if profile else 0
+        o.tc_sweeps = tc_sweeps
         if check_every:
             o.check_every = check_every
         self._offsets = None

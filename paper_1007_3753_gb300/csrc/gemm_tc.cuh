@@ -4,17 +4,25 @@
 // Each term t is a pair of operand "pieces" in the layouts of the SIMT path
 // (Aop_t K-major row-major, X_t column-major = K-major).  Summing terms gives
 // split-precision products: with TF32 pieces a = a1 + a2 (+ a3) the products
-// a1 x1 + a1 x2 + a2 x1 recover FP32-level accuracy on TF32 tensor cores.
+// a1 x1 + a1 x2 + a2 x1 recover FP32-level products on TF32 tensor cores.
+//
+// Accumulation.  Successive tcgen05.mma into one TMEM accumulator lose about
+// four bits over a few hundred steps (measured on this part), which the DALM
+// y-step amplifies by cond(B B^T).  The K loop is therefore cut into chunks
+// of CHUNK K blocks; each chunk accumulates in one of two TMEM buffers, and
+// the epilogue warps drain a finished chunk into Kahan-compensated FP32
+// register sums while the MMA warp fills the other buffer.
 //
 // Structure of one CTA (one 128 x BN output tile, non-persistent):
 //   warp 0      TMA producer: for every (term, K block) loads a 128 x 32-float
 //               tile of Aop_t and a BN x 32-float tile of X_t (128B swizzle)
-//               into a STAGES-deep ring, signalling "full" mbarriers
-//   warp 1      allocates BN TMEM columns, issues tcgen05.mma (kind::tf32 or
-//               kind::f16) from one elected thread, and tcgen05.commit frees
-//               each ring slot and finally signals the accumulator
-//   warps 2..5  epilogue: tcgen05.ld of the FP32 accumulator (TMEM lane = row),
-//               the functor per element, per-column reductions
+//               into a kStages-deep ring ("full" mbarriers)
+//   warp 1      allocates 2*BN TMEM columns, issues tcgen05.mma (kind::tf32 or
+//               kind::f16) from one thread; tcgen05.commit frees ring slots
+//               ("empty") and hands finished chunks to the epilogue
+//   warps 2..5  epilogue: tcgen05.ld of each chunk (TMEM lane = output row),
+//               compensated sums, then the functor per element and the
+//               per-column reductions
 // Every mbarrier wait is bounded; a wait that runs out records an error code
 // in *err and the CTA leaves its loops, waits (bounded) for its own copies,
 // frees TMEM and returns.
@@ -26,6 +34,10 @@
 #include "common.cuh"
 #include "gemm_simt.cuh"
 
+#ifndef L1_TC_KAHAN
+#define L1_TC_KAHAN 1
+#endif
+
 namespace l1 {
 namespace tc {
 
@@ -36,7 +48,7 @@ constexpr int kStages = 4;
 constexpr int kThreads = 192;   // 6 warps
 constexpr uint32_t kSpinLimit = 1u << 26;
 
-enum : int { ERR_NONE = 0, ERR_WAIT_FULL = 1, ERR_WAIT_EMPTY = 2, ERR_WAIT_ACC = 3 };
+enum : int { ERR_NONE = 0, ERR_WAIT_FULL = 1, ERR_WAIT_EMPTY = 2, ERR_WAIT_ACC = 3, ERR_WAIT_DRAIN = 4 };
 
 struct TermMaps {
     CUtensorMap a[kMaxTerms];
@@ -49,7 +61,7 @@ struct Smem {
     static constexpr int kXTile = BN * kRowBytes;
     static constexpr int kStage = kATile + kXTile;
     // barriers and flags after the ring; the epilogue's reduction scratch
-    // reuses the ring once the accumulator is complete
+    // reuses the ring once the last chunk has been drained
     static constexpr int kBytes = kStages * kStage + 256 + 1024 /* alignment slack */;
 };
 
@@ -65,6 +77,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -150,7 +166,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 // ------------------------------------------------------------------ kernel
-template <class E, int BN, bool TF32>
+template <class E, int BN, bool TF32, int CHUNK>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ TermMaps maps, int terms, int M, int N, int K, E epi,
                double* __restrict__ part, const int32_t* __restrict__ active, int* __restrict__ err) {
@@ -159,7 +175,8 @@ gemm_tc_kernel(const __grid_constant__ TermMaps maps, int terms, int M, int N, i
     constexpr int kMmaK = TF32 ? 8 : 16;                   // K per tcgen05.mma
     constexpr int kMmaPerBlock = kElemPerRow / kMmaK;      // 4
     constexpr uint32_t kIdesc = instr_desc(TF32 ? 2 : 1, kBM, BN);
-    constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+    constexpr uint32_t kTmemCols = 2 * BN;                 // two accumulator buffers
+    static_assert(BN == 32 || BN == 64 || BN == 128, "tile width");
     using S = Smem<BN>;
 
     extern __shared__ uint8_t smem_raw[];
@@ -167,16 +184,18 @@ gemm_tc_kernel(const __grid_constant__ TermMaps maps, int terms, int M, int N, i
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * S::kStage);
     uint64_t* empty = full + kStages;
-    uint64_t* acc_bar = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_bar + 1);
-    int* flags = reinterpret_cast<int*>(tmem_slot + 1);  // [0]: any active, [1]: abort
-    double* red_s = reinterpret_cast<double*>(smem);  // [4][BN][NR], valid once the ring is drained
+    uint64_t* acc_full = empty + kStages;   // [2] chunk finished in buffer b
+    uint64_t* acc_empty = acc_full + 2;     // [2] buffer b drained
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    int* flags = reinterpret_cast<int*>(tmem_slot + 1);  // [0]: any active column, [1]: abort
+    double* red_s = reinterpret_cast<double*>(smem);      // [4][BN][NR], after the last drain
     static_assert(4 * BN * NR * 8 <= kStages * S::kStage, "reduction scratch");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
     const int kblocks = (K + kElemPerRow - 1) / kElemPerRow;
     const int total = terms * kblocks;
+    const int nchunks = (total + CHUNK - 1) / CHUNK;
 
     if (threadIdx.x == 0) {
         flags[0] = 0;
@@ -202,7 +221,10 @@ gemm_tc_kernel(const __grid_constant__ TermMaps maps, int terms, int M, int N, i
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(acc_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -247,63 +269,95 @@ gemm_tc_kernel(const __grid_constant__ TermMaps maps, int terms, int M, int N, i
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            bool ok = true;
             for (int it = 0; it < total; ++it) {
                 const int s = it % kStages;
                 const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+                const int chunk = it / CHUNK;
+                const int b = chunk & 1;
+                const bool first = (it % CHUNK) == 0;
+                const bool last = (it % CHUNK) == CHUNK - 1 || it == total - 1;
+                if (first && !mbar_wait(&acc_empty[b], ((uint32_t)(chunk >> 1) & 1u) ^ 1u)) {
+                    atomicCAS(err, ERR_NONE, ERR_WAIT_DRAIN);
+                    atomicExch(&flags[1], 1);
+                    break;
+                }
                 if (!mbar_wait(&full[s], ph)) {
                     atomicCAS(err, ERR_NONE, ERR_WAIT_FULL);
                     atomicExch(&flags[1], 1);
-                    ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t a_addr = smem_u32(smem + s * S::kStage);
                 const uint32_t x_addr = a_addr + S::kATile;
+                const uint32_t d = tmem + (uint32_t)(b * BN);
 #pragma unroll
                 for (int k = 0; k < kMmaPerBlock; ++k) {
                     const uint64_t ad = smem_desc(a_addr + k * kMmaK * (TF32 ? 4 : 2));
                     const uint64_t bd = smem_desc(x_addr + k * kMmaK * (TF32 ? 4 : 2));
-                    mma<TF32>(tmem, ad, bd, kIdesc, (it > 0 || k > 0) ? 1u : 0u);
+                    mma<TF32>(d, ad, bd, kIdesc, (first && k == 0) ? 0u : 1u);
                 }
                 mma_commit(&empty[s]);
+                if (last) mma_commit(&acc_full[b]);
             }
-            if (ok) mma_commit(acc_bar);
-            else atomicExch(&flags[1], 1);
         }
         __syncwarp();
     } else {
         // -------------------------------------------------------- epilogue
         const int q = warp & 3;  // TMEM lane quarter this warp may access
-        const int row = q * 32 + lane;
-        const int i = m0 + row;
-        bool ready = true;
-        if (lane == 0) ready = mbar_wait(acc_bar, 0);
-        ready = __shfl_sync(0xffffffffu, ready ? 1 : 0, 0) != 0;
-        if (!ready) {
-            if (lane == 0) {
-                atomicCAS(err, ERR_NONE, ERR_WAIT_ACC);
-                atomicExch(&flags[1], 1);
+        const int i = m0 + q * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+        float sum[BN], comp[BN];
+#pragma unroll
+        for (int c = 0; c < BN; ++c) sum[c] = comp[c] = 0.0f;
+        bool ok = true;
+        for (int chunk = 0; chunk < nchunks && ok; ++chunk) {
+            const int b = chunk & 1;
+            bool ready = true;
+            if (lane == 0) ready = mbar_wait(&acc_full[b], (uint32_t)(chunk >> 1) & 1u);
+            ready = __shfl_sync(0xffffffffu, ready ? 1 : 0, 0) != 0;
+            if (!ready) {
+                if (lane == 0) {
+                    atomicCAS(err, ERR_NONE, ERR_WAIT_ACC);
+                    atomicExch(&flags[1], 1);
+                }
+                ok = false;
+                break;
             }
-        } else {
             asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll 1
+#pragma unroll
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                tmem_ld16(lane_addr + (uint32_t)(b * BN + c0), v);
 #pragma unroll
                 for (int cc = 0; cc < 16; ++cc) {
-                    const int j = n0 + c0 + cc;
-                    double red[NR];
+#if L1_TC_KAHAN
+                    // Kahan: sum + v with the running compensation
+                    const float y = v[cc] - comp[c0 + cc];
+                    const float t = sum[c0 + cc] + y;
+                    comp[c0 + cc] = (t - sum[c0 + cc]) - y;
+                    sum[c0 + cc] = t;
+#else
+                    sum[c0 + cc] += v[cc];
+#endif
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+        if (ok) {
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) red[r] = 0.0;
-                    if (i < M && j < N) epi(i, j, v[cc], red);
-                    if constexpr (E::NRED > 0) {
+            for (int c = 0; c < BN; ++c) {
+                const int j = n0 + c;
+                double red[NR];
 #pragma unroll
-                        for (int r = 0; r < NR; ++r) {
-                            const double sv = warp_sum(red[r]);
-                            if (lane == 0) red_s[((q * BN) + c0 + cc) * NR + r] = sv;
-                        }
+                for (int r = 0; r < NR; ++r) red[r] = 0.0;
+                if (i < M && j < N) epi(i, j, sum[c] - comp[c], red);
+                if constexpr (E::NRED > 0) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const double sv = warp_sum(red[r]);
+                        if (lane == 0) red_s[((q * BN) + c) * NR + r] = sv;
                     }
                 }
             }

@@ -366,54 +366,50 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
             pieces_valid = true;
         }
         for (int r = 0; r < check_every; ++r) {
-            if (solver == L1_DALM && tc_now) {
-                // Algorithm 2 on tcgen05: split-TF32 products, the y-step with
-                // a 33-bit inverse (six terms), see tc.cuh
-                const tc::Term g1[3] = {{h->A_rm_p[0], w.Up[0]}, {h->A_rm_p[0], w.Up[1]}, {h->A_rm_p[1], w.Up[0]}};
-                const tc::Term g2[6] = {{h->F_p[0], w.Rp[0]}, {h->F_p[0], w.Rp[1]}, {h->F_p[1], w.Rp[0]},
-                                        {h->F_p[0], w.Rp[2]}, {h->F_p[1], w.Rp[1]}, {h->F_p[2], w.Rp[0]}};
-                const tc::Term g3[3] = {{h->A_cm_p[0], w.Yp[0]}, {h->A_cm_p[0], w.Yp[1]}, {h->A_cm_p[1], w.Yp[0]}};
+            if (solver == L1_DALM) {
+                // Algorithm 2: three sweeps per iteration.  On tcgen05 the
+                // products are split-TF32 (three terms; six for the y-step so
+                // the inverse carries 33 bits), see tc.cuh; the epilogues also
+                // write the TF32 pieces the next tensor-core sweep reads.
+                // default: the two A sweeps on tensor cores, the y-step on the
+                // compensated CUDA-core sweep (see l1_options.tc_sweeps)
+                const int mask = o.tc_sweeps ? o.tc_sweeps : 5;
+                const bool t1 = tc_now && (mask & 1), t2 = tc_now && (mask & 2), t3 = tc_now && (mask & 4);
+                const Pieces rp = h->use_tc ? Pieces{{w.Rp[0], w.Rp[1], w.Rp[2]}} : Pieces{{nullptr, nullptr, nullptr}};
+                const Pieces yp = h->use_tc ? Pieces{{w.Yp[0], w.Yp[1], nullptr}} : Pieces{{nullptr, nullptr, nullptr}};
+                const Pieces up = h->use_tc ? Pieces{{w.Up[0], w.Up[1], nullptr}} : Pieces{{nullptr, nullptr, nullptr}};
+                const EpiDalmRhs e1{w.R, P->Ue, P->B, c.binv, c.active, ldm, cab ? 1 : 0, rp};
+                const EpiDalmY e2{P->Y, P->We, P->Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0, yp};
+                const EpiDalmS e3{P->Wx, P->Ux, c.beta, c.binv, c.active, ldn, up};
                 prof.start(0, 2.0 * m * n * na);
-                int rc = tc::launch(h, m, N_cur, n, g1, 3, ldn, ldn,
-                                    EpiDalmRhs{w.R, P->Ue, P->B, c.binv, c.active, ldm, cab ? 1 : 0,
-                                               Pieces{{w.Rp[0], w.Rp[1], w.Rp[2]}}},
-                                    part_m, c.active);
+                int rc;
+                if (t1) {
+                    const tc::Term g1[3] = {{h->A_rm_p[0], w.Up[0]}, {h->A_rm_p[0], w.Up[1]}, {h->A_rm_p[1], w.Up[0]}};
+                    rc = tc::launch(h, m, N_cur, n, g1, 3, ldn, ldn, e1, part_m, c.active);
+                } else {
+                    rc = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Ux, ldn, e1, part_m, c.active);
+                }
                 prof.stop();
                 if (rc < 0) return rc;
-                prof.start(1, 2.0 * m * m * na);
-                const int np_e = tc::launch(h, m, N_cur, m, g2, 6, ldm, ldm,
-                                            EpiDalmY{P->Y, P->We, P->Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0,
-                                                     Pieces{{w.Yp[0], w.Yp[1], nullptr}}},
-                                            part_m, c.active);
+                prof.start(1, (t2 ? 2.0 : 4.0) * m * m * na);  // SIMT: F_hi and F_lo products
+                int np_e;
+                if (t2) {
+                    const tc::Term g2[6] = {{h->F_p[0], w.Rp[0]}, {h->F_p[0], w.Rp[1]}, {h->F_p[1], w.Rp[0]},
+                                            {h->F_p[0], w.Rp[2]}, {h->F_p[1], w.Rp[1]}, {h->F_p[2], w.Rp[0]}};
+                    np_e = tc::launch(h, m, N_cur, m, g2, 6, ldm, ldm, e2, part_m, c.active);
+                } else {
+                    np_e = launch_sweep(h, m, N_cur, m, h->F, ldm, w.R, ldm, e2, part_m, c.active, h->F_lo);
+                }
                 prof.stop();
                 if (np_e < 0) return np_e;
                 prof.start(2, 2.0 * m * n * na);
-                const int np_x = tc::launch(h, n, N_cur, m, g3, 3, ldm, ldm,
-                                            EpiDalmS{P->Wx, P->Ux, c.beta, c.binv, c.active, ldn,
-                                                     Pieces{{w.Up[0], w.Up[1], nullptr}}},
-                                            part_n, c.active);
-                prof.stop();
-                if (np_x < 0) return np_x;
-                ctrl_dalm_kernel<<<N_cur, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e, part_n, np_x, tol, max_iter);
-                L1_LAUNCH_CHECK(h);
-            } else if (solver == L1_DALM) {
-                // Algorithm 2: three sweeps per iteration
-                prof.start(0, 2.0 * m * n * na);
-                int rc = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Ux, ldn,
-                                      EpiDalmRhs{w.R, P->Ue, P->B, c.binv, c.active, ldm, cab ? 1 : 0},
-                                      part_m, c.active);
-                prof.stop();
-                if (rc < 0) return rc;
-                prof.start(1, 4.0 * m * m * na);  // F_hi and F_lo products
-                const int np_e = launch_sweep(h, m, N_cur, m, h->F, ldm, w.R, ldm,
-                                              EpiDalmY{P->Y, P->We, P->Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0},
-                                              part_m, c.active, h->F_lo);
-                prof.stop();
-                if (np_e < 0) return np_e;
-                prof.start(2, 2.0 * m * n * na);
-                const int np_x = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, P->Y, ldm,
-                                              EpiDalmS{P->Wx, P->Ux, c.beta, c.binv, c.active, ldn}, part_n,
-                                              c.active);
+                int np_x;
+                if (t3) {
+                    const tc::Term g3[3] = {{h->A_cm_p[0], w.Yp[0]}, {h->A_cm_p[0], w.Yp[1]}, {h->A_cm_p[1], w.Yp[0]}};
+                    np_x = tc::launch(h, n, N_cur, m, g3, 3, ldm, ldm, e3, part_n, c.active);
+                } else {
+                    np_x = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, P->Y, ldm, e3, part_n, c.active);
+                }
                 prof.stop();
                 if (np_x < 0) return np_x;
                 ctrl_dalm_kernel<<<N_cur, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e, part_n, np_x, tol, max_iter);

@@ -68,9 +68,10 @@ struct Pieces {
     float* p[3];
     __device__ __forceinline__ void store(int64_t o, float v) const {
         if (!p[0]) return;
-        const float a = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        // round-to-nearest TF32 pieces (unbiased remainders), v == a + b + (r - b)
+        const float a = __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
         const float r = v - a;
-        const float b = __uint_as_float(__float_as_uint(r) & 0xFFFFE000u);
+        const float b = __uint_as_float((__float_as_uint(r) + 0x1000u) & 0xFFFFE000u);
         p[0][o] = a;
         p[1][o] = b;
         if (p[2]) p[2][o] = r - b;

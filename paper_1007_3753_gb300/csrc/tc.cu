@@ -62,9 +62,9 @@ __global__ void split_tf32_f64_kernel(const double* x, int rows, int cols, int64
     if (idx >= (int64_t)ld_dst * cols) return;
     const int64_t c = idx / ld_dst, r = idx % ld_dst;
     const double v = r < rows ? x[c * ld_src + r] : 0.0;
-    const float a = tf32_trunc((float)v);
+    const float a = tf32_rn((float)v);
     const double r1 = v - (double)a;
-    const float b = tf32_trunc((float)r1);
+    const float b = tf32_rn((float)r1);
     const float cc = (float)(r1 - (double)b);
     p1[idx] = a;
     p2[idx] = b;

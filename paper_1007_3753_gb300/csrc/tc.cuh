@@ -23,15 +23,20 @@ int split_tf32(Handle* h, const float* x, int64_t count, float* p1, float* p2, f
 int split_tf32_from_f64(Handle* h, const double* x, int rows, int cols, int64_t ld_src, int64_t ld_dst,
                         float* p1, float* p2, float* p3);
 
-__device__ __forceinline__ float tf32_trunc(float x) {
-    return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+// x rounded to the nearest TF32 value (10 explicit mantissa bits; ties away
+// from zero), returned as an FP32 whose low 13 bits are zero.  Rounding to
+// nearest makes the remainder x - tf32_rn(x) take either sign, so the product
+// term a2 x2 that a three-term split leaves out is not biased (with
+// truncation it always has the sign of a x).
+__device__ __forceinline__ float tf32_rn(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// pieces of one FP32 value (device side, for epilogues)
+// pieces of one FP32 value (device side): x == a + b + c exactly
 __device__ __forceinline__ void tf32_split3(float x, float& a, float& b, float& c) {
-    a = tf32_trunc(x);
-    const float r = x - a;
-    b = tf32_trunc(r);
+    a = tf32_rn(x);
+    const float r = x - a;  // exact (Sterbenz)
+    b = tf32_rn(r);
     c = r - b;
 }
 
@@ -41,6 +46,12 @@ struct Term {
 };
 
 constexpr int kBN = 64;
+// K blocks (of 32 TF32 elements, 4 MMAs) accumulated in TMEM before the
+// epilogue drains them into compensated register sums
+#ifndef L1_TC_CHUNK
+#define L1_TC_CHUNK 1
+#endif
+constexpr int kDrainChunk = L1_TC_CHUNK;
 
 // Tensor maps of a term list, encoded once per (pointers, shape) and cached
 // in the handle (encoding costs host time on every sweep otherwise).
@@ -89,15 +100,16 @@ int launch(Handle* h, int M, int N, int K, const Term* terms, int nterms, int64_
     TermMaps maps;
     L1_TRY(get_maps(h, M, N, K, terms, nterms, lda, ldx, &maps));
     using S = Smem<BN>;
+    constexpr int CHUNK = kDrainChunk;
     static bool attr_set = false;
     if (!attr_set) {
-        L1_CUDA_TRY(cudaFuncSetAttribute(gemm_tc_kernel<E, BN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         S::kBytes));
+        L1_CUDA_TRY(cudaFuncSetAttribute(gemm_tc_kernel<E, BN, true, CHUNK>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes));
         attr_set = true;
     }
     dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM);
-    gemm_tc_kernel<E, BN, true><<<grid, kThreads, S::kBytes, h->stream>>>(maps, nterms, M, N, K, epi, part, active,
-                                                                          h->tc_err);
+    gemm_tc_kernel<E, BN, true, CHUNK><<<grid, kThreads, S::kBytes, h->stream>>>(maps, nterms, M, N, K, epi, part,
+                                                                                 active, h->tc_err);
     L1_LAUNCH_CHECK(h);
     return (int)grid.y;
 }
