@@ -87,6 +87,7 @@ struct Workspace {
     float* Up[2] = {nullptr, nullptr};         // of U_x (n x N)
     float* Rp[3] = {nullptr, nullptr, nullptr}; // of R (m x N)
     float* Yp[2] = {nullptr, nullptr};          // of y (m x N)
+    float* Ylo = nullptr;                       // (B B^T)^{-1}_lo R (m x N)
     // results in the caller's column order ("home")
     float* hB = nullptr;
     float* hWx = nullptr;

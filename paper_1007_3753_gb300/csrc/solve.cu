@@ -151,7 +151,7 @@ static int ensure_workspace(Handle* h, int N) {
     }
     old.insert(old.end(), {w.R, w.hB, w.hWx, w.hWe, w.hY, w.hcoli, w.hcold, w.hcolf, w.part, w.newpos,
                            w.count, w.resid2, w.classl1, w.class_off, w.Up[0], w.Up[1], w.Rp[0], w.Rp[1],
-                           w.Rp[2], w.Yp[0], w.Yp[1]});
+                           w.Rp[2], w.Yp[0], w.Yp[1], w.Ylo});
     for (void* p : old) {
         if (!p) continue;
         cudaFree(p);
@@ -181,6 +181,7 @@ static int ensure_workspace(Handle* h, int N) {
         for (int k = 0; k < 2; ++k) L1_TRY(dev_alloc_t(h, &w.Up[k], ldn * N));
         for (int k = 0; k < 3; ++k) L1_TRY(dev_alloc_t(h, &w.Rp[k], ldm * N));
         for (int k = 0; k < 2; ++k) L1_TRY(dev_alloc_t(h, &w.Yp[k], ldm * N));
+        L1_TRY(dev_alloc_t(h, &w.Ylo, ldm * N));
     }
     L1_TRY(dev_alloc_t(h, &w.hB, ldm * N));
     L1_TRY(dev_alloc_t(h, &w.hWx, ldn * N));
@@ -384,19 +385,31 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                 prof.start(0, 2.0 * m * n * na);
                 int rc;
                 if (t1) {
-                    const tc::Term g1[3] = {{h->A_rm_p[0], w.Up[0]}, {h->A_rm_p[0], w.Up[1]}, {h->A_rm_p[1], w.Up[0]}};
-                    rc = tc::launch(h, m, N_cur, n, g1, 3, ldn, ldn, e1, part_m, c.active);
+                    const float* ap[2] = {h->A_rm_p[0], h->A_rm_p[1]};
+                    const float* xp[2] = {w.Up[0], w.Up[1]};
+                    rc = tc::launch(h, m, N_cur, n, ap, 2, xp, 2, tc::terms_split3(), ldn, ldn, e1, part_m, c.active);
                 } else {
                     rc = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Ux, ldn, e1, part_m, c.active);
                 }
                 prof.stop();
                 if (rc < 0) return rc;
-                prof.start(1, (t2 ? 2.0 : 4.0) * m * m * na);  // SIMT: F_hi and F_lo products
+                prof.start(1, 2.0 * m * m * na);  // algorithmic: one m x m product per column
                 int np_e;
                 if (t2) {
-                    const tc::Term g2[6] = {{h->F_p[0], w.Rp[0]}, {h->F_p[0], w.Rp[1]}, {h->F_p[1], w.Rp[0]},
-                                            {h->F_p[0], w.Rp[2]}, {h->F_p[1], w.Rp[1]}, {h->F_p[2], w.Rp[0]}};
-                    np_e = tc::launch(h, m, N_cur, m, g2, 6, ldm, ldm, e2, part_m, c.active);
+                    const float* ap[3] = {h->F_p[0], h->F_p[1], h->F_p[2]};
+                    const float* xp[3] = {w.Rp[0], w.Rp[1], w.Rp[2]};
+                    np_e = tc::launch(h, m, N_cur, m, ap, 3, xp, 3, tc::terms_split6(), ldm, ldm, e2, part_m, c.active);
+                } else if (tc_now) {
+                    // F_lo R is a 2^-24-relative correction: one TF32 product on
+                    // tensor cores is exact enough; F_hi R runs on the
+                    // compensated CUDA-core sweep, which adds the correction
+                    const float* ap[1] = {h->F_lo};
+                    const float* xp[1] = {w.R};
+                    const int rc_lo = tc::launch(h, m, N_cur, m, ap, 1, xp, 1, tc::terms_single(), ldm, ldm,
+                                                 EpiStorePanel{w.Ylo, c.active, ldm}, nullptr, c.active);
+                    if (rc_lo < 0) return rc_lo;
+                    np_e = launch_sweep(h, m, N_cur, m, h->F, ldm, w.R, ldm, EpiAddPanel<EpiDalmY>{w.Ylo, ldm, e2},
+                                        part_m, c.active);
                 } else {
                     np_e = launch_sweep(h, m, N_cur, m, h->F, ldm, w.R, ldm, e2, part_m, c.active, h->F_lo);
                 }
@@ -405,8 +418,9 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                 prof.start(2, 2.0 * m * n * na);
                 int np_x;
                 if (t3) {
-                    const tc::Term g3[3] = {{h->A_cm_p[0], w.Yp[0]}, {h->A_cm_p[0], w.Yp[1]}, {h->A_cm_p[1], w.Yp[0]}};
-                    np_x = tc::launch(h, n, N_cur, m, g3, 3, ldm, ldm, e3, part_n, c.active);
+                    const float* ap[2] = {h->A_cm_p[0], h->A_cm_p[1]};
+                    const float* xp[2] = {w.Yp[0], w.Yp[1]};
+                    np_x = tc::launch(h, n, N_cur, m, ap, 2, xp, 2, tc::terms_split3(), ldm, ldm, e3, part_n, c.active);
                 } else {
                     np_x = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, P->Y, ldm, e3, part_n, c.active);
                 }

@@ -133,6 +133,30 @@ struct EpiDalmY {
     }
 };
 
+// Store a sweep's result (active columns only): out = acc.
+struct EpiStorePanel {
+    static constexpr int NRED = 0;
+    float* out;
+    const int32_t* active;
+    int64_t ld;
+    __device__ void operator()(int i, int j, float acc, double*) const {
+        if (active[j]) out[(int64_t)j * ld + i] = acc;
+    }
+};
+
+// Add a panel to the accumulator before an inner epilogue: the y-step as
+// (F_hi R) + (F_lo R) with the two products from different sweeps.
+template <class E>
+struct EpiAddPanel {
+    static constexpr int NRED = E::NRED;
+    const float* add;
+    int64_t ld;
+    E inner;
+    __device__ void operator()(int i, int j, float acc, double* red) const {
+        inner(i, j, acc + add[(int64_t)j * ld + i], red);
+    }
+};
+
 // G3: s = A^T y_{k+1}; the x-part of the w-step and the next z - w/beta.
 // red: ||dw_x||^2, ||w_x||^2.
 struct EpiDalmS {
