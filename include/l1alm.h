@@ -159,6 +159,38 @@ L1_API int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t m
                     const l1_options* opt, l1_handle* out);
 
 /*
+ * l1_setup_group -- a batch of `count` independent (QP_lambda) problems
+ * (Eq. 3) whose dictionaries differ in size: instance i has A[i], m[i] x n[i],
+ * column-major FP32 with leading dimension m[i] (host or device).  The group
+ * is solved by FISTA (Eq. 18, §IV-A) in one persistent launch per solve with
+ * per-instance stopping (§VI-C rule) and an active-instance work list.
+ * opt->precision selects the storage of the dictionaries: L1_A_FP32 or
+ * L1_A_BF16 (round to nearest even; FP32 arithmetic).  L = ||A_i||_2^2 of
+ * each instance comes from a batched power iteration (x 1.01).  A == NULL
+ * allocates the group and leaves the dictionaries to l1_group_load.
+ * Errors: L1_ERR_INVALID_ARG (mode other than QP_LAMBDA, lambda <= 0, count
+ * or a size <= 0), L1_ERR_OOM, L1_ERR_CUDA, L1_ERR_UNSUPPORTED.
+ */
+L1_API int l1_setup_group(const float* const* A, const int64_t* m, const int64_t* n, int64_t count,
+                          int32_t mode, const l1_options* opt, l1_handle* out);
+
+/*
+ * l1_group_load -- copy (and quantise) the dictionaries of instances
+ * first .. first+k-1 of a group handle from A[0..k-1] (layout as in
+ * l1_setup_group), then (re)compute their Lipschitz constants.  Lets a
+ * caller stream a group that does not fit in host or device memory in FP32.
+ */
+L1_API int l1_group_load(l1_handle h, int64_t first, int64_t k, const float* const* A);
+
+/*
+ * l1_solve_batch on a group handle: b packs the right-hand sides (instance i
+ * at offset sum_{k<i} m[k]), x packs the solutions (offset sum_{k<i} n[k]);
+ * N must equal count, ldb and ldx are ignored, y must be NULL.  res[i].resid
+ * is ||b - A x||_2 and primal_obj 1/2||b - A x||^2 + lambda ||x||_1;
+ * dual_obj and gap are NaN (not computed for groups).
+ */
+
+/*
  * l1_solve_batch -- solve N independent problems that share A, one per
  * column of b (m x N, leading dimension ldb >= m), 1 <= N <= 65535.
  *   tol       stopping tolerance of the relative-change rule (§VI-C); 0 runs

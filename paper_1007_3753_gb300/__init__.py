@@ -28,8 +28,9 @@ OK, ERR_INVALID_ARG, ERR_NOT_SPD, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_TAPE, E
 CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
 
 # every symbol include/l1alm.h declares
-EXPORTS = ("l1_options_init", "l1_setup", "l1_solve_batch", "l1_backward", "l1_set_stream",
-           "l1_get_info", "l1_destroy", "l1_status_string", "l1_last_error")
+EXPORTS = ("l1_options_init", "l1_setup", "l1_setup_group", "l1_group_load", "l1_solve_batch",
+           "l1_backward", "l1_set_stream", "l1_get_info", "l1_destroy", "l1_status_string",
+           "l1_last_error")
 
 
 class Options(C.Structure):
@@ -85,6 +86,11 @@ def load() -> C.CDLL:
     L.l1_options_init.restype = None
     L.l1_setup.argtypes = [vp, i64, i64, i64, i32, C.POINTER(Options), C.POINTER(vp)]
     L.l1_setup.restype = C.c_int
+    L.l1_setup_group.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), i64, i32, C.POINTER(Options),
+                                 C.POINTER(vp)]
+    L.l1_setup_group.restype = C.c_int
+    L.l1_group_load.argtypes = [vp, i64, i64, vp]
+    L.l1_group_load.restype = C.c_int
     L.l1_solve_batch.argtypes = [vp, vp, i64, i64, dbl, i32, vp, i64, vp, i64, C.POINTER(Result)]
     L.l1_solve_batch.restype = C.c_int
     L.l1_backward.argtypes = [vp, vp, i64, vp, vp]
@@ -241,6 +247,82 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Group:
+    """A handle over an uneven batch of (QP_lambda) problems (l1_setup_group).
+
+    ``As`` is a list of m_i x n_i FP32 arrays (numpy Fortran order, or CUDA
+    tensors in column-major layout), or None to load later with ``load``.
+    """
+
+    def __init__(self, As, ms, ns, lam: float, precision: int = A_FP32, lipschitz: float = 0.0,
+                 stream=None):
+        L = load()
+        o = Options()
+        L.l1_options_init(C.byref(o))
+        o.lambda_ = lam
+        o.precision = precision
+        o.lipschitz = lipschitz
+        o.stream = stream if stream is not None else _current_stream()
+        self.ms = np.ascontiguousarray(ms, dtype=np.int64)
+        self.ns = np.ascontiguousarray(ns, dtype=np.int64)
+        self.count = len(self.ms)
+        self.boff = np.concatenate([[0], np.cumsum(self.ms)])
+        self.xoff = np.concatenate([[0], np.cumsum(self.ns)])
+        h = C.c_void_p()
+        ptrs = None
+        keep = None
+        if As is not None:
+            keep = [np.asfortranarray(a, dtype=np.float32) if isinstance(a, np.ndarray) else a for a in As]
+            ptrs = (C.c_void_p * self.count)(*[_ptr(a).value for a in keep])
+        _check(L.l1_setup_group(ptrs, self.ms.ctypes.data_as(C.POINTER(C.c_int64)),
+                                self.ns.ctypes.data_as(C.POINTER(C.c_int64)), self.count, QP_LAMBDA,
+                                C.byref(o), C.byref(h)), "l1_setup_group")
+        self._h = h
+
+    def load(self, first: int, As):
+        keep = [np.asfortranarray(a, dtype=np.float32) if isinstance(a, np.ndarray) else a for a in As]
+        ptrs = (C.c_void_p * len(keep))(*[_ptr(a).value for a in keep])
+        _check(load().l1_group_load(self._h, first, len(keep), ptrs), "l1_group_load")
+
+    def solve(self, b_packed, tol: float, max_iter: int, x_packed=None):
+        """b_packed: sum(m_i) FP32 (numpy or torch); returns (x_packed, results)."""
+        if isinstance(b_packed, np.ndarray):
+            b_packed = np.ascontiguousarray(b_packed, dtype=np.float32)
+            if x_packed is None:
+                x_packed = np.zeros(int(self.xoff[-1]), dtype=np.float32)
+        elif x_packed is None:
+            import torch
+            x_packed = torch.empty(int(self.xoff[-1]), dtype=torch.float32, device=b_packed.device)
+        res = (Result * self.count)()
+        _check(load().l1_solve_batch(self._h, _ptr(b_packed), 0, self.count, float(tol), int(max_iter),
+                                     _ptr(x_packed), 0, None, 0, res), "l1_solve_batch(group)")
+        return x_packed, results_to_dict(res)
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().l1_get_info(self._h, C.byref(inf)), "l1_get_info")
+        return {k: (list(getattr(inf, k)) if k.startswith("sweep_") else getattr(inf, k))
+                for k, _ in Info._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().l1_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """FP32 -> nearest BF16 (ties to even), returned as FP32 (host helper for tests)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).copy()
+    u = (u + np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000)
+    return u.view(np.float32).reshape(np.shape(a))
 
 
 def results_to_dict(res) -> dict:

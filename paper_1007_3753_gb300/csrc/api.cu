@@ -199,9 +199,57 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
     return L1_OK;
 }
 
+int l1_setup_group(const float* const* A, const int64_t* m, const int64_t* n, int64_t count, int32_t mode,
+                   const l1_options* opt, l1_handle* out) {
+    if (!out) return L1_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!m || !n || count <= 0 || count > (1 << 22) || mode != L1_QP_LAMBDA) return L1_ERR_INVALID_ARG;
+    l1_options o;
+    if (opt) o = *opt;
+    else l1_options_init(&o);
+    if (!(o.lambda > 0.0)) return L1_ERR_INVALID_ARG;
+    if (o.precision != L1_A_FP32 && o.precision != L1_A_BF16) return L1_ERR_UNSUPPORTED;
+    for (int64_t i = 0; i < count; ++i)
+        if (m[i] <= 0 || n[i] <= 0) return L1_ERR_INVALID_ARG;
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return L1_ERR_OOM;
+    h->mode = mode;
+    h->opt = o;
+    h->opt.class_offsets = nullptr;
+    h->opt.solver = L1_PALM;
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    cudaGetDevice(&h->device);
+    int rc = group_setup(h, A, m, n, count);
+    if (rc == L1_OK) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("l1_setup_group: ") + cudaGetErrorString(e));
+            rc = L1_ERR_CUDA;
+        }
+    }
+    if (rc != L1_OK) {
+        free_all(h);
+        group_free(h);
+        delete h;
+        return rc;
+    }
+    *out = reinterpret_cast<l1_handle>(h);
+    return L1_OK;
+}
+
+int l1_group_load(l1_handle hh, int64_t first, int64_t k, const float* const* A) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || !h->grp || !A) return L1_ERR_INVALID_ARG;
+    return group_load(h, first, k, A);
+}
+
 int l1_solve_batch(l1_handle hh, const float* b, int64_t ldb, int64_t N, double tol, int32_t max_iter, float* x,
                    int64_t ldx, float* y, int64_t ldy, l1_result* res) {
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (h && h->grp) {
+        if (!b || !x || !res || y || max_iter <= 0 || !(tol >= 0.0)) return L1_ERR_INVALID_ARG;
+        return group_solve(h, b, N, tol, max_iter, x, res);
+    }
     if (!h || !b || !x || !res || N <= 0 || N > 65535 || max_iter <= 0 || !(tol >= 0.0)) return L1_ERR_INVALID_ARG;
     if (ldb < h->m) return L1_ERR_INVALID_ARG;
     const int64_t nx = (h->mode == L1_CAB) ? h->n + h->m : h->n;
@@ -256,6 +304,7 @@ int l1_destroy(l1_handle hh) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return L1_OK;
     free_all(h);
+    group_free(h);
     delete h;
     return L1_OK;
 }

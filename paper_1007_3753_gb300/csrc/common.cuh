@@ -139,6 +139,8 @@ struct Handle {
     std::vector<void*> allocations;
     // unrolled tape (differentiation)
     bool has_tape = false;
+    // uneven batch of independent dictionaries (l1_setup_group), see group.cu
+    struct GroupState* grp = nullptr;
     // sweep profiling (l1_options.profile)
     std::vector<cudaEvent_t> ev_pool;
     int64_t sweep_launches[4] = {0, 0, 0, 0};

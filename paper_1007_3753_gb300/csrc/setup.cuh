@@ -15,6 +15,12 @@ int power_iteration(Handle* h, int max_iter, double rtol, double* L_out);
 // L1_ERR_NOT_SPD when a pivot is not positive beyond rounding
 int dalm_factor(Handle* h, double diag_add);
 
+// uneven groups of independent dictionaries (group.cu)
+int group_setup(Handle* h, const float* const* A, const int64_t* m, const int64_t* n, int64_t count);
+int group_load(Handle* h, int64_t first, int64_t k, const float* const* A);
+int group_solve(Handle* h, const float* b, int64_t N, double tol, int max_iter, float* x, l1_result* res);
+void group_free(Handle* h);
+
 // batched solve (solve.cu)
 int solve_batch(Handle* h, const float* b_dev, int64_t ldb, int N, double tol, int max_iter,
                 float* x_dev, int64_t ldx, float* y_dev, int64_t ldy, l1_result* res);
