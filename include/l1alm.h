@@ -221,6 +221,34 @@ L1_API int l1_solve_batch(l1_handle h, const float* b, int64_t ldb, int64_t N, d
 L1_API int l1_backward(l1_handle h, const float* grad_x, int64_t N, float* grad_b,
                        float* grad_A);
 
+/*
+ * l1_lipschitz_static -- the power-iteration estimate of ||A||_2^2 that
+ * l1_setup makes (start vector 1/sqrt(n), Rayleigh quotient ||A v||^2, stop
+ * when it changes by at most rtol relative or after max_iter iterations;
+ * l1_setup takes L = 1.01 x this), computed without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not call cudaMalloc or cudaFree -- a process whose device memory is owned by
+ * its own pool allocator, or a loop that must not stall the device while
+ * memory is allocated or freed.
+ *   A        device (or managed) memory, m x n, column-major, leading
+ *            dimension lda >= m; on the current device; read only.
+ *   stream   the work is enqueued there (NULL: the legacy default stream)
+ *            and the call returns after synchronising it.
+ *   rho_out  host pointer; receives the estimate.
+ * Scratch: one static device array of 1.34 MiB per GPU that loads this
+ * library, held until the process exits; hence m <= 8192 and n <= 65536.
+ * Larger sizes return L1_ERR_INVALID_ARG with a message in l1_last_error.
+ * The first call on a device looks up that array's device address (once,
+ * with that device current); make that first call before any stream
+ * capture.  Each call initialises the scratch it reads, but every call on a
+ * device shares the one array: calls that can overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Errors: L1_ERR_INVALID_ARG (null pointer, a size <= 0 or above the limits,
+ * lda < m, max_iter <= 0, rtol < 0, A not device memory), L1_ERR_CUDA.
+ */
+L1_API int l1_lipschitz_static(const float* A, int64_t m, int64_t n, int64_t lda, int32_t max_iter,
+                               double rtol, void* stream, double* rho_out);
+
 /* Set the stream later calls enqueue on. */
 L1_API int l1_set_stream(l1_handle h, void* stream);
 
@@ -233,7 +261,8 @@ L1_API int l1_destroy(l1_handle h);
 /* Static string naming a return code or status. */
 L1_API const char* l1_status_string(int code);
 
-/* Message of the last L1_ERR_CUDA on this thread (static storage). */
+/* Message of the last L1_ERR_CUDA (or of a rejected size) on this thread
+ * (static storage). */
 L1_API const char* l1_last_error(void);
 
 #ifdef __cplusplus

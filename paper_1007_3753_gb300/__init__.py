@@ -30,7 +30,7 @@ CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
 # every symbol include/l1alm.h declares
 EXPORTS = ("l1_options_init", "l1_setup", "l1_setup_group", "l1_group_load", "l1_solve_batch",
            "l1_backward", "l1_set_stream", "l1_get_info", "l1_destroy", "l1_status_string",
-           "l1_last_error")
+           "l1_last_error", "l1_lipschitz_static")
 
 
 class Options(C.Structure):
@@ -105,6 +105,8 @@ def load() -> C.CDLL:
     L.l1_status_string.restype = C.c_char_p
     L.l1_last_error.argtypes = []
     L.l1_last_error.restype = C.c_char_p
+    L.l1_lipschitz_static.argtypes = [vp, i64, i64, i64, i32, dbl, vp, C.POINTER(dbl)]
+    L.l1_lipschitz_static.restype = C.c_int
     _lib = L
     return L
 
@@ -316,6 +318,23 @@ class Group:
             self.close()
         except Exception:
             pass
+
+
+def lipschitz_static(A, max_iter: int = 1000, rtol: float = 1e-6, stream=None) -> float:
+    """Power-iteration estimate of ||A||_2^2 without any allocation.
+
+    ``A`` is a device-resident m x n FP32 column-major tensor (m <= 8192,
+    n <= 65536).  For callers that may not allocate device memory; every
+    call shares one static scratch array per GPU, so calls that can overlap
+    on the GPU must be serialised.  The first call on a device should come
+    before any stream capture.  A handle's L is 1.01 times this estimate."""
+    L = load()
+    m, n = A.shape
+    rho = C.c_double(0.0)
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    _check(L.l1_lipschitz_static(_ptr(A), m, n, _ld(A), max_iter, rtol, st, C.byref(rho)),
+           "l1_lipschitz_static")
+    return rho.value
 
 
 def bf16_round(a: np.ndarray) -> np.ndarray:
