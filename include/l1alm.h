@@ -211,12 +211,29 @@ L1_API int l1_solve_batch(l1_handle h, const float* b, int64_t ldb, int64_t N, d
                           l1_result* res);
 
 /*
- * l1_backward -- after an l1_solve_batch of a handle set up with
- * unroll_K > 0 (K unrolled PALM steps in P1 mode, multiplier update every J
- * steps, xi and L held constant), propagate grad_x (n x N, the adjoint of the
- * returned x) back to grad_b (m x N, nullable) and grad_A (m x n, nullable,
- * leading dimension m, overwritten).  Errors: L1_ERR_NO_TAPE,
- * L1_ERR_INVALID_ARG, L1_ERR_OOM, L1_ERR_CUDA.
+ * l1_solve_batch on a handle set up with unroll_K > 0 (mode L1_P1, solver
+ * L1_PALM): runs exactly K inner FISTA steps of Algorithm 1 in total, with the
+ * multiplier step theta += xi (b - A x) after every unroll_J inner steps and
+ * FISTA restarted (t = 1, z = w = x) at each block start (reading R11).  xi is
+ * xi0, or 2m/||b||_1 per column when xi0 = 0, and stays constant; L is the
+ * handle's.  tol and max_iter are ignored; y must be NULL.  Every column
+ * reports L1_MAX_ITER with iters = ceil(K / J) and inner_iters = K,
+ * primal_obj = ||x||_1, resid = ||b - A x||, param = xi; rel_change, dual_obj
+ * and gap are NaN.  The call keeps a tape for l1_backward: (z, w, theta) every
+ * ckpt_every steps and x at the end of every block.
+ */
+
+/*
+ * l1_backward -- reverse-mode derivative of that unrolled forward (R11: xi and
+ * L held constant; the soft-threshold derivative is 1 where |v| > 1/(xi L),
+ * else 0).  grad_x (n x N, leading dimension n, host or device) is the
+ * adjoint of the x the forward returned; N must equal the forward's N.  Each
+ * checkpointed segment is recomputed once and then reversed.  Outputs (host
+ * or device, nullable): grad_b (m x N, leading dimension m) and grad_A
+ * (m x n, leading dimension m, the sum over the N columns); both are
+ * overwritten.  Returns after the outputs are written.  Errors:
+ * L1_ERR_NO_TAPE (no unrolled forward yet), L1_ERR_INVALID_ARG (N differs,
+ * null grad_x), L1_ERR_OOM, L1_ERR_CUDA.
  */
 L1_API int l1_backward(l1_handle h, const float* grad_x, int64_t N, float* grad_b,
                        float* grad_A);

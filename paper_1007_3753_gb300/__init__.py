@@ -157,7 +157,8 @@ class Solver:
                  xi_growth: float = 0.0, xi_max: float = 0.0, lipschitz: float = 0.0,
                  inner_max: int = 0, inner_tol: float = 0.0, check_every: int = 0,
                  class_offsets=None, precision: int = A_FP32, engine: int = ENGINE_AUTO,
-                 profile: bool = False, tc_sweeps: int = 0, stream=None):
+                 profile: bool = False, tc_sweeps: int = 0, unroll_K: int = 0, unroll_J: int = 0,
+                 ckpt_every: int = 0, stream=None):
         L = load()
         o = Options()
         L.l1_options_init(C.byref(o))
@@ -172,6 +173,11 @@ class Solver:
         o.lipschitz, o.inner_tol = lipschitz, inner_tol
         o.profile = 1 if profile else 0
         o.tc_sweeps = tc_sweeps
+        o.unroll_K = unroll_K
+        if unroll_J:
+            o.unroll_J = unroll_J
+        if ckpt_every:
+            o.ckpt_every = ckpt_every
         if check_every:
             o.check_every = check_every
         self._offsets = None
@@ -235,6 +241,33 @@ class Solver:
         _check(L.l1_solve_batch(self._h, _ptr(b), _ld(b), N, float(tol), int(max_iter), _ptr(x), _ld(x),
                                 _ptr(y), _ld(y) if y is not None else 0, res), "l1_solve_batch")
         return x, y, results_to_dict(res)
+
+    def backward(self, grad_x, grad_b=None, grad_A=None, want_b: bool = True, want_A: bool = True):
+        """l1_backward after an unrolled forward: grad_x is n x N (column-major,
+        like x); returns (grad_b m x N, grad_A m x n), allocated like grad_x
+        when not given (None where not wanted)."""
+        L = load()
+        is_np = isinstance(grad_x, np.ndarray)
+        if is_np:
+            grad_x = np.asfortranarray(grad_x, dtype=np.float32)
+        if _ld(grad_x) != self.n:
+            raise ValueError("grad_x must be n x N with leading dimension n")
+        N = grad_x.shape[1]
+
+        def alloc(rows, cols):
+            if is_np:
+                return np.zeros((rows, cols), dtype=np.float32, order="F")
+            import torch
+            return torch.empty((cols, rows), dtype=torch.float32, device=grad_x.device).t()
+        if grad_b is None and want_b:
+            grad_b = alloc(self.m, N)
+        if grad_A is None and want_A:
+            grad_A = alloc(self.m, self.n)
+        for t in (grad_b, grad_A):
+            if t is not None and _ld(t) != self.m:
+                raise ValueError("grad_b and grad_A must have leading dimension m")
+        _check(L.l1_backward(self._h, _ptr(grad_x), N, _ptr(grad_b), _ptr(grad_A)), "l1_backward")
+        return grad_b, grad_A
 
     def set_stream(self, stream):
         _check(load().l1_set_stream(self._h, stream), "l1_set_stream")
@@ -335,6 +368,46 @@ def lipschitz_static(A, max_iter: int = 1000, rtol: float = 1e-6, stream=None) -
     _check(L.l1_lipschitz_static(_ptr(A), m, n, _ld(A), max_iter, rtol, st, C.byref(rho)),
            "l1_lipschitz_static")
     return rho.value
+
+
+def _colmajor(t):
+    """CUDA tensor -> column-major FP32 copy (the layout the C ABI reads)."""
+    t = t.detach().to(dtype=__import__("torch").float32)
+    return t.t().contiguous().t()
+
+
+def unrolled_palm(A, b, K: int, J: int = 10, ckpt_every: int = 20, xi: float = 0.0,
+                  lipschitz: float = 0.0):
+    """x = K unrolled PALM steps (P1 mode) on CUDA tensors A (m x n) and b
+    (m x N), differentiable with respect to A and b through l1_backward.
+
+    xi (0: 2m/||b||_1 per column) and L (0: power iteration x 1.01) are
+    held constant.  The autograd glue only moves pointers; every step runs in
+    the library's kernels."""
+    import torch
+
+    class _Unrolled(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, A_, b_):
+            s = Solver(_colmajor(A_), mode=P1, solver=PALM, xi0=xi, lipschitz=lipschitz,
+                       unroll_K=K, unroll_J=J, ckpt_every=ckpt_every,
+                       stream=torch.cuda.current_stream(A_.device).cuda_stream)
+            x, _, res = s.solve(_colmajor(b_), 0.0, 1)
+            ctx.solver = s
+            ctx.results = res
+            return x.contiguous()
+
+        @staticmethod
+        def backward(ctx, gx):
+            s = ctx.solver
+            gb, gA = s.backward(_colmajor(gx), want_b=ctx.needs_input_grad[1],
+                                want_A=ctx.needs_input_grad[0])
+            s.close()
+            return gA, gb
+
+    squeeze = b.dim() == 1
+    x = _Unrolled.apply(A, b.reshape(b.shape[0], -1))
+    return x.reshape(-1) if squeeze else x
 
 
 def bf16_round(a: np.ndarray) -> np.ndarray:

@@ -108,7 +108,13 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
     if (mode == L1_P1_2) return L1_ERR_UNSUPPORTED;
     if (o.precision != L1_A_FP32) return L1_ERR_UNSUPPORTED;
     if (o.engine == L1_ENGINE_TC && (o.solver != L1_DALM || mode == L1_QP_LAMBDA)) return L1_ERR_UNSUPPORTED;
-    if (o.unroll_K > 0) return L1_ERR_UNSUPPORTED;
+    if (o.unroll_K < 0 || o.unroll_J < 0 || o.ckpt_every < 0) return L1_ERR_INVALID_ARG;
+    if (o.unroll_K > 0) {
+        // R11: unrolled PALM in P1 mode on the CUDA cores
+        if (mode != L1_P1 || o.solver != L1_PALM || o.engine == L1_ENGINE_TC) return L1_ERR_UNSUPPORTED;
+        if (o.unroll_J == 0) o.unroll_J = 10;
+        if (o.ckpt_every == 0) o.ckpt_every = 20;
+    }
 
     Handle* h = new (std::nothrow) Handle();
     if (!h) return L1_ERR_OOM;
@@ -255,21 +261,26 @@ int l1_solve_batch(l1_handle hh, const float* b, int64_t ldb, int64_t N, double 
     const int64_t nx = (h->mode == L1_CAB) ? h->n + h->m : h->n;
     if (ldx < nx) return L1_ERR_INVALID_ARG;
     if (y && ldy < h->m) return L1_ERR_INVALID_ARG;
+    if (h->opt.unroll_K > 0 && y) return L1_ERR_INVALID_ARG;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != h->device) cudaSetDevice(h->device);
-    int rc = solve_batch(h, b, ldb, (int)N, tol, max_iter, x, ldx, y, ldy, res);
+    int rc = h->opt.unroll_K > 0 ? unroll_forward(h, b, ldb, (int)N, x, ldx, res)
+                                 : solve_batch(h, b, ldb, (int)N, tol, max_iter, x, ldx, y, ldy, res);
     if (dev != h->device) cudaSetDevice(dev);
     return rc;
 }
 
 int l1_backward(l1_handle hh, const float* grad_x, int64_t N, float* grad_b, float* grad_A) {
     Handle* h = reinterpret_cast<Handle*>(hh);
-    if (!h || !grad_x || N <= 0) return L1_ERR_INVALID_ARG;
-    (void)grad_b;
-    (void)grad_A;
-    if (!h->has_tape) return L1_ERR_NO_TAPE;
-    return L1_ERR_UNSUPPORTED;
+    if (!h || !grad_x || N <= 0 || N > 65535) return L1_ERR_INVALID_ARG;
+    if (!h->has_tape || !h->ur) return L1_ERR_NO_TAPE;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != h->device) cudaSetDevice(h->device);
+    int rc = unroll_backward(h, grad_x, (int)N, grad_b, grad_A);
+    if (dev != h->device) cudaSetDevice(dev);
+    return rc;
 }
 
 int l1_set_stream(l1_handle hh, void* stream) {
@@ -305,6 +316,7 @@ int l1_destroy(l1_handle hh) {
     if (!h) return L1_OK;
     free_all(h);
     group_free(h);
+    unroll_free(h);
     delete h;
     return L1_OK;
 }

@@ -137,8 +137,9 @@ struct Handle {
     std::vector<int32_t> class_offsets;  // host copy
     Workspace ws;
     std::vector<void*> allocations;
-    // unrolled tape (differentiation)
+    // unrolled PALM and its tape (differentiation), see unroll.cu
     bool has_tape = false;
+    struct UnrollState* ur = nullptr;
     // uneven batch of independent dictionaries (l1_setup_group), see group.cu
     struct GroupState* grp = nullptr;
     // sweep profiling (l1_options.profile)

@@ -21,6 +21,11 @@ int group_load(Handle* h, int64_t first, int64_t k, const float* const* A);
 int group_solve(Handle* h, const float* b, int64_t N, double tol, int max_iter, float* x, l1_result* res);
 void group_free(Handle* h);
 
+// unrolled PALM with a checkpointed tape and its adjoint (unroll.cu)
+int unroll_forward(Handle* h, const float* b, int64_t ldb, int N, float* x, int64_t ldx, l1_result* res);
+int unroll_backward(Handle* h, const float* grad_x, int N, float* grad_b, float* grad_A);
+void unroll_free(Handle* h);
+
 // batched solve (solve.cu)
 int solve_batch(Handle* h, const float* b_dev, int64_t ldb, int N, double tol, int max_iter,
                 float* x_dev, int64_t ldx, float* y_dev, int64_t ldy, l1_result* res);
