@@ -105,8 +105,11 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
             if (o.class_offsets[c + 1] <= o.class_offsets[c]) return L1_ERR_INVALID_ARG;
     }
     // not implemented in this build
-    if (mode == L1_P1_2) return L1_ERR_UNSUPPORTED;
-    if (o.precision != L1_A_FP32) return L1_ERR_UNSUPPORTED;
+    if (mode == L1_P1_2 && o.solver != L1_PALM) return L1_ERR_UNSUPPORTED;  // R10 is a PALM
+    // low-precision A: batched DALM on the CUDA-core sweeps (with refinement)
+    if (o.precision != L1_A_FP32 &&
+        (o.solver != L1_DALM || mode == L1_QP_LAMBDA || o.engine == L1_ENGINE_TC || o.unroll_K > 0))
+        return L1_ERR_UNSUPPORTED;
     if (o.engine == L1_ENGINE_TC && (o.solver != L1_DALM || mode == L1_QP_LAMBDA)) return L1_ERR_UNSUPPORTED;
     if (o.unroll_K < 0 || o.unroll_J < 0 || o.ckpt_every < 0) return L1_ERR_INVALID_ARG;
     if (o.unroll_K > 0) {
@@ -127,6 +130,7 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
     h->opt.class_offsets = nullptr;
     h->stream = static_cast<cudaStream_t>(o.stream);
     cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     if (o.class_count > 0) h->class_offsets.assign(o.class_offsets, o.class_offsets + o.class_count + 1);
 
     int rc = L1_OK;
@@ -148,6 +152,10 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
         }
         rc = make_layouts(h, stage, m);
         if (rc) break;
+        if (o.precision != L1_A_FP32) {
+            rc = make_lowp(h);
+            if (rc) break;
+        }
         // tensor-core engine (batched DALM): TF32 pieces of both layouts of A
         h->use_tc = (o.engine == L1_ENGINE_TC) && o.solver == L1_DALM && mode != L1_QP_LAMBDA;
         if (h->use_tc) {

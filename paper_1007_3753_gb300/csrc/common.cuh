@@ -93,7 +93,9 @@ struct Workspace {
     float* hWx = nullptr;
     float* hWe = nullptr;
     float* hY = nullptr;
-    int32_t* hcoli = nullptr;  // [8][cap]: status, iters, inner, label, sci_label
+    float* hUx = nullptr;  // low-precision A only: z - w/beta at retirement (refinement restart)
+    float* hUe = nullptr;
+    int32_t* hcoli = nullptr;  // [8][cap]: status, iters, inner, label, sci_label, first-phase iters
     double* hcold = nullptr;   // [10][cap]: rel, param, fin[8] (interleaved per column)
     float* hcolf = nullptr;    // [2][cap]: xi, smax
     double* part = nullptr;    // reduction partials, 2 x [slots][N][4]
@@ -113,11 +115,22 @@ struct Handle {
     l1_options opt{};
     cudaStream_t stream = nullptr;
     int device = 0;
+    int sms = 0;  // multiprocessors of the device
+    // split-K slices of the narrow CUDA-core sweeps (grows on demand)
+    float* splitk = nullptr;
+    size_t splitk_floats = 0;
     // dictionary
     float* A_cm = nullptr;  // column-major m x n, ld = ldm  (rows of A^T contiguous: K-major for A^T y)
     float* A_rm = nullptr;  // row-major m x n, ld = ldn     (K-major for A u)
     float* F = nullptr;     // DALM: (B B^T)^{-1}, m x m symmetric, ld = ldm (high FP32 part)
     float* F_lo = nullptr;  // low FP32 part: F + F_lo = (B B^T)^{-1} to ~48 bits
+    // low-precision copies of both layouts of A (l1_options.precision BF16 or
+    // FP8 e4m3; same leading dimensions); FP8 carries one FP32 scale per row
+    // of each layout: A_rm(i, k) = A_rm_scale[i] q(i, k), A_cm likewise
+    void* A_rm_lp = nullptr;
+    void* A_cm_lp = nullptr;
+    float* A_rm_scale = nullptr;
+    float* A_cm_scale = nullptr;
     // tensor-core engine: TF32 pieces (p1 + p2 (+ p3) == value) of the operands
     bool use_tc = false;
     float* A_rm_p[2] = {nullptr, nullptr};

@@ -17,11 +17,48 @@
 // reduction is deterministic.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 
 namespace l1 {
 
 constexpr int kPartStride = 4;  // doubles per (row block, column) partial
+
+// ------------------------------------------------------ element types of Aop
+// Aop may be FP32, BF16 or FP8 e4m3 (one byte, wrapped so that overloads can
+// tell it apart); the sweeps convert four consecutive K elements to FP32 as
+// they load them and accumulate in FP32.
+struct fp8e4m3 {
+    uint8_t v;
+};
+
+__device__ __forceinline__ float4 load_a4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+__device__ __forceinline__ float4 load_a4(const __nv_bfloat16* p) {
+    // a BF16 value is the high half of the FP32 value with the same bits
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+
+__device__ __forceinline__ float4 load_a4(const fp8e4m3* p) {
+    const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
+    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3);
+    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3);
+    const float2 a = __half22float2(__half2(lo)), b = __half22float2(__half2(hi));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Output-row scale of an FP8 operand (Aop(i, k) = scale[i] q(i, k)).
+template <class E>
+struct EpiRowScale {
+    static constexpr int NRED = E::NRED;
+    const float* scale;
+    E inner;
+    __device__ void operator()(int i, int j, float acc, double* red) const { inner(i, j, acc * scale[i], red); }
+};
 
 // ------------------------------------------------------------------- GEMV
 // N <= NC columns (NC in 1..8): one warp per row, 128-bit loads along K.
@@ -33,9 +70,9 @@ constexpr int kGemvRowsPerWarp = 1;
 // Aop2 (nullable) is the low part of a split operand Aop + Aop2 (same
 // layout): its products go to a separate accumulator that is added last, so
 // the small terms are not absorbed by the large ones.
-template <int NC, class E>
+template <int NC, class E, class TA>
 __global__ void __launch_bounds__(kGemvWarps * 32)
-gemv_kernel(int M, int N, int K, const float* __restrict__ Aop, const float* __restrict__ Aop2,
+gemv_kernel(int M, int N, int K, const TA* __restrict__ Aop, const TA* __restrict__ Aop2,
             int64_t lda, const float* __restrict__ X, int64_t ldx, E epi, double* __restrict__ part) {
     constexpr int NR = E::NRED > 0 ? E::NRED : 1;
     __shared__ double red_s[kGemvWarps][NC][NR];
@@ -51,12 +88,12 @@ gemv_kernel(int M, int N, int K, const float* __restrict__ Aop, const float* __r
         float acc[NC], acc2[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = acc2[c] = 0.0f;
-        const float* arow = Aop + (int64_t)i * lda;
-        const float* arow2 = Aop2 ? Aop2 + (int64_t)i * lda : nullptr;
+        const TA* arow = Aop + (int64_t)i * lda;
+        const TA* arow2 = Aop2 ? Aop2 + (int64_t)i * lda : nullptr;
         for (int k = lane * 4; k < Kp; k += 128) {
-            const float4 a = __ldg(reinterpret_cast<const float4*>(arow + k));
+            const float4 a = load_a4(arow + k);
             float4 a2 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (arow2) a2 = __ldg(reinterpret_cast<const float4*>(arow2 + k));
+            if (arow2) a2 = load_a4(arow2 + k);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 if (c < N) {
@@ -112,74 +149,80 @@ gemv_kernel(int M, int N, int K, const float* __restrict__ Aop, const float* __r
 // 64 x 64 output tile per 256-thread CTA, 4 x 4 per thread, K step 16,
 // double-buffered shared memory.
 constexpr int kBM = 64, kBN = 64, kBK = 16;
+constexpr int kMaxSplitK = 8;
 
-template <class E, bool SPLIT>
-__global__ void __launch_bounds__(256)
-gemm_simt_kernel(int M, int N, int K, const float* __restrict__ Aop, const float* __restrict__ Aop2,
-                 int64_t lda, const float* __restrict__ X, int64_t ldx, E epi,
-                 double* __restrict__ part, const int32_t* __restrict__ active) {
-    constexpr int NR = E::NRED > 0 ? E::NRED : 1;
-    __shared__ __align__(16) float As[2][kBK][kBM];
-    __shared__ __align__(16) float As2[SPLIT ? 2 : 1][SPLIT ? kBK : 1][SPLIT ? kBM : 4];
-    __shared__ __align__(16) float Xs[2][kBK][kBN];
-    __shared__ double red_s[8][kBN][NR];
-    __shared__ int any_active;
+template <bool SPLIT>
+struct SimtSmem {
+    float As[2][kBK][kBM];
+    float As2[SPLIT ? 2 : 1][SPLIT ? kBK : 1][SPLIT ? kBM : 4];
+    float Xs[2][kBK][kBN];
+};
 
+// true when some column of the tile starting at n0 is still active (all
+// threads of the CTA get the same answer)
+__device__ __forceinline__ bool tile_has_active(const int32_t* active, int N, int n0, int* flag) {
+    if (active == nullptr) return true;
+    const int t = threadIdx.x;
+    if (t == 0) *flag = 0;
+    __syncthreads();
+    if (t < kBN && n0 + t < N && active[n0 + t]) *flag = 1;
+    __syncthreads();
+    return *flag != 0;
+}
+
+// Main loop of one 64 x 64 tile over K in [k_begin, k_end) (multiples of 4,
+// k_end <= round_up(K, 4)).  Each K tile of 16 products is summed into a
+// fresh FP32 partial, and the partials are merged with Kahan compensation, so
+// the rounding error grows with the number of K tiles, not with K.  The low
+// part of a split operand (Aop2) has its own accumulator, added last.
+// out[p][q] is the sum for row m0 + tr*4 + p and column n0 + tc*4 + q.
+template <bool SPLIT, class TA>
+__device__ __forceinline__ void simt_tile_mainloop(int M, int N, int m0, int n0, int k_begin, int k_end,
+                                                   const TA* __restrict__ Aop, const TA* __restrict__ Aop2,
+                                                   int64_t lda, const float* __restrict__ X, int64_t ldx,
+                                                   SimtSmem<SPLIT>& sm, float (&out)[4][4]) {
     const int t = threadIdx.x;
     const int tc = t & 15, tr = t >> 4;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-
-    if (active != nullptr) {
-        if (t == 0) any_active = 0;
-        __syncthreads();
-        if (t < kBN && n0 + t < N && active[n0 + t]) any_active = 1;
-        __syncthreads();
-        if (!any_active) {
-            // every column of this tile is frozen: nothing to compute, but the
-            // partials must still be defined for the controller
-            if constexpr (E::NRED > 0) {
-                if (t < kBN && n0 + t < N)
-                    for (int r = 0; r < NR; ++r)
-                        part[((int64_t)blockIdx.y * N + n0 + t) * kPartStride + r] = 0.0;
-            }
-            return;
-        }
-    }
-
     // load mapping: one float4 of Aop and one of X per thread per K step
+    // (four lanes per row, 64 contiguous bytes).  The transposing stores put
+    // row r of K slice k at r ^ swz(k): the four lanes of a row write four
+    // slices whose swizzles differ in bits 3-4, so a warp's stores hit 32
+    // distinct banks; reads apply the same swizzle to a 4-aligned group.
     const int la_row = t >> 2, la_k = (t & 3) * 4;  // 64 rows x 4 float4
     const int lx_col = t >> 2, lx_k = (t & 3) * 4;  // 64 cols x 4 float4
-    const int Kp = (K + 3) & ~3;
+    auto swz = [](int k) { return ((k >> 2) & 3) << 3; };
 
-    auto load_tiles = [&](int buf, int k0) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), x = make_float4(0.f, 0.f, 0.f, 0.f);
+    // global -> registers (issued a K step ahead) -> shared memory (stored
+    // after the current step's FMAs), so the L2 latency overlaps the math
+    float4 ra_g, ra2_g, rx_g;
+    auto fetch = [&](int k0) {
+        ra_g = ra2_g = rx_g = make_float4(0.f, 0.f, 0.f, 0.f);
         const int gi = m0 + la_row, gk = k0 + la_k;
-        if (gi < M && gk < Kp) a = __ldg(reinterpret_cast<const float4*>(Aop + (int64_t)gi * lda + gk));
-        if constexpr (SPLIT) {
-            float4 a2 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gi < M && gk < Kp) a2 = __ldg(reinterpret_cast<const float4*>(Aop2 + (int64_t)gi * lda + gk));
-            As2[buf][la_k + 0][la_row] = a2.x;
-            As2[buf][la_k + 1][la_row] = a2.y;
-            As2[buf][la_k + 2][la_row] = a2.z;
-            As2[buf][la_k + 3][la_row] = a2.w;
+        if (gi < M && gk < k_end) {
+            ra_g = load_a4(Aop + (int64_t)gi * lda + gk);
+            if constexpr (SPLIT) ra2_g = load_a4(Aop2 + (int64_t)gi * lda + gk);
         }
         const int gj = n0 + lx_col, gkx = k0 + lx_k;
-        if (gj < N && gkx < Kp) x = __ldg(reinterpret_cast<const float4*>(X + (int64_t)gj * ldx + gkx));
-        As[buf][la_k + 0][la_row] = a.x;
-        As[buf][la_k + 1][la_row] = a.y;
-        As[buf][la_k + 2][la_row] = a.z;
-        As[buf][la_k + 3][la_row] = a.w;
-        Xs[buf][lx_k + 0][lx_col] = x.x;
-        Xs[buf][lx_k + 1][lx_col] = x.y;
-        Xs[buf][lx_k + 2][lx_col] = x.z;
-        Xs[buf][lx_k + 3][lx_col] = x.w;
+        if (gj < N && gkx < k_end) rx_g = __ldg(reinterpret_cast<const float4*>(X + (int64_t)gj * ldx + gkx));
+    };
+    auto stash = [&](int buf) {
+        const int ra = la_row ^ swz(la_k), rx = lx_col ^ swz(lx_k);
+        if constexpr (SPLIT) {
+            sm.As2[buf][la_k + 0][ra] = ra2_g.x;
+            sm.As2[buf][la_k + 1][ra] = ra2_g.y;
+            sm.As2[buf][la_k + 2][ra] = ra2_g.z;
+            sm.As2[buf][la_k + 3][ra] = ra2_g.w;
+        }
+        sm.As[buf][la_k + 0][ra] = ra_g.x;
+        sm.As[buf][la_k + 1][ra] = ra_g.y;
+        sm.As[buf][la_k + 2][ra] = ra_g.z;
+        sm.As[buf][la_k + 3][ra] = ra_g.w;
+        sm.Xs[buf][lx_k + 0][rx] = rx_g.x;
+        sm.Xs[buf][lx_k + 1][rx] = rx_g.y;
+        sm.Xs[buf][lx_k + 2][rx] = rx_g.z;
+        sm.Xs[buf][lx_k + 3][rx] = rx_g.w;
     };
 
-    // Accumulation: each K tile of 16 products is summed into a fresh FP32
-    // partial t, and the partials are merged into acc with Kahan
-    // compensation (comp), so the rounding error grows with the number of
-    // tiles, not with K.  The low part of a split operand (Aop2) has its own
-    // accumulator, added last.
     float acc[4][4], comp[4][4], acc2[SPLIT ? 4 : 1][SPLIT ? 4 : 1];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -193,28 +236,37 @@ gemm_simt_kernel(int M, int N, int K, const float* __restrict__ Aop, const float
     }
 
     int buf = 0;
-    load_tiles(0, 0);
+    fetch(k_begin);
+    stash(0);
     __syncthreads();
-    for (int k0 = 0; k0 < Kp; k0 += kBK) {
-        if (k0 + kBK < Kp) load_tiles(buf ^ 1, k0 + kBK);
-        float t[4][4];
+    for (int k0 = k_begin; k0 < k_end; k0 += kBK) {
+        const bool more = k0 + kBK < k_end;
+        if (more) fetch(k0 + kBK);
+        float tt[4][4];
 #pragma unroll
         for (int p = 0; p < 4; ++p)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) t[p][q] = 0.0f;
+            for (int q = 0; q < 4; ++q) tt[p][q] = 0.0f;
+        // fragments of slice kk + 1 are read before the FMAs of slice kk
+        float4 fa = *reinterpret_cast<const float4*>(&sm.As[buf][0][(tr * 4) ^ swz(0)]);
+        float4 fx = *reinterpret_cast<const float4*>(&sm.Xs[buf][0][(tc * 4) ^ swz(0)]);
+        float4 fa2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (SPLIT) fa2 = *reinterpret_cast<const float4*>(&sm.As2[buf][0][(tr * 4) ^ swz(0)]);
 #pragma unroll
         for (int kk = 0; kk < kBK; ++kk) {
-            const float4 a = *reinterpret_cast<const float4*>(&As[buf][kk][tr * 4]);
-            const float4 x = *reinterpret_cast<const float4*>(&Xs[buf][kk][tc * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w};
-            const float xv[4] = {x.x, x.y, x.z, x.w};
+            const float av[4] = {fa.x, fa.y, fa.z, fa.w};
+            const float xv[4] = {fx.x, fx.y, fx.z, fx.w};
+            const float av2[4] = {fa2.x, fa2.y, fa2.z, fa2.w};
+            if (kk + 1 < kBK) {
+                fa = *reinterpret_cast<const float4*>(&sm.As[buf][kk + 1][(tr * 4) ^ swz(kk + 1)]);
+                fx = *reinterpret_cast<const float4*>(&sm.Xs[buf][kk + 1][(tc * 4) ^ swz(kk + 1)]);
+                if constexpr (SPLIT) fa2 = *reinterpret_cast<const float4*>(&sm.As2[buf][kk + 1][(tr * 4) ^ swz(kk + 1)]);
+            }
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) t[p][q] = fmaf(av[p], xv[q], t[p][q]);
+                for (int q = 0; q < 4; ++q) tt[p][q] = fmaf(av[p], xv[q], tt[p][q]);
             if constexpr (SPLIT) {
-                const float4 a2 = *reinterpret_cast<const float4*>(&As2[buf][kk][tr * 4]);
-                const float av2[4] = {a2.x, a2.y, a2.z, a2.w};
 #pragma unroll
                 for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -225,27 +277,33 @@ gemm_simt_kernel(int M, int N, int K, const float* __restrict__ Aop, const float
         for (int p = 0; p < 4; ++p)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float yv = t[p][q] - comp[p][q];
+                const float yv = tt[p][q] - comp[p][q];
                 const float sv = acc[p][q] + yv;
                 comp[p][q] = (sv - acc[p][q]) - yv;
                 acc[p][q] = sv;
             }
+        if (more) stash(buf ^ 1);
         __syncthreads();
         buf ^= 1;
     }
-    if constexpr (SPLIT) {
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 4; ++p)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[p][q] += acc2[p][q] - comp[p][q];
-    } else {
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[p][q] -= comp[p][q];
-    }
+        for (int q = 0; q < 4; ++q) {
+            if constexpr (SPLIT) out[p][q] = acc[p][q] + (acc2[p][q] - comp[p][q]);
+            else out[p][q] = acc[p][q] - comp[p][q];
+        }
+}
 
-    // epilogue
+// Epilogue of one tile: E on every element, then the per-column reduction
+// terms of the tile's rows in a fixed order (warp shuffles, shared memory) to
+// part[(row_block * N + j) * 4 + r].
+template <class E, int NR>
+__device__ __forceinline__ void simt_tile_epilogue(int M, int N, int m0, int n0, int row_block,
+                                                   const float (&acc)[4][4], const E& epi, double* part,
+                                                   double (*red_s)[kBN][NR]) {
+    const int t = threadIdx.x;
+    const int tc = t & 15, tr = t >> 4;
     double red[4][NR];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -285,26 +343,133 @@ gemm_simt_kernel(int M, int N, int K, const float* __restrict__ Aop, const float
             if (j < N) {
                 double s = 0.0;
                 for (int w = 0; w < 8; ++w) s += red_s[w][c][r];
-                part[((int64_t)blockIdx.y * N + j) * kPartStride + r] = s;
+                part[((int64_t)row_block * N + j) * kPartStride + r] = s;
             }
         }
     }
 }
 
+// every column of the tile is frozen: nothing to compute, but the partials
+// must still be defined for the controller
+template <class E>
+__device__ __forceinline__ void simt_tile_zero_parts(int N, int n0, int row_block, double* part) {
+    if constexpr (E::NRED > 0) {
+        const int t = threadIdx.x;
+        if (t < kBN && n0 + t < N)
+            for (int r = 0; r < E::NRED; ++r) part[((int64_t)row_block * N + n0 + t) * kPartStride + r] = 0.0;
+    }
+}
+
+template <class E, bool SPLIT, class TA>
+__global__ void __launch_bounds__(256)
+gemm_simt_kernel(int M, int N, int K, const TA* __restrict__ Aop, const TA* __restrict__ Aop2,
+                 int64_t lda, const float* __restrict__ X, int64_t ldx, E epi,
+                 double* __restrict__ part, const int32_t* __restrict__ active) {
+    constexpr int NR = E::NRED > 0 ? E::NRED : 1;
+    __shared__ __align__(16) SimtSmem<SPLIT> sm;
+    __shared__ double red_s[8][kBN][NR];
+    __shared__ int any_active;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    if (!tile_has_active(active, N, n0, &any_active)) {
+        simt_tile_zero_parts<E>(N, n0, blockIdx.y, part);
+        return;
+    }
+    float acc[4][4];
+    simt_tile_mainloop<SPLIT, TA>(M, N, m0, n0, 0, (K + 3) & ~3, Aop, Aop2, lda, X, ldx, sm, acc);
+    simt_tile_epilogue<E, NR>(M, N, m0, n0, blockIdx.y, acc, epi, part, red_s);
+}
+
+// Split-K, for panels too narrow to fill the GPU with output tiles: slice
+// blockIdx.z of K (chunk kchunk, a multiple of kBK) writes its tile sum to
+// Wk[(z * N + j) * ldw + i].
+template <bool SPLIT, class TA>
+__global__ void __launch_bounds__(256)
+gemm_simt_splitk_kernel(int M, int N, int K, int kchunk, const TA* __restrict__ Aop,
+                        const TA* __restrict__ Aop2, int64_t lda, const float* __restrict__ X, int64_t ldx,
+                        float* __restrict__ Wk, int64_t ldw, const int32_t* __restrict__ active) {
+    __shared__ __align__(16) SimtSmem<SPLIT> sm;
+    __shared__ int any_active;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    if (!tile_has_active(active, N, n0, &any_active)) return;
+    const int Kp = (K + 3) & ~3;
+    const int k_begin = blockIdx.z * kchunk, k_end = min(Kp, k_begin + kchunk);
+    float acc[4][4];
+    simt_tile_mainloop<SPLIT, TA>(M, N, m0, n0, k_begin, k_end, Aop, Aop2, lda, X, ldx, sm, acc);
+    const int t = threadIdx.x, tc = t & 15, tr = t >> 4;
+    float* w = Wk + (int64_t)blockIdx.z * N * ldw;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = n0 + tc * 4 + q;
+        if (j >= N) continue;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int i = m0 + tr * 4 + p;
+            if (i < M) w[(int64_t)j * ldw + i] = acc[p][q];
+        }
+    }
+}
+
+// Sums the S slices of every element in slice order with Kahan compensation,
+// then runs the epilogue exactly as the single-pass kernel does.
+template <class E>
+__global__ void __launch_bounds__(256)
+splitk_epilogue_kernel(int M, int N, int S, const float* __restrict__ Wk, int64_t ldw, E epi,
+                       double* __restrict__ part, const int32_t* __restrict__ active) {
+    constexpr int NR = E::NRED > 0 ? E::NRED : 1;
+    __shared__ double red_s[8][kBN][NR];
+    __shared__ int any_active;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    if (!tile_has_active(active, N, n0, &any_active)) {
+        simt_tile_zero_parts<E>(N, n0, blockIdx.y, part);
+        return;
+    }
+    const int t = threadIdx.x, tc = t & 15, tr = t >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = min(n0 + tc * 4 + q, N - 1);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const int i = min(m0 + tr * 4 + p, M - 1);
+            float s = 0.0f, c = 0.0f;
+            for (int z = 0; z < S; ++z) {
+                const float y = Wk[((int64_t)z * N + j) * ldw + i] - c;
+                const float u = s + y;
+                c = (u - s) - y;
+                s = u;
+            }
+            acc[p][q] = s - c;
+        }
+    }
+    simt_tile_epilogue<E, NR>(M, N, m0, n0, blockIdx.y, acc, epi, part, red_s);
+}
+
+// K slices for an M x N sweep: enough CTAs to give every SM two tiles, each
+// slice at least 64 deep.
+inline int splitk_slices(const Handle* h, int M, int N, int K) {
+    const int tiles = ((N + kBN - 1) / kBN) * ((M + kBM - 1) / kBM);
+    const int sms = h->sms > 0 ? h->sms : 152;
+    if (tiles >= sms || K < 128) return 1;
+    int S = (2 * sms + tiles - 1) / tiles;
+    S = std::min(S, kMaxSplitK);
+    S = std::min(S, std::max(1, K / 64));
+    return S;
+}
+
 // Host-side launcher.  Returns the number of row blocks (the count of
 // partials per column the controller must sum), or a negative error code.
 // Aop2 (nullable): low part of a split operand, see gemv_kernel.
-template <class E>
-int launch_sweep(Handle* h, int M, int N, int K, const float* Aop, int64_t lda, const float* X,
+template <class E, class TA>
+int launch_sweep(Handle* h, int M, int N, int K, const TA* Aop, int64_t lda, const float* X,
                  int64_t ldx, const E& epi, double* part, const int32_t* active,
-                 const float* Aop2 = nullptr) {
+                 const TA* Aop2 = nullptr) {
     cudaStream_t s = h->stream;
     if (N <= 8) {
         const int rows_per_block = kGemvWarps * kGemvRowsPerWarp;
         const int grid = (M + rows_per_block - 1) / rows_per_block;
         switch (N) {
 #define L1_GEMV_CASE(nc) \
-    case nc: gemv_kernel<nc, E><<<grid, kGemvWarps * 32, 0, s>>>(M, N, K, Aop, Aop2, lda, X, ldx, epi, part); break;
+    case nc: gemv_kernel<nc, E, TA><<<grid, kGemvWarps * 32, 0, s>>>(M, N, K, Aop, Aop2, lda, X, ldx, epi, part); break;
             L1_GEMV_CASE(1) L1_GEMV_CASE(2) L1_GEMV_CASE(3) L1_GEMV_CASE(4)
             L1_GEMV_CASE(5) L1_GEMV_CASE(6) L1_GEMV_CASE(7) L1_GEMV_CASE(8)
 #undef L1_GEMV_CASE
@@ -314,10 +479,42 @@ int launch_sweep(Handle* h, int M, int N, int K, const float* Aop, int64_t lda, 
         return grid;
     }
     dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
+    int S = splitk_slices(h, M, N, K);
+    const int64_t ldw = ((int64_t)M + 3) & ~int64_t(3);
+    if (S > 1) {
+        const size_t need = (size_t)S * N * ldw;
+        if (need > h->splitk_floats) {
+            // grows once to the largest narrow sweep this handle has seen
+            if (h->splitk) cudaStreamSynchronize(s);
+            float* p = nullptr;
+            if (dev_alloc_t(h, &p, need) != L1_OK) {
+                S = 1;  // no room for the slices: single pass
+            } else {
+                h->splitk = p;
+                h->splitk_floats = need;
+            }
+        }
+    }
+    if (S > 1) {
+        const int Kp = (K + 3) & ~3;
+        const int kchunk = ((Kp + S - 1) / S + kBK - 1) / kBK * kBK;
+        S = (Kp + kchunk - 1) / kchunk;
+        dim3 g3(grid.x, grid.y, S);
+        if (Aop2)
+            gemm_simt_splitk_kernel<true, TA><<<g3, 256, 0, s>>>(M, N, K, kchunk, Aop, Aop2, lda, X, ldx, h->splitk,
+                                                                 ldw, active);
+        else
+            gemm_simt_splitk_kernel<false, TA><<<g3, 256, 0, s>>>(M, N, K, kchunk, Aop, nullptr, lda, X, ldx,
+                                                                  h->splitk, ldw, active);
+        L1_LAUNCH_CHECK(h);
+        splitk_epilogue_kernel<E><<<grid, 256, 0, s>>>(M, N, S, h->splitk, ldw, epi, part, active);
+        L1_LAUNCH_CHECK(h);
+        return (int)grid.y;
+    }
     if (Aop2)
-        gemm_simt_kernel<E, true><<<grid, 256, 0, s>>>(M, N, K, Aop, Aop2, lda, X, ldx, epi, part, active);
+        gemm_simt_kernel<E, true, TA><<<grid, 256, 0, s>>>(M, N, K, Aop, Aop2, lda, X, ldx, epi, part, active);
     else
-        gemm_simt_kernel<E, false><<<grid, 256, 0, s>>>(M, N, K, Aop, nullptr, lda, X, ldx, epi, part, active);
+        gemm_simt_kernel<E, false, TA><<<grid, 256, 0, s>>>(M, N, K, Aop, nullptr, lda, X, ldx, epi, part, active);
     L1_LAUNCH_CHECK(h);
     return (int)grid.y;
 }
