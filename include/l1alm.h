@@ -68,7 +68,9 @@ typedef enum { L1_PALM = 0, L1_DALM = 1 } l1_solver;
 typedef enum {
     L1_A_FP32 = 0, /* A held in FP32 */
     L1_A_BF16 = 1, /* A held in BF16 (round to nearest even), FP32 accumulate */
-    L1_A_FP8E4M3 = 2 /* A held in FP8 e4m3 with a per-column FP32 scale */
+    L1_A_FP8E4M3 = 2 /* A held in FP8 e4m3 (nearest, saturating) with one FP32 scale
+                      * per row of each stored layout (per row of A for A u, per
+                      * column of A for A^T y), FP32 accumulate */
 } l1_precision;
 
 typedef enum {
@@ -105,7 +107,11 @@ typedef struct {
                           * accumulation rounds with a bias that the iteration
                           * accumulates, so by default it stays on the compensated
                           * CUDA-core sweep. */
-    int32_t reserved;
+    int32_t refine;      /* precision BF16 / FP8: 0 -> after every column has met the
+                          * stopping rule on the low-precision A, resume each one from
+                          * its iterate on the FP32 A until the rule is met again
+                          * (results and iters cover both phases); -1 -> return the
+                          * low-precision answer */
 } l1_options;
 
 /* Per-instance results (host memory). */

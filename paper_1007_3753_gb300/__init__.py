@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("check_every", C.c_int32), ("class_count", C.c_int32),
                 ("class_offsets", C.POINTER(C.c_int32)), ("stream", C.c_void_p),
                 ("unroll_K", C.c_int32), ("unroll_J", C.c_int32), ("ckpt_every", C.c_int32),
-                ("profile", C.c_int32), ("tc_sweeps", C.c_int32), ("reserved", C.c_int32)]
+                ("profile", C.c_int32), ("tc_sweeps", C.c_int32), ("refine", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -158,7 +158,7 @@ class Solver:
                  inner_max: int = 0, inner_tol: float = 0.0, check_every: int = 0,
                  class_offsets=None, precision: int = A_FP32, engine: int = ENGINE_AUTO,
                  profile: bool = False, tc_sweeps: int = 0, unroll_K: int = 0, unroll_J: int = 0,
-                 ckpt_every: int = 0, stream=None):
+                 ckpt_every: int = 0, refine: bool = True, stream=None):
         L = load()
         o = Options()
         L.l1_options_init(C.byref(o))
@@ -174,6 +174,7 @@ class Solver:
         o.profile = 1 if profile else 0
         o.tc_sweeps = tc_sweeps
         o.unroll_K = unroll_K
+        o.refine = 0 if refine else -1
         if unroll_J:
             o.unroll_J = unroll_J
         if ckpt_every:

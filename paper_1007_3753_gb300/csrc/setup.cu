@@ -54,6 +54,60 @@ int make_layouts(Handle* h, const float* A_dev, int64_t lda) {
     return L1_OK;
 }
 
+// ------------------------------------------------ low-precision copies of A
+// One block per row of a layout (rows x cols, leading dimension ld, the
+// padding zero).  BF16: round to nearest even.  FP8 e4m3: scale = max |row|
+// / 448 (the largest finite e4m3), q = e4m3(a / scale) rounded to nearest
+// with saturation; an all-zero row keeps scale 1.
+__global__ void quantize_rows_kernel(const float* __restrict__ src, int rows, int64_t ld, int prec,
+                                     void* dst, float* scale) {
+    __shared__ float sh[32];
+    const int r = blockIdx.x;
+    if (r >= rows) return;
+    const float* row = src + (int64_t)r * ld;
+    float sc = 1.0f;
+    if (prec == L1_A_FP8E4M3) {
+        float mx = 0.0f;
+        for (int64_t k = threadIdx.x; k < ld; k += blockDim.x) mx = fmaxf(mx, fabsf(row[k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m2 = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmaxf(m2, sh[w]);
+            sh[0] = m2 > 0.0f ? m2 / 448.0f : 1.0f;
+        }
+        __syncthreads();
+        sc = sh[0];
+        if (threadIdx.x == 0) scale[r] = sc;
+        uint8_t* d = static_cast<uint8_t*>(dst) + (int64_t)r * ld;
+        for (int64_t k = threadIdx.x; k < ld; k += blockDim.x)
+            d[k] = (uint8_t)__nv_cvt_float_to_fp8(row[k] / sc, __NV_SATFINITE, __NV_E4M3);
+    } else {
+        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(dst) + (int64_t)r * ld;
+        for (int64_t k = threadIdx.x; k < ld; k += blockDim.x) d[k] = __float2bfloat16_rn(row[k]);
+    }
+}
+
+int make_lowp(Handle* h) {
+    const int prec = h->opt.precision;
+    const size_t es = prec == L1_A_FP8E4M3 ? 1 : 2;
+    L1_TRY(dev_alloc(h, &h->A_rm_lp, es * (size_t)h->ldn * h->m));
+    L1_TRY(dev_alloc(h, &h->A_cm_lp, es * (size_t)h->ldm * h->n));
+    if (prec == L1_A_FP8E4M3) {
+        L1_TRY(dev_alloc_t(h, &h->A_rm_scale, (size_t)h->m));
+        L1_TRY(dev_alloc_t(h, &h->A_cm_scale, (size_t)h->n));
+    }
+    quantize_rows_kernel<<<(unsigned)h->m, 256, 0, h->stream>>>(h->A_rm, (int)h->m, h->ldn, prec, h->A_rm_lp,
+                                                                 h->A_rm_scale);
+    L1_LAUNCH_CHECK(h);
+    quantize_rows_kernel<<<(unsigned)h->n, 256, 0, h->stream>>>(h->A_cm, (int)h->n, h->ldm, prec, h->A_cm_lp,
+                                                                 h->A_cm_scale);
+    L1_LAUNCH_CHECK(h);
+    return L1_OK;
+}
+
 // ----------------------------------------------------- Lipschitz constant
 // Power iteration on A^T A (reading of "L" in Algorithm 1 step 6 as the
 // Lipschitz constant ||A||_2^2 of the smooth term's gradient, §IV-A):

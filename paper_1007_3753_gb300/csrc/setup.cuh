@@ -8,6 +8,9 @@ namespace l1 {
 // A_cm / A_rm from a device column-major copy of A
 int make_layouts(Handle* h, const float* A_dev, int64_t lda);
 
+// BF16 / FP8 copies of both layouts of A (l1_options.precision)
+int make_lowp(Handle* h);
+
 // Rayleigh-quotient estimate of ||A||_2^2 by power iteration on A^T A
 int power_iteration(Handle* h, int max_iter, double rtol, double* L_out);
 

@@ -88,6 +88,26 @@ __global__ void fill_i32_kernel(int32_t* p, int n, int32_t v) {
     if (i < n) p[i] = v;
 }
 
+// Refinement restart: keep the first phase's iteration count apart, and leave
+// columns that went non-finite retired.
+__global__ void refine_restart_kernel(Cols c, const int32_t* home_status, const int32_t* home_iters,
+                                      int32_t* iters1, int N) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    iters1[j] = home_iters[j];
+    if (home_status[j] == L1_NONFINITE) {
+        c.active[j] = 0;
+        c.status[j] = L1_NONFINITE;
+    }
+}
+
+__global__ void add_iters_kernel(int32_t* iters, int32_t* inner, const int32_t* iters1, int N) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    iters[j] += iters1[j];
+    inner[j] += iters1[j];
+}
+
 __global__ void set_param_kernel(double* param, int n, double v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) param[i] = v;
@@ -140,6 +160,19 @@ struct SweepProf {
 
 }  // namespace
 
+// A u (rm) or A^T y (cm) sweep on the low-precision copy of A
+template <class E>
+static int sweep_lowp(Handle* h, bool rm, int M, int N, int K, const float* X, int64_t ldx, const E& e,
+                      double* part, const int32_t* active) {
+    const int64_t lda = rm ? h->ldn : h->ldm;
+    const void* A = rm ? h->A_rm_lp : h->A_cm_lp;
+    if (h->opt.precision == L1_A_BF16)
+        return launch_sweep(h, M, N, K, static_cast<const __nv_bfloat16*>(A), lda, X, ldx, e, part, active);
+    const float* sc = rm ? h->A_rm_scale : h->A_cm_scale;
+    return launch_sweep(h, M, N, K, static_cast<const fp8e4m3*>(A), lda, X, ldx, EpiRowScale<E>{sc, e}, part,
+                        active);
+}
+
 static int ensure_workspace(Handle* h, int N) {
     Workspace& w = h->ws;
     if (w.cap_N >= N) return L1_OK;
@@ -149,7 +182,7 @@ static int ensure_workspace(Handle* h, int N) {
         PanelSet& p = w.ps[q];
         old.insert(old.end(), {p.B, p.Wx, p.We, p.Ux, p.Ue, p.Y, p.X, p.Cc, p.colf, p.coli, p.cold});
     }
-    old.insert(old.end(), {w.R, w.hB, w.hWx, w.hWe, w.hY, w.hcoli, w.hcold, w.hcolf, w.part, w.newpos,
+    old.insert(old.end(), {w.R, w.hB, w.hWx, w.hWe, w.hY, w.hUx, w.hUe, w.hcoli, w.hcold, w.hcolf, w.part, w.newpos,
                            w.count, w.resid2, w.classl1, w.class_off, w.Up[0], w.Up[1], w.Rp[0], w.Rp[1],
                            w.Rp[2], w.Yp[0], w.Yp[1], w.Ylo});
     for (void* p : old) {
@@ -187,6 +220,10 @@ static int ensure_workspace(Handle* h, int N) {
     L1_TRY(dev_alloc_t(h, &w.hWx, ldn * N));
     L1_TRY(dev_alloc_t(h, &w.hWe, ldm * N));
     L1_TRY(dev_alloc_t(h, &w.hY, ldm * N));
+    if (h->opt.precision != L1_A_FP32) {
+        L1_TRY(dev_alloc_t(h, &w.hUx, ldn * N));
+        L1_TRY(dev_alloc_t(h, &w.hUe, ldm * N));
+    }
     L1_TRY(dev_alloc_t(h, &w.hcoli, (size_t)8 * N));
     L1_TRY(dev_alloc_t(h, &w.hcold, (size_t)10 * N));
     L1_TRY(dev_alloc_t(h, &w.hcolf, (size_t)2 * N));
@@ -287,8 +324,8 @@ static int compact(Handle* h, int q, int N_cur, int solver, double xi_max, int* 
     };
     const int m = (int)h->m, n = (int)h->n;
     const P panels[] = {{a.B, b.B, nullptr, h->ldm, m},  {a.Wx, b.Wx, w.hWx, h->ldn, n},
-                        {a.We, b.We, w.hWe, h->ldm, m},  {a.Ux, b.Ux, nullptr, h->ldn, n},
-                        {a.Ue, b.Ue, nullptr, h->ldm, m}, {a.Y, b.Y, w.hY, h->ldm, m},
+                        {a.We, b.We, w.hWe, h->ldm, m},  {a.Ux, b.Ux, w.hUx, h->ldn, n},
+                        {a.Ue, b.Ue, w.hUe, h->ldm, m}, {a.Y, b.Y, w.hY, h->ldm, m},
                         {a.X, b.X, nullptr, h->ldn, n},   {a.Cc, b.Cc, nullptr, h->ldm, m}};
     for (const P& p : panels) {
         dim3 grid((unsigned)std::min(8, (p.rows + 255) / 256), (unsigned)N_cur);
@@ -356,9 +393,15 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                                                                           : (int64_t)max_iter * inner_max;
     int64_t rounds = 0;
     bool pieces_valid = false;  // TF32 pieces of U_x match the current set
+    // low-precision A: phase 1 sweeps the BF16 / FP8 copy, phase 2 (refinement)
+    // resumes every column on the FP32 A
+    const bool lowp = o.precision != L1_A_FP32;
+    int phase = 1;
+    int32_t* iters1 = w.hcoli + 5 * w.cap_N;
     while (true) {
         P = &w.ps[q];
         c = make_cols(h, q, N_cur);
+        const bool lowp_now = lowp && phase == 1;
         const double na = N_cur;
         // tensor-core sweeps while the batch fills at least half a 64-column tile
         const bool tc_now = h->use_tc && solver == L1_DALM && N_cur >= 32;
@@ -388,6 +431,8 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                     const float* ap[2] = {h->A_rm_p[0], h->A_rm_p[1]};
                     const float* xp[2] = {w.Up[0], w.Up[1]};
                     rc = tc::launch(h, m, N_cur, n, ap, 2, xp, 2, tc::terms_split3(), ldn, ldn, e1, part_m, c.active);
+                } else if (lowp_now) {
+                    rc = sweep_lowp(h, true, m, N_cur, n, P->Ux, ldn, e1, part_m, c.active);
                 } else {
                     rc = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Ux, ldn, e1, part_m, c.active);
                 }
@@ -421,6 +466,8 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                     const float* ap[2] = {h->A_cm_p[0], h->A_cm_p[1]};
                     const float* xp[2] = {w.Yp[0], w.Yp[1]};
                     np_x = tc::launch(h, n, N_cur, m, ap, 2, xp, 2, tc::terms_split3(), ldm, ldm, e3, part_n, c.active);
+                } else if (lowp_now) {
+                    np_x = sweep_lowp(h, false, n, N_cur, m, P->Y, ldm, e3, part_n, c.active);
                 } else {
                     np_x = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, P->Y, ldm, e3, part_n, c.active);
                 }
@@ -435,6 +482,10 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                                               EpiPalmA{w.R, P->Cc, P->We, P->Y, P->B, c, pp, ldm}, part_m, c.active);
                 prof.stop();
                 if (np_A < 0) return np_A;
+                if (mode == L1_P1_2) {
+                    p12_fixup_kernel<<<N_cur, 128, 0, s>>>(c, part_m, np_A, P->We, P->Cc, w.R, ldm, m, o.epsilon);
+                    L1_LAUNCH_CHECK(h);
+                }
                 prof.start(2, 2.0 * m * n * na);
                 const int np_At = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, w.R, ldm,
                                                EpiPalmAt{P->Wx, P->Ux, P->X, c, pp, ldn}, part_n, c.active);
@@ -475,7 +526,34 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
             N_cur = cnt;
             pieces_valid = false;
         }
+        if (done && lowp && phase == 1 && o.refine >= 0) {
+            // refinement: reload every column's state (w, z - w/beta, y) from
+            // home and continue the same iteration on the FP32 operator
+            HomeRes hr1 = make_home_res(h);
+            phase = 2;
+            rounds = 0;
+            q = 0;
+            P = &w.ps[0];
+            L1_CUDA_TRY(cudaMemcpyAsync(P->B, w.hB, pm, cudaMemcpyDeviceToDevice, s));
+            L1_CUDA_TRY(cudaMemcpyAsync(P->Wx, w.hWx, pn, cudaMemcpyDeviceToDevice, s));
+            L1_CUDA_TRY(cudaMemcpyAsync(P->Ux, w.hUx, pn, cudaMemcpyDeviceToDevice, s));
+            L1_CUDA_TRY(cudaMemcpyAsync(P->We, w.hWe, pm, cudaMemcpyDeviceToDevice, s));
+            L1_CUDA_TRY(cudaMemcpyAsync(P->Ue, w.hUe, pm, cudaMemcpyDeviceToDevice, s));
+            L1_CUDA_TRY(cudaMemcpyAsync(P->Y, w.hY, pm, cudaMemcpyDeviceToDevice, s));
+            c = make_cols(h, 0, N);
+            init_cols_kernel<<<N, 128, 0, s>>>(c, P->B, ldm, m, mode, o.beta, o.xi0, xi_max, o.lambda);
+            L1_LAUNCH_CHECK(h);
+            refine_restart_kernel<<<(N + 255) / 256, 256, 0, s>>>(c, hr1.status, hr1.iters, iters1, N);
+            L1_LAUNCH_CHECK(h);
+            N_cur = N;
+            continue;
+        }
         if (done) break;
+    }
+    if (phase == 2) {
+        HomeRes hr2 = make_home_res(h);
+        add_iters_kernel<<<(N + 255) / 256, 256, 0, s>>>(hr2.iters, hr2.inner, iters1, N);
+        L1_LAUNCH_CHECK(h);
     }
 
     // ---- finalisation on the home panels: objective, dual point, gap, residual
@@ -493,7 +571,8 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     const int np_F2 = launch_sweep(h, n, N, m, h->A_cm, ldm, (mode == L1_QP_LAMBDA) ? w.R : w.hY, ldm,
                                    EpiFinalAt{w.hWx, hr.smax, ldn}, part_n, nullptr);
     if (np_F2 < 0) return np_F2;
-    final_metrics_kernel<<<N, 128, 0, s>>>(N, hr.smax, hr.fin, part_m, np_F1, part_n, np_F2, mode, o.lambda);
+    final_metrics_kernel<<<N, 128, 0, s>>>(N, hr.smax, hr.fin, part_m, np_F1, part_n, np_F2, mode,
+                                           mode == L1_P1_2 ? o.epsilon : o.lambda);
     L1_LAUNCH_CHECK(h);
 
     // ---- classification (CAB with classes)

@@ -202,7 +202,7 @@ struct PalmParams {
 // c = b - e + theta/xi' and the first inner residual r = c - A x.
 // red (outer phase only): ||e_{k+1} - e_k||^2, ||e_k||^2.
 struct EpiPalmA {
-    static constexpr int NRED = 2;
+    static constexpr int NRED = 3;
     float* R;
     float* Cc;
     float* E;
@@ -226,6 +226,22 @@ struct EpiPalmA {
         if (ph == PH_OUTER) th = fmaf(xi, b - acc - e_old, th);
         const float xin = xi_for_phase(ph, xi, p.growth, c.xicap[j]);
         const float thx = th / xin;
+        if (p.mode == L1_P1_2) {
+            // R10: e is the projection of v = b - A x + theta/xi onto the
+            // eps-ball; its scale needs ||v||, so v is stored here and
+            // p12_fixup_kernel scales it (and corrects c and r) before the
+            // next sweep.  red: ||v||^2, ||e_k||^2, v . e_k
+            const float v = b - acc + thx;
+            TH[o] = th;
+            E[o] = v;
+            const float cc = b + thx;
+            Cc[o] = cc;
+            R[o] = cc - acc;
+            red[0] += (double)v * v;
+            red[1] += (double)e_old * e_old;
+            red[2] += (double)v * e_old;
+            return;
+        }
         float e_new = 0.0f;
         if (p.mode == L1_CAB) e_new = soft_thr(b - acc + thx, 1.0f / xin);
         TH[o] = th;
@@ -335,7 +351,10 @@ __global__ void ctrl_palm_kernel(Cols c, PalmParams p, const double* part_A, int
     if (!c.active[j]) return;
     const int ph = c.phase[j];
     double de2 = 0.0, e2 = 0.0;
-    if (ph != PH_INNER && p.mode != L1_QP_LAMBDA) {
+    if (ph != PH_INNER && p.mode == L1_P1_2) {
+        de2 = c.de2[j];  // from p12_fixup_kernel
+        e2 = c.e2[j];
+    } else if (ph != PH_INNER && p.mode != L1_QP_LAMBDA) {
         de2 = sum_parts(part_A, np_A, c.N, j, 0, sh);
         e2 = sum_parts(part_A, np_A, c.N, j, 1, sh);
     }
@@ -400,6 +419,36 @@ __global__ void ctrl_palm_kernel(Cols c, PalmParams p, const double* part_A, int
             X[o + i] = w;
             V[o + i] = w;
         }
+    }
+}
+
+// P1,2 outer step (R10), between the two sweeps: e = min(1, eps/||v||) v,
+// c -= e, r -= e, and ||e_{k+1} - e_k||^2 = s^2||v||^2 - 2 s v.e_k + ||e_k||^2
+// for the outer rule.  One 128-thread block per column in its outer phase.
+__global__ void p12_fixup_kernel(Cols c, const double* part_A, int np_A, float* E, float* Cc, float* R,
+                                 int64_t ldm, int m, double eps) {
+    __shared__ double sh[4];
+    __shared__ float s_sh;
+    const int j = blockIdx.x;
+    if (!c.active[j] || c.phase[j] == PH_INNER) return;
+    const double vv = sum_parts(part_A, np_A, c.N, j, 0, sh);
+    const double ee = sum_parts(part_A, np_A, c.N, j, 1, sh);
+    const double ve = sum_parts(part_A, np_A, c.N, j, 2, sh);
+    if (threadIdx.x == 0) {
+        const double nv = sqrt(vv);
+        const double sc = nv > eps ? eps / nv : 1.0;
+        c.de2[j] = fmax(0.0, sc * sc * vv - 2.0 * sc * ve + ee);
+        c.e2[j] = ee;
+        s_sh = (float)sc;
+    }
+    __syncthreads();
+    const float sc = s_sh;
+    const int64_t o = (int64_t)j * ldm;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const float e = sc * E[o + i];
+        E[o + i] = e;
+        Cc[o + i] -= e;
+        R[o + i] -= e;
     }
 }
 
@@ -518,7 +567,7 @@ __global__ void count_active_kernel(const int32_t* active, int N, int32_t* count
 // matches the returned x.  QP keeps r in R for the dual point.
 // red: ||r||^2, b^T y (P1/CAB) or b^T r (QP), ||e||_1, ||y||^2 (unused).
 struct EpiFinalA {
-    static constexpr int NRED = 3;
+    static constexpr int NRED = 4;
     float* R;
     float* Y;
     const float* E;  // nullable
@@ -532,7 +581,13 @@ struct EpiFinalA {
         const float b = B[o];
         const float e = E ? E[o] : 0.0f;
         const float r = b - acc - e;
-        red[0] += (double)r * r;
+        if (mode == L1_P1_2) {
+            // the constraint of Eq. 2 is on b - A x
+            const double rb = (double)b - (double)acc;
+            red[0] += rb * rb;
+        } else {
+            red[0] += (double)r * r;
+        }
         red[2] += fabs((double)e);
         if (mode == L1_QP_LAMBDA) {
             R[o] = r;
@@ -545,6 +600,7 @@ struct EpiFinalA {
             Y[o] = y;
         }
         red[1] += (double)b * y;
+        red[3] += (double)y * y;
         if (mode == L1_CAB) atomicMax(reinterpret_cast<int*>(smax + j), __float_as_int(fabsf(y)));
     }
 };
@@ -569,6 +625,7 @@ __global__ void final_metrics_kernel(int N, const float* smax_arr, double* fin, 
     const double r2 = sum_parts(part_A, np_A, N, j, 0, sh);
     const double by = sum_parts(part_A, np_A, N, j, 1, sh);
     const double e1 = sum_parts(part_A, np_A, N, j, 2, sh);
+    const double y2 = sum_parts(part_A, np_A, N, j, 3, sh);
     const double x1 = sum_parts(part_At, np_At, N, j, 0, sh);
     if (threadIdx.x != 0) return;
     const double smax = (double)smax_arr[j];
@@ -579,6 +636,11 @@ __global__ void final_metrics_kernel(int N, const float* smax_arr, double* fin, 
         primal = 0.5 * r2 + lambda * x1;
         const double s = smax > 0.0 ? fmin(1.0, lambda / smax) : 1.0;
         dual = s * by - 0.5 * s * s * r2;
+    } else if (mode == L1_P1_2) {
+        // dual of Eq. 2: max b^T y - eps ||y|| s.t. ||A^T y||_inf <= 1, made
+        // feasible by scaling (lambda carries eps here)
+        primal = x1;
+        dual = (by - lambda * sqrt(y2)) / fmax(1.0, smax);
     } else {
         // dual of Eq. 1 / Eq. 5: max b^T y s.t. ||B^T y||_inf <= 1 (§V-B),
         // made feasible by scaling
