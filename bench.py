@@ -43,6 +43,10 @@ METRIC = "solves/sec at rel. err <=1e-4 vs FP64 oracle"
 L2_FLUSH_BYTES = 512 << 20
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates of the part
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-batch launch
+# (all 1024 columns active, cold cache) of each CUDA-core sweep, and the
+# algorithmic bytes of that launch (profiles/dalm_sweeps_cab_m1024_n1200_N1024_ncu_full.md)
+SIMT_TRAFFIC = {"A_u": (18.42e6, 18.2e6), "Finv_r": (21.16e6, 21.0e6), "At_y": (19.24e6, 19.1e6)}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -296,9 +300,12 @@ def bench_ours(args, rank, world):
         # the y-step multiplies by the FP32 pair F_hi + F_lo: two products per
         # algorithmic one
         terms = [1, 2, 1, 1][k]
+        tr = SIMT_TRAFFIC.get(names[k])
         roofline = {"bound": "alu", "kernel": f"sweep {names[k]} (gemm_simt_kernel / split-K pair)",
                     "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": tr[0] if tr else None,
+                    "traffic_note": ("bytes of one full-batch launch (N = 1024, cold cache) from ncu; "
+                                     f"algorithmic bytes of that launch {tr[1]:.3g}") if tr else None,
                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, no measured FP32 peak)",
                     "executed_tflops": achieved * terms, "executed_frac": achieved * terms / FP32_SIMT_PEAK_TFLOPS,
                     "launches": d_ln[k], "avg_launch_us": 1e3 * d_ms[k] / max(1, d_ln[k]),
