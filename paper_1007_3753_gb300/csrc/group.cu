@@ -4,15 +4,19 @@
 //
 // Work.  The dictionaries are stored column-major (FP32 or BF16) in one
 // allocation.  A work unit is (instance, tile of consecutive columns) sized so
-// the tile fits in shared memory (<= 64 KB).  One FISTA step over a unit
-//   1. stages r = b - A z (the instance's residual, from the accumulator of
-//      the previous step) in shared memory,
-//   2. reads its A tile from HBM once into shared memory while forming
-//      g_J = A_J^T r (one warp per column),
-//   3. updates x_J = soft(z_J + g_J/L, lambda/L), z_J = x_J + mu (x_J - x_J_old)
-//      and the per-instance sums ||dx||^2, ||x_old||^2,
-//   4. adds A_J z_J to the next step's accumulator from the tile in shared
-//      memory (red.global.add),
+// the tile (padding rows included) fits a 64 KB shared-memory buffer; a tile
+// is one contiguous, 16-byte aligned region of the arena.  Each CTA owns a
+// contiguous range of the active units of a step and
+//   1. streams its tiles from HBM into two shared buffers with 1-D TMA bulk
+//      copies (cp.async.bulk + mbarrier), the next tile in flight while the
+//      current one is processed,
+//   2. on entering an instance stages its residual r = b - A z (from the
+//      previous step's accumulator) in shared memory,
+//   3. forms g_J = A_J^T r (one warp per column, 16-byte shared loads) and
+//      updates x_J = soft(z_J + g_J/L, lambda/L), z_J = x_J + mu (x_J - x_J_old),
+//   4. adds A_J z_J to a shared-memory copy of the instance's next
+//      accumulator, which goes to global memory (one atomic per row) only
+//      when the CTA leaves the instance,
 // so every element of every active dictionary is read from HBM once per step.
 // After the pass a bounded grid barrier, a per-instance finalisation (stopping
 // rule of §VI-C, FISTA momentum), another barrier, and a rebuild of the
@@ -31,7 +35,7 @@ namespace l1 {
 
 enum GroupMode : int { GM_FISTA = 0, GM_POWER_INIT = 1, GM_POWER = 2, GM_FINAL = 3 };
 
-constexpr int kGThreads = 256;
+constexpr int kGThreads = 512;
 constexpr int kGWarps = kGThreads / 32;
 constexpr int kGMaxM = 8192;               // rows of r staged in shared memory
 constexpr int kGTileBytes = 64 * 1024;     // A tile in shared memory
@@ -117,113 +121,252 @@ __device__ bool grid_sync(const GArgs& g, volatile int* abort) {
     return ok != 0;
 }
 
-__device__ __forceinline__ float load_a(const GArgs& g, int64_t idx) {
-    if (g.bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(g.A)[idx]);
-    return reinterpret_cast<const float*>(g.A)[idx];
+// ----------------------------------------------------------- TMA staging
+__device__ __forceinline__ uint32_t g_smem(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// one work unit: columns col0 .. col0+nc-1 of instance i
-__device__ void group_unit(const GArgs& g, int i, int col0, int nc, int cur, float* r_s, uint8_t* tile_raw,
-                           float* zj_s, double* red_s) {
-    const int m = g.m[i], ld = g.ld[i];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float* racc_cur = cur ? g.racc1 : g.racc0;
-    float* racc_next = cur ? g.racc0 : g.racc1;
-    const int64_t bo = g.boff[i], xo = g.xoff[i] + col0;
-    const int64_t a0 = g.aoff[i] + (int64_t)col0 * ld;
-    const bool dots = g.mode == GM_FISTA || g.mode == GM_POWER;
-    float* tile_f = reinterpret_cast<float*>(tile_raw);
-    __nv_bfloat16* tile_h = reinterpret_cast<__nv_bfloat16*>(tile_raw);
+// 1-D bulk copy global -> shared completing on an mbarrier (both addresses
+// 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void g_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(g_smem(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(g_smem(dst)), "l"(src), "r"(bytes), "r"(g_smem(bar))
+                 : "memory");
+}
 
-    // 1. residual (FISTA: b - A z) or u = A v (power) into shared memory
+// bounded wait on an mbarrier phase: false when the limit ran out
+__device__ __forceinline__ bool g_mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kGBarrierSpin; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(g_smem(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (i > (1u << 16)) __nanosleep(64);
+    }
+    return false;
+}
+
+// Geometry of a work unit: slot k of the active list, instance i, its
+// columns col0 .. col0+nc-1, and the instance's n, columns per unit, leading
+// dimension and arena offset (so that the next unit needs no memory reads
+// unless it starts a new instance).
+struct UnitGeom {
+    int k, i, col0, nc, n, uc, ld;
+    int64_t aoff;
+};
+
+__device__ __forceinline__ UnitGeom geom_at(const GArgs& g, int k, int64_t local) {
+    UnitGeom r;
+    r.k = k;
+    r.i = g.act[k];
+    r.n = g.n[r.i];
+    r.uc = g.ucols[r.i];
+    r.ld = g.ld[r.i];
+    r.aoff = g.aoff[r.i];
+    r.col0 = (int)(local * r.uc);
+    r.nc = min(r.uc, r.n - r.col0);
+    return r;
+}
+
+// unit u: slot k with upref[k] <= u < upref[k+1] (binary search)
+__device__ __forceinline__ UnitGeom geom_first(const GArgs& g, int64_t u, int nact) {
+    int lo = 0, hi = nact;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (g.upref[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    return geom_at(g, lo, u - g.upref[lo]);
+}
+
+// the unit after p in the active list
+__device__ __forceinline__ UnitGeom geom_next(const GArgs& g, const UnitGeom& p) {
+    if (p.col0 + p.uc < p.n) {
+        UnitGeom r = p;
+        r.col0 = p.col0 + p.uc;
+        r.nc = min(p.uc, p.n - r.col0);
+        return r;
+    }
+    return geom_at(g, p.k + 1, 0);
+}
+
+__device__ __forceinline__ void issue_tile(const GArgs& g, const UnitGeom& q, uint8_t* dst, uint64_t* bar) {
+    const int es = g.bf16 ? 2 : 4;
+    const int64_t e0 = q.aoff + (int64_t)q.col0 * q.ld;
+    g_bulk_load(dst, static_cast<const uint8_t*>(g.A) + e0 * es, (uint32_t)((int64_t)q.nc * q.ld * es), bar);
+}
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+// Row r of an instance lives at plane r % E, position r / E of the shared
+// vectors r_s and acc_s (E = 8 elements per 16-byte group for BF16, 4 for
+// FP32, RG = ld / E groups): a lane that owns row group v touches word
+// k * RG + v of plane k, so a warp's accesses are consecutive words.
+__device__ __forceinline__ int soa_index(int r, int E, int RG) { return (r % E) * RG + r / E; }
+
+// Per-unit column state, loaded before the tile arrives: x_c, z_c for the
+// thread's column c = threadIdx.x < nc.
+struct ColState {
+    float x, z;
+};
+
+__device__ __forceinline__ ColState load_cols(const GArgs& g, const UnitGeom& q) {
+    ColState cs{0.0f, 0.0f};
+    if ((int)threadIdx.x < q.nc && g.mode != GM_POWER_INIT) {
+        const int64_t j = g.xoff[q.i] + q.col0 + threadIdx.x;
+        cs.x = g.x[j];
+        if (g.mode == GM_FISTA) cs.z = g.z[j];
+    }
+    return cs;
+}
+
+// Columns of one staged tile: g_J = A_J^T r (when the tile has fewer columns
+// than warps, G warps share a column and leave partial dots in dot_s), then
+// threads c < nc apply the per-mode update, write z_c to zj_s and accumulate
+// their columns' reduction terms in d2 / w2.  Ends with a block barrier.
+__device__ __forceinline__ void tile_columns(const GArgs& g, const UnitGeom& q, const uint8_t* tile,
+                                             const float* r_s, float* dot_s, float* zj_s, const ColState& cst,
+                                             float Li, float mu, double& d2, double& w2) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = q.i, ld = q.ld, nc = q.nc;
+    const bool dots = g.mode == GM_FISTA || g.mode == GM_POWER;
+    const int G = nc >= kGWarps ? 1 : kGWarps / nc;  // warps per column
     if (dots) {
-        for (int r = threadIdx.x; r < m; r += blockDim.x) {
-            const float acc = racc_cur[bo + r];
-            r_s[r] = g.mode == GM_FISTA ? g.b[bo + r] - acc : acc;
+        const int c_first = G == 1 ? warp : warp / G, c_step = G == 1 ? kGWarps : nc;
+        const int gi = G == 1 ? 0 : warp % G;
+        if (warp < nc * G) {
+            for (int c = c_first; c < nc; c += c_step) {
+                float dot = 0.0f;
+                if (g.bf16) {
+                    const int RG = ld / 8;
+                    const uint4* col = reinterpret_cast<const uint4*>(tile + (size_t)c * ld * 2);
+                    for (int v = gi * 32 + lane; v < RG; v += 32 * G) {
+                        const uint4 a = col[v];
+                        dot = fmaf(bf_lo(a.x), r_s[v], dot);
+                        dot = fmaf(bf_hi(a.x), r_s[RG + v], dot);
+                        dot = fmaf(bf_lo(a.y), r_s[2 * RG + v], dot);
+                        dot = fmaf(bf_hi(a.y), r_s[3 * RG + v], dot);
+                        dot = fmaf(bf_lo(a.z), r_s[4 * RG + v], dot);
+                        dot = fmaf(bf_hi(a.z), r_s[5 * RG + v], dot);
+                        dot = fmaf(bf_lo(a.w), r_s[6 * RG + v], dot);
+                        dot = fmaf(bf_hi(a.w), r_s[7 * RG + v], dot);
+                    }
+                } else {
+                    const int RG = ld / 4;
+                    const float4* col = reinterpret_cast<const float4*>(tile + (size_t)c * ld * 4);
+                    for (int v = gi * 32 + lane; v < RG; v += 32 * G) {
+                        const float4 a = col[v];
+                        dot = fmaf(a.x, r_s[v], dot);
+                        dot = fmaf(a.y, r_s[RG + v], dot);
+                        dot = fmaf(a.z, r_s[2 * RG + v], dot);
+                        dot = fmaf(a.w, r_s[3 * RG + v], dot);
+                    }
+                }
+                dot = warp_sum_f(dot);
+                if (lane == 0) dot_s[c * G + gi] = dot;
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // 2-3. stage the tile; per column the dot product and the update
-    double d2 = 0.0, w2 = 0.0;
-    for (int c = warp; c < nc; c += kGWarps) {
-        const int64_t colbase = a0 + (int64_t)c * ld;
+    const int c = threadIdx.x;
+    if (c < nc) {
         float dot = 0.0f;
-        if (g.bf16) {
-            for (int r = lane; r < m; r += 32) {
-                const __nv_bfloat16 v = reinterpret_cast<const __nv_bfloat16*>(g.A)[colbase + r];
-                tile_h[c * m + r] = v;
-                if (dots) dot = fmaf(__bfloat162float(v), r_s[r], dot);
-            }
-        } else {
-            for (int r = lane; r < m; r += 32) {
-                const float v = reinterpret_cast<const float*>(g.A)[colbase + r];
-                tile_f[c * m + r] = v;
-                if (dots) dot = fmaf(v, r_s[r], dot);
-            }
-        }
-        dot = warp_sum_f(dot);
-        if (lane == 0) {
-            const int64_t j = xo + c;
-            float zn;
-            if (g.mode == GM_FISTA) {
-                // Eq. 18: x = soft(z + A^T(b - A z)/L, lambda/L), z' = x + mu (x - x_old)
-                const float Li = 1.0f / g.L[i];
-                const float xo_ = g.x[j];
-                const float xn = soft_g(fmaf(dot, Li, g.z[j]), g.lambda * Li);
-                zn = fmaf(g.mu[i], xn - xo_, xn);
-                g.x[j] = xn;
-                g.z[j] = zn;
-                const float dx = xn - xo_;
-                d2 += (double)dx * dx;
-                w2 += (double)xo_ * xo_;
-            } else if (g.mode == GM_POWER) {
-                zn = dot * g.cscale[i];  // v' = A^T A v scaled to about unit norm
-                g.x[j] = zn;
-                d2 += (double)zn * zn;
-            } else if (g.mode == GM_POWER_INIT) {
-                zn = rsqrtf((float)g.n[i]);
-                g.x[j] = zn;
-                d2 += (double)zn * zn;
-            } else {  // GM_FINAL: A x
-                zn = g.x[j];
-                w2 += fabs((double)zn);
-            }
-            zj_s[c] = zn;
-        }
-    }
-    __syncthreads();
-    // 4. partial product A_J z_J into the next accumulator
-    for (int r = threadIdx.x; r < m; r += blockDim.x) {
-        float acc = 0.0f;
-        if (g.bf16) {
-            for (int c = 0; c < nc; ++c) acc = fmaf(__bfloat162float(tile_h[c * m + r]), zj_s[c], acc);
-        } else {
-            for (int c = 0; c < nc; ++c) acc = fmaf(tile_f[c * m + r], zj_s[c], acc);
-        }
-        atomicAdd(&racc_next[bo + r], acc);
-    }
-    // per-instance sums (lane 0 of each warp holds its columns' terms)
-    if (lane == 0) {
-        red_s[warp] = d2;
-        red_s[kGWarps + warp] = w2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int w = 0; w < kGWarps; ++w) {
-            s1 += red_s[w];
-            s2 += red_s[kGWarps + w];
-        }
+        if (dots)
+            for (int k = 0; k < G; ++k) dot += dot_s[c * G + k];
+        const int64_t j = g.xoff[i] + q.col0 + c;
+        float zn;
         if (g.mode == GM_FISTA) {
-            atomicAdd(&g.d2[i], s1);
-            atomicAdd(&g.w2[i], s2);
-        } else if (g.mode == GM_FINAL) {
-            atomicAdd(&g.w2[i], s2);
-        } else {
-            atomicAdd(&g.vv[i], s1);
+            // Eq. 18: x = soft(z + A^T(b - A z)/L, lambda/L), z' = x + mu (x - x_old)
+            const float xn = soft_g(fmaf(dot, Li, cst.z), g.lambda * Li);
+            zn = fmaf(mu, xn - cst.x, xn);
+            g.x[j] = xn;
+            g.z[j] = zn;
+            const float dx = xn - cst.x;
+            d2 += (double)dx * dx;
+            w2 += (double)cst.x * cst.x;
+        } else if (g.mode == GM_POWER) {
+            zn = dot * g.cscale[i];  // v' = A^T A v scaled to about unit norm
+            g.x[j] = zn;
+            d2 += (double)zn * zn;
+        } else if (g.mode == GM_POWER_INIT) {
+            zn = rsqrtf((float)q.n);
+            g.x[j] = zn;
+            d2 += (double)zn * zn;
+        } else {  // GM_FINAL: A x
+            zn = cst.x;
+            w2 += fabs((double)zn);
         }
+        zj_s[c] = zn;
     }
     __syncthreads();
+}
+
+// acc_s[r] += sum_c A(r, c) z_c over the staged tile.  Threads take groups of
+// 8 (BF16) or 4 (FP32) consecutive rows; when an instance has fewer row
+// groups than threads, several threads share a row group over disjoint column
+// slices and combine with shared-memory atomics.
+__device__ __forceinline__ void tile_accumulate(const GArgs& g, const UnitGeom& q, const uint8_t* tile,
+                                                const float* zj_s, float* acc_s) {
+    const int ld = q.ld;
+    if (g.bf16) {
+        const int RG = ld / 8;
+        const int span = RG >= kGThreads ? kGThreads : RG;
+        const int CS = RG >= kGThreads ? 1 : kGThreads / RG;
+        const int cs = threadIdx.x / span;
+        if (cs >= CS) return;
+        for (int rg = threadIdx.x % span; rg < RG; rg += span) {
+            float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int c = cs; c < q.nc; c += CS) {
+                const uint4 a = reinterpret_cast<const uint4*>(tile + (size_t)c * ld * 2)[rg];
+                const float z = zj_s[c];
+                s[0] = fmaf(bf_lo(a.x), z, s[0]);
+                s[1] = fmaf(bf_hi(a.x), z, s[1]);
+                s[2] = fmaf(bf_lo(a.y), z, s[2]);
+                s[3] = fmaf(bf_hi(a.y), z, s[3]);
+                s[4] = fmaf(bf_lo(a.z), z, s[4]);
+                s[5] = fmaf(bf_hi(a.z), z, s[5]);
+                s[6] = fmaf(bf_lo(a.w), z, s[6]);
+                s[7] = fmaf(bf_hi(a.w), z, s[7]);
+            }
+            if (CS == 1) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc_s[k * RG + rg] += s[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) atomicAdd(&acc_s[k * RG + rg], s[k]);
+            }
+        }
+    } else {
+        const int RG = ld / 4;
+        const int span = RG >= kGThreads ? kGThreads : RG;
+        const int CS = RG >= kGThreads ? 1 : kGThreads / RG;
+        const int cs = threadIdx.x / span;
+        if (cs >= CS) return;
+        for (int rg = threadIdx.x % span; rg < RG; rg += span) {
+            float s[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int c = cs; c < q.nc; c += CS) {
+                const float4 a = reinterpret_cast<const float4*>(tile + (size_t)c * ld * 4)[rg];
+                const float z = zj_s[c];
+                s[0] = fmaf(a.x, z, s[0]);
+                s[1] = fmaf(a.y, z, s[1]);
+                s[2] = fmaf(a.z, z, s[2]);
+                s[3] = fmaf(a.w, z, s[3]);
+            }
+            if (CS == 1) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc_s[k * RG + rg] += s[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(&acc_s[k * RG + rg], s[k]);
+            }
+        }
+    }
 }
 
 // rebuild the active-instance list and unit prefix (block 0 only)
@@ -269,39 +412,160 @@ __device__ void group_rebuild(const GArgs& g, int64_t* scan_s) {
     }
 }
 
+// Enter instance i: stage its residual (FISTA: b - A z; power: A v) and
+// clear the shared accumulator of its next A z (padding rows zero).
+__device__ __forceinline__ void stage_instance(const GArgs& g, int i, const float* racc_cur, float* r_s,
+                                               float* acc_s) {
+    const int m = g.m[i], ld = g.ld[i];
+    const int64_t bo = g.boff[i];
+    const bool dots = g.mode == GM_FISTA || g.mode == GM_POWER;
+    const int E = g.bf16 ? 8 : 4, RG = ld / E;
+    for (int r = threadIdx.x; r < ld; r += blockDim.x) {
+        float v = 0.0f;
+        if (dots && r < m) {
+            const float acc = racc_cur[bo + r];
+            v = g.mode == GM_FISTA ? g.b[bo + r] - acc : acc;
+        }
+        const int o = soa_index(r, E, RG);
+        r_s[o] = v;
+        acc_s[o] = 0.0f;
+    }
+    __syncthreads();
+}
+
+// Leave instance i: add the CTA's share of A z to the global accumulator and
+// its reduction terms to the instance's sums.
+__device__ __forceinline__ void flush_instance(const GArgs& g, int i, float* racc_next, const float* acc_s,
+                                               double* red_s, double& d2, double& w2) {
+    const int m = g.m[i], E = g.bf16 ? 8 : 4, RG = g.ld[i] / E;
+    const int64_t bo = g.boff[i];
+    for (int r = threadIdx.x; r < m; r += blockDim.x) atomicAdd(&racc_next[bo + r], acc_s[soa_index(r, E, RG)]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double wd2 = warp_sum(d2), ww2 = warp_sum(w2);
+    if (lane == 0) {
+        red_s[warp] = wd2;
+        red_s[kGWarps + warp] = ww2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int w = 0; w < kGWarps; ++w) {
+            s1 += red_s[w];
+            s2 += red_s[kGWarps + w];
+        }
+        if (g.mode == GM_FISTA) {
+            atomicAdd(&g.d2[i], s1);
+            atomicAdd(&g.w2[i], s2);
+        } else if (g.mode == GM_FINAL) {
+            atomicAdd(&g.w2[i], s2);
+        } else {
+            atomicAdd(&g.vv[i], s1);
+        }
+    }
+    d2 = 0.0;
+    w2 = 0.0;
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kGThreads) group_kernel(GArgs g) {
-    extern __shared__ __align__(16) uint8_t gsm[];
-    float* r_s = reinterpret_cast<float*>(gsm);                                   // kGMaxM floats
-    uint8_t* tile = gsm + kGMaxM * sizeof(float);                                  // kGTileBytes
-    float* zj_s = reinterpret_cast<float*>(tile + kGTileBytes);                    // 256 floats
-    double* red_s = reinterpret_cast<double*>(zj_s + 256);                         // 2 * kGWarps
-    int64_t* scan_s = reinterpret_cast<int64_t*>(red_s + 2 * kGWarps);             // kGThreads
+    extern __shared__ __align__(128) uint8_t gsm[];
+    float* r_s = reinterpret_cast<float*>(gsm);                               // kGMaxM floats
+    float* acc_s = r_s + kGMaxM;                                              // kGMaxM floats
+    uint8_t* tiles[2] = {gsm + 2 * kGMaxM * sizeof(float),                    // 2 x kGTileBytes
+                         gsm + 2 * kGMaxM * sizeof(float) + kGTileBytes};
+    float* zj_s = reinterpret_cast<float*>(tiles[1] + kGTileBytes);           // 256 floats
+    float* dot_s = zj_s + 256;                                                // 256 floats
+    double* red_s = reinterpret_cast<double*>(dot_s + 256);                   // 2 * kGWarps
+    int64_t* scan_s = reinterpret_cast<int64_t*>(red_s + 2 * kGWarps);        // kGThreads
+    uint64_t* bars = reinterpret_cast<uint64_t*>(scan_s + kGThreads);         // 2
+    __shared__ UnitGeom geo_s[2];
     __shared__ int abort_s;
-    if (threadIdx.x == 0) abort_s = 0;
+    if (threadIdx.x == 0) {
+        abort_s = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(g_smem(&bars[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(g_smem(&bars[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
     volatile int* abort = &abort_s;
     const int nwarps_grid = gridDim.x * kGWarps;
     const int gwarp = blockIdx.x * kGWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    uint32_t phase[2] = {0u, 0u};
 
     for (int step = 0; step < g.max_steps; ++step) {
         const int cur = step & 1;
         const int nact = *(volatile int32_t*)g.nact;
         if (nact == 0) break;
         const int64_t total = g.upref[nact];
-        // ---- pass over the active units
-        for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
-            int lo = 0, hi = nact;  // last k with upref[k] <= u
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (g.upref[mid] <= u) lo = mid;
-                else hi = mid;
+        // ---- pass over this CTA's contiguous range of active units
+        {
+            const float* racc_cur = cur ? g.racc1 : g.racc0;
+            float* racc_next = cur ? g.racc0 : g.racc1;
+            const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+            const int64_t u0 = min(total, (int64_t)blockIdx.x * per), u1 = min(total, u0 + per);
+            // thread 0 keeps two units in flight: the geometry of the units in
+            // buffers 0 and 1 lives in geo_s; the copy of unit u + 2 is issued
+            // as soon as unit u's buffer is free
+            bool pending[2] = {false, false};
+            if (threadIdx.x == 0 && u0 < u1) {
+                geo_s[0] = geom_first(g, u0, nact);
+                issue_tile(g, geo_s[0], tiles[0], &bars[0]);
+                if (u0 + 1 < u1) {
+                    geo_s[1] = geom_next(g, geo_s[0]);
+                    issue_tile(g, geo_s[1], tiles[1], &bars[1]);
+                }
             }
-            const int i = g.act[lo];
-            const int64_t local = u - g.upref[lo];
-            const int col0 = (int)(local * g.ucols[i]);
-            const int nc = min(g.ucols[i], g.n[i] - col0);
-            group_unit(g, i, col0, nc, cur, r_s, tile, zj_s, red_s);
+            if (u0 < u1) pending[0] = true;
+            if (u0 + 1 < u1) pending[1] = true;
+            __syncthreads();
+            int cur_i = -1;
+            float Li = 0.0f, mu = 0.0f;
+            double d2 = 0.0, w2 = 0.0;
+            bool failed = false;
+            for (int64_t u = u0; u < u1; ++u) {
+                const int b = (int)((u - u0) & 1);
+                const UnitGeom q = geo_s[b];
+                const ColState cst = load_cols(g, q);  // in flight while the tile lands
+                if (q.i != cur_i) {
+                    if (cur_i >= 0) flush_instance(g, cur_i, racc_next, acc_s, red_s, d2, w2);
+                    stage_instance(g, q.i, racc_cur, r_s, acc_s);
+                    cur_i = q.i;
+                    if (g.mode == GM_FISTA) {
+                        Li = 1.0f / g.L[cur_i];
+                        mu = g.mu[cur_i];
+                    }
+                }
+                // every thread polls; the block agrees on the outcome
+                const bool ok = g_mbar_wait(&bars[b], phase[b]);
+                if (__syncthreads_or(!ok)) {
+                    failed = true;
+                    break;
+                }
+                phase[b] ^= 1u;
+                pending[b] = false;
+                tile_columns(g, q, tiles[b], r_s, dot_s, zj_s, cst, Li, mu, d2, w2);
+                tile_accumulate(g, q, tiles[b], zj_s, acc_s);
+                __syncthreads();
+                if (u + 2 < u1) {
+                    if (threadIdx.x == 0) {
+                        const UnitGeom q2 = geom_next(g, geo_s[b ^ 1]);
+                        geo_s[b] = q2;
+                        issue_tile(g, q2, tiles[b], &bars[b]);
+                    }
+                    pending[b] = true;
+                }
+            }
+            if (failed) {
+                // a copy did not complete in time: record it, give the copies
+                // in flight a last bounded wait, and leave
+                if (threadIdx.x == 0) atomicCAS(g.err, 0, 2);
+                for (int k = 0; k < 2; ++k)
+                    if (pending[k]) g_mbar_wait(&bars[k], phase[k]);
+                *abort = 1;
+                return;
+            }
+            if (cur_i >= 0) flush_instance(g, cur_i, racc_next, acc_s, red_s, d2, w2);
         }
         if (!grid_sync(g, abort)) return;
         // ---- per-instance finalisation: one warp per active instance
@@ -379,10 +643,11 @@ __global__ void quantize_store_kernel(const float* src, int m, int n, int ld, vo
     else reinterpret_cast<float*>(dst)[off + idx] = v;
 }
 
-__global__ void group_init_kernel(GArgs g, int mode) {
+// Instances [first, last) take part in the pass; the others stay idle.
+__global__ void group_init_kernel(GArgs g, int mode, int64_t first, int64_t last) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.count) return;
-    g.active[i] = 1;
+    g.active[i] = (i >= first && i < last) ? 1 : 0;
     g.d2[i] = 0.0;
     g.w2[i] = 0.0;
     if (mode == GM_FINAL) return;  // keeps the solve's status, counts and last change
@@ -417,14 +682,15 @@ __global__ void rebuild_kernel(GArgs g) {
     group_rebuild(g, scan_s);
 }
 
-static int run_group(Handle* h, int mode, int max_steps, double tol) {
+static int run_group(Handle* h, int mode, int max_steps, double tol, int64_t first = 0, int64_t last = -1) {
     GroupState* G = h->grp;
     cudaStream_t s = h->stream;
     GArgs a = make_args(G);
     a.mode = mode;
     a.max_steps = max_steps;
     a.tol = tol;
-    group_init_kernel<<<(unsigned)((G->count + 255) / 256), 256, 0, s>>>(a, mode);
+    if (last < 0) last = G->count;
+    group_init_kernel<<<(unsigned)((G->count + 255) / 256), 256, 0, s>>>(a, mode, first, last);
     L1_LAUNCH_CHECK(h);
     L1_CUDA_TRY(cudaMemsetAsync(G->racc[0], 0, sizeof(float) * G->sum_m, s));
     L1_CUDA_TRY(cudaMemsetAsync(G->racc[1], 0, sizeof(float) * G->sum_m, s));
@@ -440,7 +706,8 @@ static int run_group(Handle* h, int mode, int max_steps, double tol) {
     L1_CUDA_TRY(cudaMemcpyAsync(&herr, G->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     L1_CUDA_TRY(cudaStreamSynchronize(s));
     if (herr) {
-        set_last_error("group kernel: bounded grid barrier expired");
+        set_last_error(herr == 2 ? "group kernel: bounded wait for a tile copy expired"
+                                 : "group kernel: bounded grid barrier expired");
         return L1_ERR_TIMEOUT;
     }
     return L1_OK;
@@ -455,7 +722,7 @@ __global__ void set_L_kernel(GArgs g, double safety, int64_t first, int64_t last
 static int group_power(Handle* h, int64_t first, int64_t last) {
     // batched power iteration (reading of L in Algorithm 1 step 6 / Eq. 18 as
     // ||A||_2^2): the POWER_INIT pass seeds v = 1/sqrt(n) and u = A v
-    L1_TRY(run_group(h, GM_POWER_INIT, 1000, 1e-6));
+    L1_TRY(run_group(h, GM_POWER_INIT, 1000, 1e-6, first, last));
     GroupState* G = h->grp;
     GArgs a = make_args(G);
     const int64_t k = last - first;
@@ -497,7 +764,7 @@ int group_load(Handle* h, int64_t first, int64_t k, const float* const* A) {
         L1_CUDA_TRY(cudaMemcpy(G->L, Ls.data(), sizeof(float) * G->count, cudaMemcpyHostToDevice));
         return L1_OK;
     }
-    return group_power(h, 0, G->count);
+    return group_power(h, first, first + k);
 }
 
 int group_setup(Handle* h, const float* const* A, const int64_t* m, const int64_t* n, int64_t count) {
@@ -515,7 +782,7 @@ int group_setup(Handle* h, const float* const* A, const int64_t* m, const int64_
         if (m[i] <= 0 || n[i] <= 0 || m[i] > kGMaxM || n[i] > (1 << 24)) return L1_ERR_INVALID_ARG;
         const int mi = (int)m[i], ni = (int)n[i];
         const int ld = (int)round_up(mi, 8);
-        int uc = kGTileBytes / (esize * mi);
+        int uc = kGTileBytes / (esize * ld);
         uc = std::max(1, std::min(uc, 256));
         G->hm[i] = mi; G->hn[i] = ni; G->hld[i] = ld; G->hucols[i] = uc;
         G->haoff[i] = ao; G->hboff[i] = bo; G->hxoff[i] = xo;
@@ -555,8 +822,8 @@ int group_setup(Handle* h, const float* const* A, const int64_t* m, const int64_
     L1_CUDA_TRY(cudaMemcpy(G->xoff, G->hxoff.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice));
     L1_CUDA_TRY(cudaMemcpy(G->nunits, G->hnunits.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice));
     // cooperative grid: every block resident
-    G->smem = kGMaxM * (int)sizeof(float) + kGTileBytes + 256 * (int)sizeof(float) + 2 * kGWarps * 8 +
-              kGThreads * 8;
+    G->smem = 2 * kGMaxM * (int)sizeof(float) + 2 * kGTileBytes + 2 * 256 * (int)sizeof(float) +
+              2 * kGWarps * 8 + kGThreads * 8 + 2 * 8;
     L1_CUDA_TRY(cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G->smem));
     int per_sm = 0, sms = 0;
     L1_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, group_kernel, kGThreads, G->smem));

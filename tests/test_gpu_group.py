@@ -107,3 +107,23 @@ def test_group_kkt_at_workload_sizes(l1):
         assert np.max(np.abs(c)) <= lam * 1.02, (k, np.max(np.abs(c)) / lam)
         assert np.max(np.abs(c[supp] - lam * np.sign(xg[supp])), initial=0.0) <= 0.02 * lam, k
     g.close()
+
+
+def test_group_chunked_load_matches_one_shot(l1):
+    """l1_group_load of instances in two calls (each estimating L for its own
+    range) gives the solve of a handle set up with every dictionary at once."""
+    ms, ns, inst = _instances(12, 900, 24, 96)
+    As = [p["A"] for p in inst]
+    b = np.concatenate([p["b"] for p in inst]).astype(np.float32)
+    g1 = l1.Group(As, ms, ns, 5e-3)
+    g2 = l1.Group(None, ms, ns, 5e-3)
+    g2.load(0, As[:5])
+    g2.load(5, As[5:])
+    x1, r1 = g1.solve(b, 0.0, 300)
+    x2, r2 = g2.solve(b, 0.0, 300)
+    for i in range(len(ms)):
+        a, c = x1[g1.xoff[i]:g1.xoff[i + 1]], x2[g2.xoff[i]:g2.xoff[i + 1]]
+        assert np.linalg.norm(a - c) <= 1e-5 * np.linalg.norm(a), i
+    assert np.allclose(r1["param"], r2["param"], rtol=1e-5)
+    g1.close()
+    g2.close()
