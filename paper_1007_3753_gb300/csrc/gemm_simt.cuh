@@ -148,14 +148,20 @@ gemv_kernel(int M, int N, int K, const TA* __restrict__ Aop, const TA* __restric
 // --------------------------------------------------------------- tiled GEMM
 // 64 x 64 output tile per 256-thread CTA, 4 x 4 per thread, K step 16,
 // double-buffered shared memory.
-constexpr int kBM = 64, kBN = 64, kBK = 16;
+constexpr int kBM = 64, kBN = 64, kBK = 32;  // kBK: the deepest K step (split-K chunks are multiples)
+constexpr int kKahan = 16;  // products per FP32 partial merged with compensation
+// K step of a sweep: 32 for one operand, 16 for a split operand (F_hi, F_lo),
+// whose second tile would not fit the static shared-memory budget
+template <bool SPLIT>
+__host__ __device__ constexpr int bk_of() { return SPLIT ? 16 : 32; }
 constexpr int kMaxSplitK = 8;
 
 template <bool SPLIT>
 struct SimtSmem {
-    float As[2][kBK][kBM];
-    float As2[SPLIT ? 2 : 1][SPLIT ? kBK : 1][SPLIT ? kBM : 4];
-    float Xs[2][kBK][kBN];
+    static constexpr int BK = bk_of<SPLIT>();
+    float As[2][BK][kBM];
+    float As2[SPLIT ? 2 : 1][SPLIT ? BK : 1][SPLIT ? kBM : 4];
+    float Xs[2][BK][kBN];
 };
 
 // true when some column of the tile starting at n0 is still active (all
@@ -183,44 +189,53 @@ __device__ __forceinline__ void simt_tile_mainloop(int M, int N, int m0, int n0,
                                                    SimtSmem<SPLIT>& sm, float (&out)[4][4]) {
     const int t = threadIdx.x;
     const int tc = t & 15, tr = t >> 4;
-    // load mapping: one float4 of Aop and one of X per thread per K step
-    // (four lanes per row, 64 contiguous bytes).  The transposing stores put
-    // row r of K slice k at r ^ swz(k): the four lanes of a row write four
-    // slices whose swizzles differ in bits 3-4, so a warp's stores hit 32
-    // distinct banks; reads apply the same swizzle to a 4-aligned group.
-    const int la_row = t >> 2, la_k = (t & 3) * 4;  // 64 rows x 4 float4
-    const int lx_col = t >> 2, lx_k = (t & 3) * 4;  // 64 cols x 4 float4
+    // load mapping: BK/16 float4 of Aop and of X per thread per K step
+    // (four lanes per row, 64 contiguous bytes each, slices k, k + 16).
+    // The transposing stores put row r of K slice k at r ^ swz(k): the four
+    // lanes of a row write slices whose swizzles differ in bits 3-4, so a
+    // warp's stores hit 32 distinct banks; reads apply the same swizzle to a
+    // 4-aligned group.
+    const int la_row = t >> 2, la_k = (t & 3) * 4;  // 64 rows x 4 float4 (x 2 halves)
+    const int lx_col = t >> 2, lx_k = (t & 3) * 4;  // 64 cols x 4 float4 (x 2 halves)
     auto swz = [](int k) { return ((k >> 2) & 3) << 3; };
 
     // global -> registers (issued a K step ahead) -> shared memory (stored
     // after the current step's FMAs), so the L2 latency overlaps the math
-    float4 ra_g, ra2_g, rx_g;
+    constexpr int BK = bk_of<SPLIT>(), NH = BK / 16;
+    float4 ra_g[NH], ra2_g[NH], rx_g[NH];
     auto fetch = [&](int k0) {
-        ra_g = ra2_g = rx_g = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int gi = m0 + la_row, gk = k0 + la_k;
-        if (gi < M && gk < k_end) {
-            ra_g = load_a4(Aop + (int64_t)gi * lda + gk);
-            if constexpr (SPLIT) ra2_g = load_a4(Aop2 + (int64_t)gi * lda + gk);
+#pragma unroll
+        for (int hf = 0; hf < NH; ++hf) {
+            ra_g[hf] = ra2_g[hf] = rx_g[hf] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int gi = m0 + la_row, gk = k0 + la_k + 16 * hf;
+            if (gi < M && gk < k_end) {
+                ra_g[hf] = load_a4(Aop + (int64_t)gi * lda + gk);
+                if constexpr (SPLIT) ra2_g[hf] = load_a4(Aop2 + (int64_t)gi * lda + gk);
+            }
+            const int gj = n0 + lx_col, gkx = k0 + lx_k + 16 * hf;
+            if (gj < N && gkx < k_end) rx_g[hf] = __ldg(reinterpret_cast<const float4*>(X + (int64_t)gj * ldx + gkx));
         }
-        const int gj = n0 + lx_col, gkx = k0 + lx_k;
-        if (gj < N && gkx < k_end) rx_g = __ldg(reinterpret_cast<const float4*>(X + (int64_t)gj * ldx + gkx));
     };
     auto stash = [&](int buf) {
         const int ra = la_row ^ swz(la_k), rx = lx_col ^ swz(lx_k);
-        if constexpr (SPLIT) {
-            sm.As2[buf][la_k + 0][ra] = ra2_g.x;
-            sm.As2[buf][la_k + 1][ra] = ra2_g.y;
-            sm.As2[buf][la_k + 2][ra] = ra2_g.z;
-            sm.As2[buf][la_k + 3][ra] = ra2_g.w;
+#pragma unroll
+        for (int hf = 0; hf < NH; ++hf) {
+            const int ka = la_k + 16 * hf, kx = lx_k + 16 * hf;
+            if constexpr (SPLIT) {
+                sm.As2[buf][ka + 0][ra] = ra2_g[hf].x;
+                sm.As2[buf][ka + 1][ra] = ra2_g[hf].y;
+                sm.As2[buf][ka + 2][ra] = ra2_g[hf].z;
+                sm.As2[buf][ka + 3][ra] = ra2_g[hf].w;
+            }
+            sm.As[buf][ka + 0][ra] = ra_g[hf].x;
+            sm.As[buf][ka + 1][ra] = ra_g[hf].y;
+            sm.As[buf][ka + 2][ra] = ra_g[hf].z;
+            sm.As[buf][ka + 3][ra] = ra_g[hf].w;
+            sm.Xs[buf][kx + 0][rx] = rx_g[hf].x;
+            sm.Xs[buf][kx + 1][rx] = rx_g[hf].y;
+            sm.Xs[buf][kx + 2][rx] = rx_g[hf].z;
+            sm.Xs[buf][kx + 3][rx] = rx_g[hf].w;
         }
-        sm.As[buf][la_k + 0][ra] = ra_g.x;
-        sm.As[buf][la_k + 1][ra] = ra_g.y;
-        sm.As[buf][la_k + 2][ra] = ra_g.z;
-        sm.As[buf][la_k + 3][ra] = ra_g.w;
-        sm.Xs[buf][lx_k + 0][rx] = rx_g.x;
-        sm.Xs[buf][lx_k + 1][rx] = rx_g.y;
-        sm.Xs[buf][lx_k + 2][rx] = rx_g.z;
-        sm.Xs[buf][lx_k + 3][rx] = rx_g.w;
     };
 
     float acc[4][4], comp[4][4], acc2[SPLIT ? 4 : 1][SPLIT ? 4 : 1];
@@ -239,49 +254,54 @@ __device__ __forceinline__ void simt_tile_mainloop(int M, int N, int m0, int n0,
     fetch(k_begin);
     stash(0);
     __syncthreads();
-    for (int k0 = k_begin; k0 < k_end; k0 += kBK) {
-        const bool more = k0 + kBK < k_end;
-        if (more) fetch(k0 + kBK);
-        float tt[4][4];
+    for (int k0 = k_begin; k0 < k_end; k0 += BK) {
+        const bool more = k0 + BK < k_end;
+        if (more) fetch(k0 + BK);
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int half = 0; half < BK / kKahan; ++half) {
+            float tt[4][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tt[p][q] = 0.0f;
-        // fragments of slice kk + 1 are read before the FMAs of slice kk
-        float4 fa = *reinterpret_cast<const float4*>(&sm.As[buf][0][(tr * 4) ^ swz(0)]);
-        float4 fx = *reinterpret_cast<const float4*>(&sm.Xs[buf][0][(tc * 4) ^ swz(0)]);
-        float4 fa2 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (SPLIT) fa2 = *reinterpret_cast<const float4*>(&sm.As2[buf][0][(tr * 4) ^ swz(0)]);
+            for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int kk = 0; kk < kBK; ++kk) {
-            const float av[4] = {fa.x, fa.y, fa.z, fa.w};
-            const float xv[4] = {fx.x, fx.y, fx.z, fx.w};
-            const float av2[4] = {fa2.x, fa2.y, fa2.z, fa2.w};
-            if (kk + 1 < kBK) {
-                fa = *reinterpret_cast<const float4*>(&sm.As[buf][kk + 1][(tr * 4) ^ swz(kk + 1)]);
-                fx = *reinterpret_cast<const float4*>(&sm.Xs[buf][kk + 1][(tc * 4) ^ swz(kk + 1)]);
-                if constexpr (SPLIT) fa2 = *reinterpret_cast<const float4*>(&sm.As2[buf][kk + 1][(tr * 4) ^ swz(kk + 1)]);
+                for (int q = 0; q < 4; ++q) tt[p][q] = 0.0f;
+            // fragments of slice kk + 1 are read before the FMAs of slice kk
+            const int kb = half * kKahan;
+            float4 fa = *reinterpret_cast<const float4*>(&sm.As[buf][kb][(tr * 4) ^ swz(kb)]);
+            float4 fx = *reinterpret_cast<const float4*>(&sm.Xs[buf][kb][(tc * 4) ^ swz(kb)]);
+            float4 fa2 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (SPLIT) fa2 = *reinterpret_cast<const float4*>(&sm.As2[buf][kb][(tr * 4) ^ swz(kb)]);
+#pragma unroll
+            for (int kk = kb; kk < kb + kKahan; ++kk) {
+                const float av[4] = {fa.x, fa.y, fa.z, fa.w};
+                const float xv[4] = {fx.x, fx.y, fx.z, fx.w};
+                const float av2[4] = {fa2.x, fa2.y, fa2.z, fa2.w};
+                if (kk + 1 < kb + kKahan) {
+                    fa = *reinterpret_cast<const float4*>(&sm.As[buf][kk + 1][(tr * 4) ^ swz(kk + 1)]);
+                    fx = *reinterpret_cast<const float4*>(&sm.Xs[buf][kk + 1][(tc * 4) ^ swz(kk + 1)]);
+                    if constexpr (SPLIT)
+                        fa2 = *reinterpret_cast<const float4*>(&sm.As2[buf][kk + 1][(tr * 4) ^ swz(kk + 1)]);
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) tt[p][q] = fmaf(av[p], xv[q], tt[p][q]);
+                if constexpr (SPLIT) {
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc2[p][q] = fmaf(av2[p], xv[q], acc2[p][q]);
+                }
             }
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) tt[p][q] = fmaf(av[p], xv[q], tt[p][q]);
-            if constexpr (SPLIT) {
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc2[p][q] = fmaf(av2[p], xv[q], acc2[p][q]);
-            }
+                for (int q = 0; q < 4; ++q) {
+                    const float yv = tt[p][q] - comp[p][q];
+                    const float sv = acc[p][q] + yv;
+                    comp[p][q] = (sv - acc[p][q]) - yv;
+                    acc[p][q] = sv;
+                }
         }
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float yv = tt[p][q] - comp[p][q];
-                const float sv = acc[p][q] + yv;
-                comp[p][q] = (sv - acc[p][q]) - yv;
-                acc[p][q] = sv;
-            }
         if (more) stash(buf ^ 1);
         __syncthreads();
         buf ^= 1;
@@ -366,8 +386,13 @@ gemm_simt_kernel(int M, int N, int K, const TA* __restrict__ Aop, const TA* __re
                  int64_t lda, const float* __restrict__ X, int64_t ldx, E epi,
                  double* __restrict__ part, const int32_t* __restrict__ active) {
     constexpr int NR = E::NRED > 0 ? E::NRED : 1;
-    __shared__ __align__(16) SimtSmem<SPLIT> sm;
-    __shared__ double red_s[8][kBN][NR];
+    // the epilogue's reduction scratch reuses the tiles' shared memory: the
+    // main loop ends with a barrier after its last read
+    union Smem {
+        SimtSmem<SPLIT> tiles;
+        double red[8][kBN][NR];
+    };
+    __shared__ __align__(16) Smem sm;
     __shared__ int any_active;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
     if (!tile_has_active(active, N, n0, &any_active)) {
@@ -375,8 +400,8 @@ gemm_simt_kernel(int M, int N, int K, const TA* __restrict__ Aop, const TA* __re
         return;
     }
     float acc[4][4];
-    simt_tile_mainloop<SPLIT, TA>(M, N, m0, n0, 0, (K + 3) & ~3, Aop, Aop2, lda, X, ldx, sm, acc);
-    simt_tile_epilogue<E, NR>(M, N, m0, n0, blockIdx.y, acc, epi, part, red_s);
+    simt_tile_mainloop<SPLIT, TA>(M, N, m0, n0, 0, (K + 3) & ~3, Aop, Aop2, lda, X, ldx, sm.tiles, acc);
+    simt_tile_epilogue<E, NR>(M, N, m0, n0, blockIdx.y, acc, epi, part, sm.red);
 }
 
 // Split-K, for panels too narrow to fill the GPU with output tiles: slice
