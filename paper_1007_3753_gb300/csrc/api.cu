@@ -38,6 +38,11 @@ int dev_alloc(Handle* h, void** p, size_t bytes) {
 static void free_all(Handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    graph_cache_clear(h);
+    if (h->cap_stream) {
+        cudaStreamDestroy(h->cap_stream);
+        h->cap_stream = nullptr;
+    }
     for (void* p : h->allocations) cudaFree(p);
     h->allocations.clear();
     if (h->ws.h_count) cudaFreeHost(h->ws.h_count);

@@ -155,6 +155,10 @@ struct Handle {
     struct UnrollState* ur = nullptr;
     // uneven batch of independent dictionaries (l1_setup_group), see group.cu
     struct GroupState* grp = nullptr;
+    // CUDA graphs of the polling chunks of l1_solve_batch (solve.cu), and the
+    // private stream they are captured on
+    struct GraphCache* graphs = nullptr;
+    cudaStream_t cap_stream = nullptr;
     // sweep profiling (l1_options.profile)
     std::vector<cudaEvent_t> ev_pool;
     int64_t sweep_launches[4] = {0, 0, 0, 0};

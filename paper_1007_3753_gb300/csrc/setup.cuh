@@ -29,6 +29,9 @@ int unroll_forward(Handle* h, const float* b, int64_t ldb, int N, float* x, int6
 int unroll_backward(Handle* h, const float* grad_x, int N, float* grad_b, float* grad_A);
 void unroll_free(Handle* h);
 
+// release the cached CUDA graphs of solve_batch (solve.cu)
+void graph_cache_clear(Handle* h);
+
 // batched solve (solve.cu)
 int solve_batch(Handle* h, const float* b_dev, int64_t ldb, int N, double tol, int max_iter,
                 float* x_dev, int64_t ldx, float* y_dev, int64_t ldy, l1_result* res);

@@ -130,16 +130,30 @@ struct SweepProf {
         }
         return L1_OK;
     }
+    // External records become event nodes when the chunk is captured in a
+    // graph (a plain record inside a capture only marks a dependency)
     void start(int k, double f) {
         if (!on) return;
-        cudaEventRecord(h->ev_pool[2 * used], h->stream);
+        cudaEventRecordWithFlags(h->ev_pool[2 * used], h->stream, cudaEventRecordExternal);
         kind.push_back(k);
         flop.push_back(f);
     }
     void stop() {
         if (!on) return;
-        cudaEventRecord(h->ev_pool[2 * used + 1], h->stream);
+        cudaEventRecordWithFlags(h->ev_pool[2 * used + 1], h->stream, cudaEventRecordExternal);
         ++used;
+    }
+    // a replayed graph records the events of the chunk it was captured from
+    void adopt(const std::vector<int>& k, const std::vector<double>& f) {
+        if (!on) return;
+        kind = k;
+        flop = f;
+        used = (int)k.size();
+    }
+    void reset() {
+        used = 0;
+        kind.clear();
+        flop.clear();
     }
     void collect() {  // after a synchronisation of h->stream
         for (int i = 0; i < used; ++i) {
@@ -159,6 +173,50 @@ struct SweepProf {
 };
 
 }  // namespace
+
+// CUDA graphs of the polling chunks: the launches of check_every iterations
+// depend only on the panel set, the number of slots, the phase and the
+// stopping parameters, so each such chunk is captured once and replayed.
+struct GraphEntry {
+    int q, N, phase, solver, max_iter;
+    double tol;
+    cudaGraphExec_t exec;
+    int64_t nlaunch;
+    std::vector<int> kinds;
+    std::vector<double> flops;
+};
+
+struct GraphCache {
+    std::vector<GraphEntry> entries;
+};
+
+void graph_cache_clear(Handle* h) {
+    if (!h->graphs) return;
+    for (GraphEntry& e : h->graphs->entries) cudaGraphExecDestroy(e.exec);
+    delete h->graphs;
+    h->graphs = nullptr;
+}
+
+static GraphEntry* graph_find(Handle* h, int q, int N, int phase, int solver, double tol, int max_iter) {
+    if (!h->graphs) return nullptr;
+    for (GraphEntry& e : h->graphs->entries)
+        if (e.q == q && e.N == N && e.phase == phase && e.solver == solver && e.tol == tol && e.max_iter == max_iter)
+            return &e;
+    return nullptr;
+}
+
+// largest split-K scratch a sweep of this handle needs for up to N columns
+static size_t splitk_need(const Handle* h, int N) {
+    const int m = (int)h->m, n = (int)h->n;
+    const int shapes[3][2] = {{m, n}, {m, m}, {n, m}};  // (M, K) of A u, F r, A^T y
+    size_t need = 0;
+    for (const auto& sh : shapes)
+        for (int Nn = 9; Nn <= N; ++Nn) {
+            const int S = splitk_slices(h, sh[0], Nn, sh[1]);
+            if (S > 1) need = std::max(need, (size_t)S * Nn * (size_t)(((int64_t)sh[0] + 3) & ~int64_t(3)));
+        }
+    return need;
+}
 
 // A u (rm) or A^T y (cm) sweep on the low-precision copy of A
 template <class E>
@@ -193,6 +251,7 @@ static int ensure_workspace(Handle* h, int N) {
     }
     if (w.h_count) cudaFreeHost(w.h_count);
     w = Workspace{};
+    graph_cache_clear(h);  // the captured launches point into the old buffers
     const int64_t ldm = h->ldm, ldn = h->ldn;
     const int m = (int)h->m, n = (int)h->n;
     for (int q = 0; q < 2; ++q) {
@@ -231,6 +290,14 @@ static int ensure_workspace(Handle* h, int N) {
                             std::max(sweep_row_blocks(m, 1), sweep_row_blocks(n, 1)));
     w.part_slots = (size_t)np;
     L1_TRY(dev_alloc_t(h, &w.part, 2 * (size_t)np * N * kPartStride));
+    {
+        // sized now so that no sweep allocates while a chunk is captured
+        const size_t need = splitk_need(h, N);
+        if (need > h->splitk_floats) {
+            L1_TRY(dev_alloc_t(h, &h->splitk, need));
+            h->splitk_floats = need;
+        }
+    }
     L1_TRY(dev_alloc_t(h, &w.newpos, (size_t)N));
     L1_TRY(dev_alloc_t(h, &w.count, 1));
     if (cudaMallocHost(&w.h_count, 2 * sizeof(int32_t)) != cudaSuccess) return L1_ERR_OOM;
@@ -409,6 +476,7 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
             L1_TRY(tc::split_tf32(h, P->Ux, ldn * (int64_t)N_cur, w.Up[0], w.Up[1], nullptr));
             pieces_valid = true;
         }
+        auto run_chunk = [&](cudaStream_t s) -> int {
         for (int r = 0; r < check_every; ++r) {
             if (solver == L1_DALM) {
                 // Algorithm 2: three sweeps per iteration.  On tcgen05 the
@@ -495,6 +563,53 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                                                        tol, inner_tol, inner_max, max_iter);
                 L1_LAUNCH_CHECK(h);
             }
+        }
+        return L1_OK;
+        };
+        if (h->use_tc) {
+            L1_TRY(run_chunk(s));
+        } else {
+            // capture the chunk once (on the private stream, so that the
+            // caller's stream may be the legacy default stream) and replay it
+            GraphEntry* ge = graph_find(h, q, N_cur, phase, solver, tol, max_iter);
+            if (!ge) {
+                if (!h->cap_stream) L1_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+                const int64_t l0 = h->launches;
+                prof.reset();
+                h->stream = h->cap_stream;
+                cudaError_t ce = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+                int crc = ce == cudaSuccess ? run_chunk(h->cap_stream) : L1_ERR_CUDA;
+                cudaGraph_t graph = nullptr;
+                const cudaError_t ee = ce == cudaSuccess ? cudaStreamEndCapture(h->cap_stream, &graph) : ce;
+                h->stream = s;
+                if (crc == L1_OK && ee != cudaSuccess) {
+                    set_last_error(std::string("chunk capture: ") + cudaGetErrorString(ee));
+                    crc = L1_ERR_CUDA;
+                }
+                cudaGraphExec_t exec = nullptr;
+                if (crc == L1_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+                    set_last_error("chunk graph: instantiation failed");
+                    crc = L1_ERR_CUDA;
+                }
+                if (graph) cudaGraphDestroy(graph);
+                if (crc != L1_OK) {
+                    cudaGetLastError();
+                    return crc;
+                }
+                if (!h->graphs) h->graphs = new GraphCache();
+                if (h->graphs->entries.size() >= 512) {
+                    for (GraphEntry& e : h->graphs->entries) cudaGraphExecDestroy(e.exec);
+                    h->graphs->entries.clear();
+                }
+                h->graphs->entries.push_back(
+                    GraphEntry{q, N_cur, phase, solver, max_iter, tol, exec, h->launches - l0, prof.kind, prof.flop});
+                ge = &h->graphs->entries.back();
+                h->launches = l0;
+                prof.reset();
+            }
+            L1_CUDA_TRY(cudaGraphLaunch(ge->exec, s));
+            h->launches += ge->nlaunch;
+            prof.adopt(ge->kinds, ge->flops);
         }
         rounds += check_every;
         count_active_kernel<<<1, 1024, 0, s>>>(c.active, N_cur, w.count);
