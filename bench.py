@@ -60,6 +60,19 @@ def measured_peaks() -> dict:
         return dict(FALLBACK_PEAKS)
 
 
+def reduce_over_ranks(dist, time_value: float, count: int, device: str = "cuda"):
+    """Whole-job figures of a replicated run: the slowest rank's time and the
+    sum of the ranks' converged solves (dist None: this process only)."""
+    if dist is None:
+        return time_value, count
+    import torch
+    t = torch.tensor([time_value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([count], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 def workload(rank: int = 0):
     return synthetic.cab_problem(BENCH["m"], BENCH["classes"], BENCH["per_class"], BENCH["N"],
                                  corrupt=BENCH["corrupt"], seed=BENCH["seed"] + rank)
@@ -246,13 +259,7 @@ def bench_ours(args, rank, world):
     clocks = sampler.stop() if sampler else None
     info1, infop1 = s.info(), sp.info()
     total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        cv = torch.tensor([conv], dtype=torch.float64, device="cuda")
-        dist.all_reduce(cv, op=dist.ReduceOp.SUM)
-        conv = int(cv.item())
+    total_ms, conv = reduce_over_ranks(dist, total_ms, conv)
     value = conv / (total_ms / 1e3)
 
     # ---- end to end through the same call with pinned host buffers
@@ -267,13 +274,7 @@ def bench_ours(args, rank, world):
         e2e_conv += int(np.sum(res["status"] == l1.CONVERGED))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-        cv = torch.tensor([e2e_conv], dtype=torch.float64, device="cuda")
-        dist.all_reduce(cv, op=dist.ReduceOp.SUM)
-        e2e_conv = int(cv.item())
+    e2e_s, e2e_conv = reduce_over_ranks(dist, e2e_s, e2e_conv)
 
     if rank != 0:
         s.close()
