@@ -46,7 +46,7 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates of the part
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-batch launch
 # (all 1024 columns active, cold cache) of each CUDA-core sweep of this
 # build, and the algorithmic bytes of that launch
-SIMT_TRAFFIC = {"A_u": (18.42e6, 18.2e6), "Finv_r": (21.16e6, 21.0e6), "At_y": (19.24e6, 19.1e6)}
+SIMT_TRAFFIC = {"A_u": (18.42e6, 18.2e6), "Finv_r": (21.12e6, 21.0e6), "At_y": (19.27e6, 19.1e6)}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
