@@ -83,7 +83,8 @@ def config_dict(extra=None):
          "m": BENCH["m"], "n": BENCH["classes"] * BENCH["per_class"], "classes": BENCH["classes"],
          "rhs_per_gpu": BENCH["N"], "solver": BENCH["solver"], "tol": BENCH["tol"],
          "max_iter": BENCH["max_iter"], "corrupt_fraction": BENCH["corrupt"],
-         "l2": "flushed (512 MiB write) before each timed step; A (4.9 MB) is L2-resident within a solve"}
+         "l2": (f"flushed (512 MiB write) before each timed step; A ({BENCH['m'] * BENCH['classes'] * BENCH['per_class'] * 4 / 1e6:.1f} MB FP32) "
+                "and F (the inverse of A A^T + I) stay in L2 within a solve when they fit (129 MB)")}
     if extra:
         d.update(extra)
     return d
@@ -220,10 +221,11 @@ def bench_ours(args, rank, world):
     # two handles on the same dictionary: the last timed step runs on the one
     # that times every sweep with CUDA events (the roofline), the others on
     # the one without events
+    prec = {"fp32": l1.A_FP32, "bf16": l1.A_BF16, "fp8": l1.A_FP8E4M3}[args.precision]
     s = l1.Solver(A_d, mode=l1.CAB, solver=solver, class_offsets=off, profile=False, engine=engine,
-                  stream=stream.cuda_stream)
+                  precision=prec, stream=stream.cuda_stream)
     sp = l1.Solver(A_d, mode=l1.CAB, solver=solver, class_offsets=off, profile=True, engine=engine,
-                   stream=stream.cuda_stream)
+                   precision=prec, stream=stream.cuda_stream)
     setup_ms = s.info()["setup_ms"]
     tol, max_iter = BENCH["tol"], BENCH["max_iter"]
 
@@ -309,7 +311,8 @@ def bench_ours(args, rank, world):
         # the y-step multiplies by the FP32 pair F_hi + F_lo: two products per
         # algorithmic one
         terms = [1, 2, 1, 1][k]
-        tr = SIMT_TRAFFIC.get(names[k])
+        default_size = (BENCH["m"], BENCH["classes"], BENCH["per_class"], BENCH["N"]) == (1024, 40, 30, 1024)
+        tr = SIMT_TRAFFIC.get(names[k]) if default_size and args.precision == "fp32" else None
         roofline = {"bound": "alu", "kernel": f"sweep {names[k]} (gemm_simt_kernel / split-K pair)",
                     "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": tr[0] if tr else None,
@@ -321,18 +324,21 @@ def bench_ours(args, rank, world):
                     "share_of_sweep_time": d_ms[k] / max(1e-9, sum(d_ms))}
 
     # ---- CPU oracle on a bounded sample of the same workload
-    threads = min(os.cpu_count() or 1, 16)
-    sample = list(range(threads))
-    c_conv, c_dt, _ = run_cpu_oracle(p, sample, threads, tol, max_iter)
-    cpu = {"value": c_conv / c_dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
-           "sample": f"first {len(sample)} of {N} test vectors, one per thread, same tol/max_iter"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        threads = min(os.cpu_count() or 1, 16)
+        sample = list(range(threads))
+        c_conv, c_dt, _ = run_cpu_oracle(p, sample, threads, tol, max_iter)
+        cpu = {"value": c_conv / c_dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {len(sample)} of {N} test vectors, one per thread, same tol/max_iter"}
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else f"{args.precision} A, f32 arithmetic",
             "data": "synthetic",
             "config": config_dict({"parallelism": f"replicas{world}" if world > 1 else "single",
-                                   "engine": args.engine, "setup_ms": setup_ms,
+                                   "engine": args.engine, "precision": args.precision, "setup_ms": setup_ms,
                                    "mean_iters": statistics.mean(iters),
                                    "label_accuracy_vs_planted": labels_ok / (args.steps * N)}),
             "e2e": {"value": e2e_conv / e2e_s, "unit": "solves/s",
@@ -440,6 +446,84 @@ def bench_group(args, rank, world):
     return 0
 
 
+# unrolled PALM and its adjoint (reading R11): A 1024 x 2048 Gaussian with unit
+# columns, N = 256 targets with 50 nonzeros, K = 200 inner steps, a
+# multiplier step every J = 10, checkpoints every 20 steps
+UNROLL = dict(m=1024, n=2048, N=256, k=50, K=200, J=10, ckpt=20, seed=5000)
+
+
+def bench_unrolled(args, rank, world):
+    """--workload unrolled: one step = the unrolled forward (l1_solve_batch)
+    plus the adjoint (l1_backward with grad_x = x - x_target), device-resident."""
+    import torch
+
+    import paper_1007_3753_gb300 as l1
+    from paper_1007_3753_gb300 import build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    l1.load()
+    u = UNROLL
+    p = synthetic.unrolled_instance(u["m"], u["n"], u["N"], k=u["k"], seed=u["seed"] + rank)
+    m, n, N, K, J = u["m"], u["n"], u["N"], u["K"], u["J"]
+    stream = torch.cuda.current_stream()
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32).T)).cuda().t()
+    A_d, B_d, Xt_d = dev(p["A"]), dev(p["B"]), dev(p["X_target"])
+    s = l1.Solver(A_d, mode=l1.P1, solver=l1.PALM, unroll_K=K, unroll_J=J, ckpt_every=u["ckpt"],
+                  stream=stream.cuda_stream)
+    x_d = torch.empty((N, n), dtype=torch.float32, device="cuda").t()
+    gb = torch.empty((N, m), dtype=torch.float32, device="cuda").t()
+    gA = torch.empty((n, m), dtype=torch.float32, device="cuda").t()
+
+    def step():
+        s.solve(B_d, 0.0, 1, x=x_d)
+        gx = (x_d - Xt_d).t().contiguous().t()
+        s.backward(gx, grad_b=gb, grad_A=gA)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info0 = s.info()
+    step_ms = []
+    for _ in range(args.steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+    info1 = s.info()
+    total_ms = sum(step_ms)
+    # executed FP32 flops per step: every sweep is 2 m n N; forward K steps x 2
+    # sweeps + (K/J - 1) multiplier sweeps + 1 residual sweep; backward the
+    # recomputation (forward again, less the residual sweep), K x 2 reverse
+    # sweeps, K/J - 1 multiplier adjoints, and grad_A as 2 m n N per step x 2
+    # plus 2 m n N per multiplier adjoint
+    sweep = 2.0 * m * n * N
+    n_outer = -(-K // J)
+    fwd = (2 * K + (n_outer - 1) + 1) * sweep
+    bwd = (2 * K + (n_outer - 1)) * sweep + 2 * K * sweep + (n_outer - 1) * sweep + (2 * K + (n_outer - 1)) * sweep
+    flop = fwd + bwd
+    achieved = flop / (total_ms / args.steps / 1e3) / 1e12
+    line = {"metric": "unrolled PALM forward + adjoint samples/sec", "value": N * args.steps / (total_ms / 1e3),
+            "unit": "samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"unrolled_palm_m{m}_n{n}_N{N}_K{K}", "J": J, "ckpt_every": u["ckpt"],
+                       "device_bytes": info1["device_bytes"], "flop_per_step": flop},
+            "gpu_launches": int(info1["gpu_launches"] - info0["gpu_launches"]),
+            "roofline": {"bound": "alu", "kernel": "whole step (CUDA-core sweeps and rank_update_kernel)",
+                         "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
+                         "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived)"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,9 +533,19 @@ def main():
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--max-iter", type=int, default=None)
     ap.add_argument("--engine", choices=["tc", "simt"], default="simt")
-    ap.add_argument("--workload", choices=["cab", "qp-group"], default="cab")
+    ap.add_argument("--workload", choices=["cab", "qp-group", "unrolled"], default="cab")
     ap.add_argument("--count", type=int, default=None, help="qp-group: number of instances")
+    ap.add_argument("--m", type=int, default=None, help="cab: rows of A")
+    ap.add_argument("--classes", type=int, default=None, help="cab: classes")
+    ap.add_argument("--per-class", type=int, default=None, help="cab: columns per class")
+    ap.add_argument("--N", type=int, default=None, help="cab: right-hand sides")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32",
+                    help="cab: stored precision of A (bf16 / fp8 add the FP32 refinement phase)")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="cab: skip the CPU oracle leg")
     args = ap.parse_args()
+    for key, val in (("m", args.m), ("classes", args.classes), ("per_class", args.per_class), ("N", args.N)):
+        if val is not None:
+            BENCH[key] = val
     if args.tol is not None:
         BENCH["tol"] = args.tol
     if args.max_iter is not None:
@@ -462,6 +556,8 @@ def main():
         return bench_reference(args, rank, world)
     if args.workload == "qp-group":
         return bench_group(args, rank, world)
+    if args.workload == "unrolled":
+        return bench_unrolled(args, rank, world)
     return bench_ours(args, rank, world)
 
 
