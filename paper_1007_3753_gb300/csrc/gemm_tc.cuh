@@ -204,11 +204,7 @@ gemm_tc_kernel(const __grid_constant__ PieceMaps maps, const TermList tl, int M,
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
     const int kblocks = (K + kElemPerRow - 1) / kElemPerRow;
     const int nterms = tl.n;
-#ifdef L1_TC_NODRAIN
-    const int nprod = 1;  // timing experiment: one accumulator for the whole sweep
-#else
     const int nprod = kblocks * nterms;  // products drained one by one
-#endif
 
     if (threadIdx.x == 0) {
         flags[0] = 0;
@@ -294,19 +290,6 @@ gemm_tc_kernel(const __grid_constant__ PieceMaps maps, const TermList tl, int M,
                 }
                 const uint32_t st = smem_u32(smem + s * S::kStage);
                 for (int t = 0; t < nterms; ++t, ++prod) {
-#ifdef L1_TC_NODRAIN
-                    {
-                        const uint32_t a0 = st + tl.ia[t] * S::kATile;
-                        const uint32_t x0 = st + NPA * S::kATile + tl.ix[t] * S::kXTile;
-                        asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-                        for (int k = 0; k < kMmaPerBlock; ++k)
-                            mma_tf32(tmem, smem_desc(a0 + k * kMmaK * 4), smem_desc(x0 + k * kMmaK * 4), kIdesc,
-                                     (prod == 0 && k == 0) ? 0u : 1u);
-                        if (prod == kblocks * nterms - 1) mma_commit(&acc_full[0]);
-                        continue;
-                    }
-#endif
                     const int b = prod % kAccBufs;
                     if (!mbar_wait(&acc_empty[b], ((uint32_t)(prod / kAccBufs) & 1u) ^ 1u)) {
                         atomicCAS(err, ERR_NONE, ERR_WAIT_DRAIN);
