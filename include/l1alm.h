@@ -48,7 +48,7 @@ extern "C" {
 #define L1_ERR_CUDA (-4)        /* a CUDA runtime call failed (message: l1_last_error) */
 #define L1_ERR_TIMEOUT (-5)     /* a bounded device wait expired; the context stays usable */
 #define L1_ERR_NO_TAPE (-6)     /* l1_backward without an unrolled forward */
-#define L1_ERR_UNSUPPORTED (-7) /* valid request this build does not implement */
+#define L1_ERR_UNSUPPORTED (-7) /* valid request the library does not implement */
 
 /* --------------------------------------------------- per-instance status */
 #define L1_CONVERGED 0 /* stopping rule met: ||w_{k+1}-w_k|| / ||w_k|| < tol (§VI-C) */

@@ -109,7 +109,7 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
         for (int c = 0; c < o.class_count; ++c)
             if (o.class_offsets[c + 1] <= o.class_offsets[c]) return L1_ERR_INVALID_ARG;
     }
-    // not implemented in this build
+    // requests the library does not implement
     if (mode == L1_P1_2 && o.solver != L1_PALM) return L1_ERR_UNSUPPORTED;  // R10 is a PALM
     // low-precision A: batched DALM on the CUDA-core sweeps (with refinement)
     if (o.precision != L1_A_FP32 &&
