@@ -406,7 +406,9 @@ gemm_simt_kernel(int M, int N, int K, const TA* __restrict__ Aop, const TA* __re
 
 // Split-K, for panels too narrow to fill the GPU with output tiles: slice
 // blockIdx.z of K (chunk kchunk, a multiple of kBK) writes its tile sum to
-// Wk[(z * N + j) * ldw + i].
+// Wk[(z * M + i) * ldw + j] (rows of a slice contiguous over the columns, so
+// a thread's four columns move as one float4 and a warp's accesses coalesce;
+// ldw = N rounded up to 4).
 template <bool SPLIT, class TA>
 __global__ void __launch_bounds__(256)
 gemm_simt_splitk_kernel(int M, int N, int K, int kchunk, const TA* __restrict__ Aop,
@@ -421,15 +423,20 @@ gemm_simt_splitk_kernel(int M, int N, int K, int kchunk, const TA* __restrict__ 
     float acc[4][4];
     simt_tile_mainloop<SPLIT, TA>(M, N, m0, n0, k_begin, k_end, Aop, Aop2, lda, X, ldx, sm, acc);
     const int t = threadIdx.x, tc = t & 15, tr = t >> 4;
-    float* w = Wk + (int64_t)blockIdx.z * N * ldw;
+    float* w = Wk + (int64_t)blockIdx.z * M * ldw;
+    const int j0 = n0 + tc * 4;
+    if (j0 >= N) return;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int j = n0 + tc * 4 + q;
-        if (j >= N) continue;
+    for (int p = 0; p < 4; ++p) {
+        const int i = m0 + tr * 4 + p;
+        if (i >= M) continue;
+        float* row = w + (int64_t)i * ldw + j0;
+        if (j0 + 3 < N) {
+            *reinterpret_cast<float4*>(row) = make_float4(acc[p][0], acc[p][1], acc[p][2], acc[p][3]);
+        } else {
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int i = m0 + tr * 4 + p;
-            if (i < M) w[(int64_t)j * ldw + i] = acc[p][q];
+            for (int q = 0; q < 4; ++q)
+                if (j0 + q < N) row[q] = acc[p][q];
         }
     }
 }
@@ -450,21 +457,32 @@ splitk_epilogue_kernel(int M, int N, int S, const float* __restrict__ Wk, int64_
     }
     const int t = threadIdx.x, tc = t & 15, tr = t >> 4;
     float acc[4][4];
+    const int j0 = n0 + tc * 4;
+    const bool vec = j0 + 3 < N;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int j = min(n0 + tc * 4 + q, N - 1);
+    for (int p = 0; p < 4; ++p) {
+        const int i = min(m0 + tr * 4 + p, M - 1);
+        float sm[4] = {0.f, 0.f, 0.f, 0.f}, cm[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int z = 0; z < S; ++z) {
+            const float* row = Wk + ((int64_t)z * M + i) * ldw;
+            float v[4];
+            if (vec) {
+                const float4 f = *reinterpret_cast<const float4*>(row + j0);
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+            } else {
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const int i = min(m0 + tr * 4 + p, M - 1);
-            float s = 0.0f, c = 0.0f;
-            for (int z = 0; z < S; ++z) {
-                const float y = Wk[((int64_t)z * N + j) * ldw + i] - c;
-                const float u = s + y;
-                c = (u - s) - y;
-                s = u;
+                for (int q = 0; q < 4; ++q) v[q] = row[min(j0 + q, N - 1)];
             }
-            acc[p][q] = s - c;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float y = v[q] - cm[q];
+                const float u = sm[q] + y;
+                cm[q] = (u - sm[q]) - y;
+                sm[q] = u;
+            }
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = sm[q] - cm[q];
     }
     simt_tile_epilogue<E, NR>(M, N, m0, n0, blockIdx.y, acc, epi, part, red_s);
 }
@@ -505,9 +523,9 @@ int launch_sweep(Handle* h, int M, int N, int K, const TA* Aop, int64_t lda, con
     }
     dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
     int S = splitk_slices(h, M, N, K);
-    const int64_t ldw = ((int64_t)M + 3) & ~int64_t(3);
+    const int64_t ldw = ((int64_t)N + 3) & ~int64_t(3);
     if (S > 1) {
-        const size_t need = (size_t)S * N * ldw;
+        const size_t need = (size_t)S * M * ldw;
         if (need > h->splitk_floats) {
             // grows once to the largest narrow sweep this handle has seen
             if (h->splitk) cudaStreamSynchronize(s);

@@ -213,7 +213,7 @@ static size_t splitk_need(const Handle* h, int N) {
     for (const auto& sh : shapes)
         for (int Nn = 9; Nn <= N; ++Nn) {
             const int S = splitk_slices(h, sh[0], Nn, sh[1]);
-            if (S > 1) need = std::max(need, (size_t)S * Nn * (size_t)(((int64_t)sh[0] + 3) & ~int64_t(3)));
+            if (S > 1) need = std::max(need, (size_t)S * sh[0] * (size_t)(((int64_t)Nn + 3) & ~int64_t(3)));
         }
     return need;
 }
