@@ -118,6 +118,7 @@ __global__ void set_param_kernel(double* param, int n, double v) {
 struct SweepProf {
     Handle* h;
     bool on;
+    bool capturing = false;  // the chunk is being captured into a graph
     int used = 0;
     std::vector<int> kind;
     std::vector<double> flop;
@@ -130,17 +131,21 @@ struct SweepProf {
         }
         return L1_OK;
     }
-    // External records become event nodes when the chunk is captured in a
-    // graph (a plain record inside a capture only marks a dependency)
+    // Inside a capture, external records become event nodes of the graph (a
+    // plain record there only marks a dependency); outside, plain records.
+    void record(cudaEvent_t e) {
+        if (capturing) cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
+        else cudaEventRecord(e, h->stream);
+    }
     void start(int k, double f) {
         if (!on) return;
-        cudaEventRecordWithFlags(h->ev_pool[2 * used], h->stream, cudaEventRecordExternal);
+        record(h->ev_pool[2 * used]);
         kind.push_back(k);
         flop.push_back(f);
     }
     void stop() {
         if (!on) return;
-        cudaEventRecordWithFlags(h->ev_pool[2 * used + 1], h->stream, cudaEventRecordExternal);
+        record(h->ev_pool[2 * used + 1]);
         ++used;
     }
     // a replayed graph records the events of the chunk it was captured from
@@ -578,7 +583,9 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                 prof.reset();
                 h->stream = h->cap_stream;
                 cudaError_t ce = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+                prof.capturing = true;
                 int crc = ce == cudaSuccess ? run_chunk(h->cap_stream) : L1_ERR_CUDA;
+                prof.capturing = false;
                 cudaGraph_t graph = nullptr;
                 const cudaError_t ee = ce == cudaSuccess ? cudaStreamEndCapture(h->cap_stream, &graph) : ce;
                 h->stream = s;

@@ -336,3 +336,22 @@ def test_graph_replay_is_deterministic(l1):
     assert np.array_equal(r3["label"][:40], r1["label"])
     assert np.array_equal(r3["label"][40:], r1["label"][:30])
     s.close()
+
+
+@pytest.mark.parametrize("engine", ["simt", "tc"])
+def test_profiled_solve_reports_sweep_times(l1, engine):
+    """l1_options.profile times every sweep with CUDA events, whether the
+    chunk is replayed from a graph (CUDA-core sweeps) or launched directly
+    (tensor-core engine); the profiled solve equals the unprofiled one."""
+    p = synthetic.cab_problem(192, 6, 30, 40, seed=23)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    eng = l1.ENGINE_TC if engine == "tc" else l1.ENGINE_SIMT
+    s0 = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=eng)
+    s1 = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=eng, profile=True)
+    x0, _, r0 = s0.solve(_dev(B), tol=0.0, max_iter=64)
+    x1, _, r1 = s1.solve(_dev(B), tol=0.0, max_iter=64)
+    assert torch.equal(x0, x1)
+    info = s1.info()
+    assert all(v > 0 for v in info["sweep_launches"][:3]) and all(v > 0 for v in info["sweep_ms"][:3])
+    s0.close()
+    s1.close()
