@@ -51,25 +51,33 @@ class PalmOpts(C.Structure):
                 ("epsilon", C.c_double)]
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile one C source of the oracle into the shared library ``out``
+    (gcc, IEEE double: no contraction into FMA, no fast-math)."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile ``l1_oracle.c`` into ``_build/liboracle.so`` with gcc."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return compile_source(_SRC, _LIB_PATH)
 
 
 def lib() -> C.CDLL:
+    """The oracle library.  ``L1_ORACLE_LIB`` names another build of it (the
+    planted-mistake tests load deliberately broken copies that way)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
+            path = os.environ.get("L1_ORACLE_LIB") or build()
             L = C.CDLL(path)
             dp = C.POINTER(C.c_double)
             ip = C.POINTER(C.c_int)

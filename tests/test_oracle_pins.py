@@ -245,6 +245,101 @@ def test_closed_forms():
     assert abs(np.abs(w).sum() - np.abs(b).sum()) <= 1e-9 * np.abs(b).sum()
 
 
+# ------------------------------------------------------------ FISTA rate
+
+def _diag_lasso(n=64, lam=1e-3, seed=0):
+    """(QP_lambda) with A = diag(d), d_i^2 log-uniform in [1e-4, 1] (so
+    L = ||A||_2^2 = 1), and a planted optimum: the problem separates, and a
+    nonzero x*_i is optimal exactly when d_i b_i = d_i^2 x*_i + lam sign(x*_i)
+    (the subgradient condition of Eq. 11 per coordinate), so b is built from
+    x*.  On this spectrum plain soft-thresholding steps (no momentum) leave a
+    gap near ||x*||^2 / (8 k ln 1e4), which crosses the FISTA bound below
+    before k = 100."""
+    g = np.random.default_rng(seed)
+    d = np.sqrt(np.logspace(-4, 0, n))
+    xs = g.choice([-1.0, 1.0], n) * (0.5 + g.random(n))
+    b = d * xs + lam * np.sign(xs) / d
+    A = np.asfortranarray(np.diag(d))
+
+    def F(x):
+        return 0.5 * np.sum((b - d * x) ** 2) + lam * np.abs(x).sum()
+    return A, b, xs, F, lam
+
+
+def _potential(xk_of, xs, F, L, K):
+    """E_k = (2/L) t_k^2 (F(x_k) - F(x*)) + ||t_k x_k - (t_k - 1) x_{k-1} - x*||^2
+    for k = 1..K, x_0 = 0, t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2.  The
+    proof of FISTA's O(1/k^2) rate (Beck and Teboulle, Lemmas 4.1-4.2, the rate
+    §IV-A quotes) shows E_k is non-increasing and E_1 <= ||x_0 - x*||^2.  The
+    first needs t_{k+1}^2 - t_{k+1} = t_k^2, so a wrong t here fails on a
+    correct iteration too."""
+    X = [np.zeros(xs.shape)] + [xk_of(k) for k in range(1, K + 1)]
+    t = [0.0, 1.0]
+    for _ in range(K):
+        t.append(0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t[-1] ** 2)))
+    Fs = F(xs)
+    E = []
+    for k in range(1, K + 1):
+        u = t[k] * X[k] - (t[k] - 1.0) * X[k - 1] - xs
+        E.append(2.0 / L * t[k] ** 2 * (F(X[k]) - Fs) + u @ u)
+    return np.array(E)
+
+
+def _rate_bound_holds(xk_of, xs, F, L, ks):
+    """F(x_k) - F(x*) <= 2 L ||x_0 - x*||^2 / (k+1)^2 with x_0 = 0: the
+    non-asymptotic O(1/k^2) rate of FISTA quoted in §IV-A (Beck and Teboulle,
+    Theorem 4.4, constant step 1/L with L >= ||A||_2^2)."""
+    Fs = F(xs)
+    R2 = xs @ xs
+    worst = 0.0
+    for k in ks:
+        gap = F(xk_of(k)) - Fs
+        assert gap >= -1e-12 * abs(Fs), (k, gap)  # x* is the minimiser
+        worst = max(worst, gap / (2.0 * L * R2 / (k + 1) ** 2))
+    return worst
+
+
+def test_fista_meets_its_rate_bound():
+    A, b, xs, F, lam = _diag_lasso()
+    worst = _rate_bound_holds(lambda k: oracle.fista_qp(A, b, lam, L=1.0, tol=0.0, max_iter=k)[0],
+                              xs, F, 1.0, range(1, 401))
+    assert worst <= 1.0, worst
+
+
+def test_palm_inner_fista_meets_its_rate_bound():
+    """One P1 outer step of Algorithm 1 from x = 0, theta = 0: the inner loop
+    is FISTA on ||w||_1 + xi/2 ||b - A w||^2, i.e. (QP_lambda) with
+    lambda = 1/xi, so its k-th iterate obeys the same bound."""
+    A, b, xs, F, lam = _diag_lasso(seed=1)
+    worst = _rate_bound_holds(
+        lambda k: oracle.palm(A, b, mode=oracle.MODE_P1, tol=0.0, max_outer=1, inner_max=k,
+                              inner_tol=0.0, xi0=1.0 / lam, L=1.0)[0],
+        xs, F, 1.0, range(1, 401))
+    assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("path", ["fista_qp", "palm_inner", "unrolled_block"])
+def test_fista_potential_is_non_increasing(path):
+    """FISTA (Eq. 18), the inner loop of one P1 outer step of Algorithm 1, and
+    the first block of unrolled PALM (K = J = k, reading R11) all take the
+    k-th FISTA iterate of (QP_lambda) with lambda = 1/xi from x = 0."""
+    A, b, xs, F, lam = _diag_lasso(seed=2)
+    if path == "fista_qp":
+        def xk_of(k):
+            return oracle.fista_qp(A, b, lam, L=1.0, tol=0.0, max_iter=k)[0]
+    elif path == "palm_inner":
+        def xk_of(k):
+            return oracle.palm(A, b, mode=oracle.MODE_P1, tol=0.0, max_outer=1, inner_max=k,
+                               inner_tol=0.0, xi0=1.0 / lam, L=1.0)[0]
+    else:
+        def xk_of(k):
+            return oracle.unrolled_palm(A, b, 1.0 / lam, 1.0, k, k, np.zeros(b.shape),
+                                        grad=False)[0]
+    E = _potential(xk_of, xs, F, 1.0, 150)
+    assert E[0] <= xs @ xs
+    assert np.all(np.diff(E) <= 1e-9 * E[:-1]), np.max(np.diff(E) / E[:-1])
+
+
 def test_lipschitz_is_spectral_norm_squared():
     for seed in range(3):
         A, _ = _tiny(seed, 30, 50)
@@ -293,8 +388,9 @@ def test_invariances():
 
 # ----------------------------------------------------------- classification
 
-def test_classify_hand_fixture():
-    fx = json.load(open(os.path.join(GOLD, "classify_hand.json")))
+@pytest.mark.parametrize("name", ["classify_hand.json", "classify_hand_error.json"])
+def test_classify_hand_fixture(name):
+    fx = json.load(open(os.path.join(GOLD, name)))
     A = np.asfortranarray(np.array(fx["A_columns"], dtype=float).T)
     lab, slab, resid, sci = oracle.classify(A, fx["offsets"], fx["b"], fx["x"], fx["e"])
     assert lab == fx["label"] and slab == fx["sci_label"]
