@@ -156,14 +156,35 @@ def run_cpu_oracle(p, cols, threads, tol, max_iter):
     A, B = p["A"], p["B"]
 
     def one(j):
-        return oracle.dalm(A, B[:, j], cab=True, tol=tol, max_iter=max_iter)[2]
+        return oracle.dalm(A, B[:, j], cab=True, tol=tol, max_iter=max_iter)
 
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        stats = list(ex.map(one, cols))
+        outs = list(ex.map(one, cols))
     dt = time.perf_counter() - t0
-    conv = sum(1 for s in stats if s["converged"])
-    return conv, dt, stats
+    conv = sum(1 for _, _, st in outs if st["converged"])
+    return conv, dt, outs
+
+
+def oracle_agreement(p, cols, x_gpu, obj_gpu, label_gpu, outs, bar=1e-4):
+    """Per sampled test vector j: ||x_gpu - w_j|| / ||w_j|| and the relative
+    objective error against the oracle's w_j = [x; e] (same tol and
+    max_iter), and whether the class labels agree.  x_gpu holds the sampled
+    columns of the GPU solve in the order of cols."""
+    import oracle
+    A, B, off = p["A"], p["B"], p["offsets"]
+    n = A.shape[1]
+    ex, eo, labels = [], [], 0
+    for k, (j, (w, _, _)) in enumerate(zip(cols, outs)):
+        nw = np.linalg.norm(w)
+        ex.append(float(np.linalg.norm(np.asarray(x_gpu[:, k], np.float64) - w) / nw) if nw > 0 else 0.0)
+        f = float(np.abs(w).sum())
+        eo.append(abs(float(obj_gpu[k]) - f) / f if f > 0 else 0.0)
+        labels += int(oracle.classify(A, off, B[:, j], w[:n], w[n:])[0] == int(label_gpu[k]))
+    return {"sample": f"test vectors {cols[0]}..{cols[-1]} of the last timed solve, oracle at the same tol/max_iter",
+            "max_rel_err_x": max(ex), "max_rel_err_obj": max(eo),
+            "within_bar": sum(1 for e in ex if e <= bar), "bar": bar, "of": len(ex),
+            "labels_equal": labels}
 
 
 def bench_reference(args, rank, world):
@@ -245,6 +266,7 @@ def bench_ours(args, rank, world):
     if sampler:
         sampler.start()
     step_ms, conv, iters, labels_ok = [], 0, [], 0
+    check_cols = min(os.cpu_count() or 1, 16, N)
     for step in range(args.steps):
         flush.fill_(1.0)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -259,6 +281,10 @@ def bench_ours(args, rank, world):
         labels_ok += int(np.sum(res["label"] == p["labels"]))
     barrier()
     clocks = sampler.stop() if sampler else None
+    # the first columns of the last timed solve, for the comparison with the
+    # oracle below (later calls reuse x_d)
+    x_check = x_d[:, :check_cols].cpu().numpy()
+    res_check = {k: np.asarray(res[k][:check_cols]) for k in ("primal_obj", "label")}
     info1, infop1 = s.info(), sp.info()
     total_ms = sum(step_ms)
     total_ms, conv = reduce_over_ranks(dist, total_ms, conv)
@@ -357,12 +383,18 @@ def bench_ours(args, rank, world):
 
     # ---- CPU oracle on a bounded sample of the same workload
     cpu = None
+    agreement = None
     if not args.no_cpu_baseline:
         threads = min(os.cpu_count() or 1, 16)
-        sample = list(range(threads))
-        c_conv, c_dt, _ = run_cpu_oracle(p, sample, threads, tol, max_iter)
+        sample = list(range(min(threads, N)))
+        c_conv, c_dt, outs = run_cpu_oracle(p, sample, threads, tol, max_iter)
         cpu = {"value": c_conv / c_dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
                "sample": f"first {len(sample)} of {N} test vectors, one per thread, same tol/max_iter"}
+        try:
+            agreement = oracle_agreement(p, sample, x_check, res_check["primal_obj"], res_check["label"],
+                                         outs)
+        except Exception as exc:  # reported in the line, never fatal to it
+            agreement = {"error": f"{type(exc).__name__}: {exc}"}
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -379,7 +411,7 @@ def bench_ours(args, rank, world):
             "gpu_launches": int((info1["gpu_launches"] - info0["gpu_launches"]) +
                                 (infop1["gpu_launches"] - infop0["gpu_launches"])),
             "roofline": roofline, "roofline_full_width": roofline_full, "cpu_baseline": cpu,
-            "per_instance_gpu": per_instance, "clocks": clocks}
+            "per_instance_gpu": per_instance, "oracle_agreement": agreement, "clocks": clocks}
     print(json.dumps(line), flush=True)
     s.close()
     sp.close()
