@@ -597,7 +597,8 @@ P1 = dict(m=200, n=400, k=20, count=20, tol=1e-6, max_iter=5000)
 def bench_p1(args, rank, world):
     """--workload p1: the 20 instances as one batch of right-hand sides
     sharing A (one dictionary, as the batched API requires): instance j is
-    x0_j on the seed-0 dictionary; DALM and PALM; exact recovery checked."""
+    x0_j on the seed-0 dictionary; DALM and PALM; exact recovery checked.
+    P1,2 runs on the same x0 with noise added to b."""
     import torch
 
     import paper_1007_3753_gb300 as l1
@@ -633,6 +634,32 @@ def bench_p1(args, rank, world):
         out[name] = {"solves_per_s": conv / (ms / 1e3), "ms_per_batch": ms / args.steps,
                      "mean_iters": float(np.mean(res["iters"])), "max_rel_err_vs_x0": float(err)}
         s.close()
+    # P1,2 (Eq. 2, PALM with the eps-ball e-step): the same x0 with Gaussian
+    # noise of standard deviation 0.01 added to b, eps = 1.1 x 0.01 sqrt(m)
+    g = np.random.default_rng(7)
+    sigma = 0.01
+    eps = 1.1 * sigma * np.sqrt(u["m"])
+    Bn = np.asfortranarray(A @ X0 + sigma * g.standard_normal((u["m"], u["count"]))).astype(np.float32)
+    Bn_d = torch.from_numpy(np.ascontiguousarray(Bn.T)).cuda().t()
+    s = l1.Solver(A, mode=l1.P1_2, solver=l1.PALM, epsilon=eps, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        s.solve(Bn_d, u["tol"], u["max_iter"])
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    conv = 0
+    for _ in range(args.steps):
+        x, _, res = s.solve(Bn_d, u["tol"], u["max_iter"])
+        conv += int(np.sum(res["status"] == l1.CONVERGED))
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    xh = x.cpu().numpy()
+    err = max(np.linalg.norm(xh[:, j] - X0[:, j]) / np.linalg.norm(X0[:, j]) for j in range(u["count"]))
+    out["PALM_P1_2"] = {"solves_per_s": conv / (ms / 1e3), "ms_per_batch": ms / args.steps,
+                        "mean_iters": float(np.mean(res["iters"])), "max_rel_err_vs_x0": float(err),
+                        "epsilon": float(eps), "max_resid_over_eps": float(np.max(res["resid"]) / eps)}
+    s.close()
     line = {"metric": "P1 solves/sec (exact recovery, 20 instances per batch)",
             "value": out["DALM"]["solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
