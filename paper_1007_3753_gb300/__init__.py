@@ -411,13 +411,6 @@ def unrolled_palm(A, b, K: int, J: int = 10, ckpt_every: int = 20, xi: float = 0
     return x.reshape(-1) if squeeze else x
 
 
-def bf16_round(a: np.ndarray) -> np.ndarray:
-    """FP32 -> nearest BF16 (ties to even), returned as FP32 (host helper for tests)."""
-    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).copy()
-    u = (u + np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))) & np.uint32(0xFFFF0000)
-    return u.view(np.float32).reshape(np.shape(a))
-
-
 def results_to_dict(res) -> dict:
     """Column arrays of an l1_result array."""
     out = {}

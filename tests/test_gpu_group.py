@@ -48,7 +48,9 @@ def test_group_trajectory_matches_oracle(l1, bf16):
     lam, steps = 5e-3, 300
     As = [p["A"] for p in inst]
     if bf16:  # the oracle solves the problem the BF16 dictionaries define
-        As = [l1.bf16_round(a).astype(np.float64) for a in As]
+        # (torch's host conversion: round to nearest even)
+        As = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+              .to(torch.float32).numpy().astype(np.float64) for a in As]
     L = 1.01 * max(np.linalg.norm(a, 2) ** 2 for a in As)
     b = np.concatenate([p["b"] for p in inst]).astype(np.float32)
     g = l1.Group([p["A"] for p in inst], ms, ns, lam, lipschitz=L,
