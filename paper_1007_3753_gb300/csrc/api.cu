@@ -31,8 +31,21 @@ int dev_alloc(Handle* h, void** p, size_t bytes) {
         return L1_ERR_CUDA;
     }
     h->allocations.push_back(*p);
+    h->allocation_bytes.push_back(bytes);
     h->device_bytes += (int64_t)bytes;
     return L1_OK;
+}
+
+void dev_free(Handle* h, void* p) {
+    if (!p) return;
+    cudaFree(p);
+    for (size_t i = 0; i < h->allocations.size(); ++i) {
+        if (h->allocations[i] != p) continue;
+        h->device_bytes -= (int64_t)h->allocation_bytes[i];
+        h->allocations.erase(h->allocations.begin() + (std::ptrdiff_t)i);
+        h->allocation_bytes.erase(h->allocation_bytes.begin() + (std::ptrdiff_t)i);
+        break;
+    }
 }
 
 static void free_all(Handle* h) {
@@ -45,6 +58,7 @@ static void free_all(Handle* h) {
     }
     for (void* p : h->allocations) cudaFree(p);
     h->allocations.clear();
+    h->allocation_bytes.clear();
     if (h->ws.h_count) cudaFreeHost(h->ws.h_count);
     h->ws = Workspace{};
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);

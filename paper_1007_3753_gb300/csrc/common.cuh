@@ -149,7 +149,8 @@ struct Handle {
     int64_t launches = 0;
     std::vector<int32_t> class_offsets;  // host copy
     Workspace ws;
-    std::vector<void*> allocations;
+    std::vector<void*> allocations;     // device buffers owned by the handle
+    std::vector<size_t> allocation_bytes;  // their sizes, same order
     // unrolled PALM and its tape (differentiation), see unroll.cu
     bool has_tape = false;
     struct UnrollState* ur = nullptr;
@@ -167,6 +168,8 @@ struct Handle {
 };
 
 int dev_alloc(Handle* h, void** p, size_t bytes);
+// frees a buffer from dev_alloc and takes it off the handle's books
+void dev_free(Handle* h, void* p);
 template <class T>
 inline int dev_alloc_t(Handle* h, T** p, size_t count) {
     return dev_alloc(h, reinterpret_cast<void**>(p), count * sizeof(T));

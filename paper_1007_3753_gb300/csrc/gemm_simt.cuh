@@ -527,7 +527,9 @@ int launch_sweep(Handle* h, int M, int N, int K, const TA* Aop, int64_t lda, con
     if (S > 1) {
         const size_t need = (size_t)S * M * ldw;
         if (need > h->splitk_floats) {
-            // grows once to the largest narrow sweep this handle has seen
+            // grows once to the largest narrow sweep this handle has seen; the
+            // old scratch stays allocated until the handle is destroyed, since
+            // graphs captured earlier may still point at it
             if (h->splitk) cudaStreamSynchronize(s);
             float* p = nullptr;
             if (dev_alloc_t(h, &p, need) != L1_OK) {

@@ -248,12 +248,7 @@ static int ensure_workspace(Handle* h, int N) {
     old.insert(old.end(), {w.R, w.hB, w.hWx, w.hWe, w.hY, w.hUx, w.hUe, w.hcoli, w.hcold, w.hcolf, w.part, w.newpos,
                            w.count, w.resid2, w.classl1, w.class_off, w.Up[0], w.Up[1], w.Rp[0], w.Rp[1],
                            w.Rp[2], w.Yp[0], w.Yp[1], w.Ylo});
-    for (void* p : old) {
-        if (!p) continue;
-        cudaFree(p);
-        auto it = std::find(h->allocations.begin(), h->allocations.end(), p);
-        if (it != h->allocations.end()) h->allocations.erase(it);
-    }
+    for (void* p : old) dev_free(h, p);
     if (w.h_count) cudaFreeHost(w.h_count);
     w = Workspace{};
     graph_cache_clear(h);  // the captured launches point into the old buffers
@@ -299,6 +294,10 @@ static int ensure_workspace(Handle* h, int N) {
         // sized now so that no sweep allocates while a chunk is captured
         const size_t need = splitk_need(h, N);
         if (need > h->splitk_floats) {
+            // the graphs that could point at the old scratch are gone (above)
+            dev_free(h, h->splitk);
+            h->splitk = nullptr;
+            h->splitk_floats = 0;
             L1_TRY(dev_alloc_t(h, &h->splitk, need));
             h->splitk_floats = need;
         }

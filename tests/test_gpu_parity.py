@@ -231,6 +231,12 @@ def test_edge_cases(l1):
     Bb = np.tile(p["B"], (1, 12))
     x2, _, res2 = s.solve(_dev(Bb), tol=1e-6, max_iter=50)
     assert _rel(x2.cpu().numpy()[:, 0], x[:, 0]) <= 1e-6
+    # the old workspace is released: a handle that grew to this width holds
+    # as much device memory as one that started there
+    s2 = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM)
+    s2.solve(_dev(Bb), tol=1e-6, max_iter=50)
+    assert s.info()["device_bytes"] == s2.info()["device_bytes"]
+    s2.close()
     s.close()
 
 
