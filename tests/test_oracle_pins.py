@@ -218,6 +218,19 @@ def test_fista_qp_matches_lasso_enumeration_and_kkt():
         assert np.max(np.abs(c[supp] - lam * np.sign(x[supp])), initial=0) <= 1e-7 * lam
 
 
+def test_p12_ball_containing_b_gives_zero():
+    """(P1,2) with eps >= ||b||: x = 0 is feasible, so it is the minimiser of
+    ||x||_1 (Eq. 2)."""
+    g = np.random.default_rng(9)
+    A = g.standard_normal((20, 40))
+    A = np.asfortranarray(A / np.linalg.norm(A, axis=0))
+    b = g.standard_normal(20)
+    x, e, _, st = oracle.palm(A, b, mode=oracle.MODE_P12, tol=1e-12, epsilon=1.01 * np.linalg.norm(b),
+                              max_outer=1000)
+    assert st["converged"] and np.all(x == 0.0)
+    assert np.linalg.norm(b - A @ x) <= 1.01 * np.linalg.norm(b)
+
+
 def test_p12_kkt_and_lasso_equivalence():
     """(P1,2) via reading R10: ||b - Ax|| = eps at the optimum, and x solves
     (QP_lambda) with lambda = ||A^T r||_inf (the KKT multiplier)."""
@@ -395,6 +408,37 @@ def test_dalm_rejects_singular_aat():
 
 
 # -------------------------------------------------------------- invariances
+
+def test_limits_do_not_depend_on_beta_or_xi():
+    """The penalty parameters set the path, not the limit: Algorithm 2
+    converges to the optimum for every beta > 0 (§V-B), Algorithm 1 for every
+    fixed xi > 0 (§V-A), which is why readings R2 and R3 cannot change an
+    answer.  Fixed iteration counts (tol = 0): with a large beta the primal w
+    stalls for a few iterations while y grows, and the relative-change rule
+    of §VI-C would stop there."""
+    for seed in (21, 22):
+        p = synthetic.p1_instance(40, 80, 4, seed=seed)
+        A, b, x0 = p["A"], p["b"], p["x0"]
+        beta0 = np.abs(b).sum() / A.shape[0]
+        for f in (0.1, 1.0, 10.0):
+            w, _, _ = oracle.dalm(A, b, cab=False, beta=f * beta0, tol=0.0, max_iter=20000)
+            assert np.linalg.norm(w - x0) <= 1e-12 * np.linalg.norm(x0), (seed, f)
+        cab = synthetic.cab_problem(32, 3, 4, 1, seed=seed)
+        A, b = cab["A"], cab["B"][:, 0]
+        beta0 = np.abs(b).sum() / A.shape[0]
+        ref = oracle.dalm(A, b, cab=True, tol=0.0, max_iter=100000)[0]
+        for f in (0.3, 3.0):
+            w = oracle.dalm(A, b, cab=True, beta=f * beta0, tol=0.0, max_iter=100000)[0]
+            assert np.linalg.norm(w - ref) <= 1e-7 * np.linalg.norm(ref), (seed, f)
+    for seed in range(3):
+        A, b = _tiny(100 + seed, 3, 3)
+        xi0 = 2.0 * A.shape[0] / np.abs(b).sum()
+        sols = []
+        for f in (1.0, 4.0):
+            x, e, _, _ = oracle.palm(A, b, mode=oracle.MODE_CAB, tol=0.0, max_outer=4000, xi0=f * xi0)
+            sols.append(np.concatenate([x, e]))
+        assert np.linalg.norm(sols[0] - sols[1]) <= 1e-9 * np.linalg.norm(sols[1]), seed
+
 
 def test_invariances():
     p = synthetic.p1_instance(40, 80, 4, seed=21)
