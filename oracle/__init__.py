@@ -12,8 +12,12 @@ ambiguous passages (R1-R11) are listed at the top of ``l1_oracle.c``.
 Parity pins (tests/test_oracle_pins.py) tie each function to something other
 than itself: brute-force LP vertex enumeration and HiGHS on the LP of Eq. 10,
 brute-force lasso enumeration, KKT / subgradient certificates (Eq. 11),
-exact recovery (§VI-A), closed forms, invariances, and central finite
-differences plus the adjoint identity for the unrolled gradient.
+exact recovery (§VI-A), closed forms, invariances (including the independence
+of the limits from beta and xi), FISTA's O(1/k^2) rate and the potential
+function of its proof (§IV-A), hand-computed classification fixtures, and
+central finite differences plus the adjoint identity for the unrolled
+gradient.  tests/test_oracle_mutants.py plants one mistake at a time in
+l1_oracle.c and checks that some pin fails on each.
 """
 from __future__ import annotations
 
