@@ -279,6 +279,13 @@ def test_closed_forms():
     lam = 0.4
     xq, _ = oracle.fista_qp(I5, b, lam, tol=1e-15)
     assert np.allclose(xq, np.sign(b) * np.maximum(np.abs(b) - lam, 0), atol=1e-13)
+    # a rotation Q: 1/2||b - Q x||^2 = 1/2||Q^T b - x||^2, so x* = soft(Q^T b, lam)
+    Q, _ = np.linalg.qr(g.standard_normal((7, 7)))
+    Q = np.asfortranarray(Q)
+    bq = g.standard_normal(7)
+    xq, _ = oracle.fista_qp(Q, bq, lam, tol=1e-15)
+    c = Q.T @ bq
+    assert np.allclose(xq, np.sign(c) * np.maximum(np.abs(c) - lam, 0), atol=1e-12)
     A, bb = _tiny(9, 6, 12)
     xz, st = oracle.fista_qp(A, bb, 1.01 * np.max(np.abs(A.T @ bb)), tol=1e-12)
     assert np.all(xz == 0.0)
