@@ -74,7 +74,8 @@ typedef enum {
 } l1_precision;
 
 typedef enum {
-    L1_ENGINE_AUTO = 0,  /* pick per shape */
+    L1_ENGINE_AUTO = 0,  /* currently the same as L1_ENGINE_SIMT (the faster at
+                          * every measured shape) */
     L1_ENGINE_SIMT = 1,  /* CUDA-core FP32 kernels (GEMV for N <= 8, tiled GEMM above) */
     L1_ENGINE_TC = 2     /* tcgen05 tensor-core sweeps (batched right-hand sides) */
 } l1_engine;
