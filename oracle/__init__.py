@@ -95,7 +95,7 @@ def lib() -> C.CDLL:
                                    C.POINTER(Stats)]
             L.orc_dalm.restype = C.c_int
             L.orc_dalm.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_double,
-                                   C.c_int, dp, dp, C.POINTER(Stats)]
+                                   C.c_int, C.c_int, dp, dp, C.POINTER(Stats)]
             L.orc_classify.restype = C.c_int
             L.orc_classify.argtypes = [dp, C.c_int, C.c_int, ip, C.c_int, dp, dp, dp, dp, dp,
                                        ip, ip]
@@ -169,8 +169,10 @@ def palm(A, b, mode: int = MODE_CAB, tol: float = 1e-10, max_outer: int = 10000,
 
 
 def dalm(A, b, cab: bool = True, beta: float = 0.0, tol: float = 1e-10,
-         max_iter: int = 100000):
-    """Dual ALM, Algorithm 2 (§V-B) with reading R1.
+         max_iter: int = 100000, cg_steps: int = 0):
+    """Dual ALM, Algorithm 2 (§V-B) with reading R1.  cg_steps > 0 replaces
+    the exact y-step by that many conjugate-gradient steps from the previous
+    y (the inexact variant §V-B mentions).
 
     Returns (w, y, stats); w = [x; e] for CAB, w = x for P1."""
     A = _f64(A, True)
@@ -179,8 +181,8 @@ def dalm(A, b, cab: bool = True, beta: float = 0.0, tol: float = 1e-10,
     w = np.zeros(n + m if cab else n)
     y = np.zeros(m)
     st = Stats()
-    _check(lib().orc_dalm(_p(A), m, n, int(bool(cab)), _p(b), beta, tol, max_iter, _p(w), _p(y),
-                          C.byref(st)), "dalm")
+    _check(lib().orc_dalm(_p(A), m, n, int(bool(cab)), _p(b), beta, tol, max_iter, int(cg_steps), _p(w),
+                          _p(y), C.byref(st)), "dalm")
     return w, y, st.as_dict()
 
 

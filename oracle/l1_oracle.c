@@ -369,33 +369,61 @@ static void b_tvec(const double* A, int m, int n, int cab, const double* y, doub
     if (cab) for (int i = 0; i < m; ++i) out[n + i] = y[i];
 }
 
+/* cg_steps conjugate-gradient steps on (B B^T) y = rhs, starting from the
+ * y passed in (the previous iterate), with B B^T applied as B (B^T p); the
+ * inexact alternative to the exact y-step that §V-B mentions (one step
+ * there).  r, p, q have length m, t length n (+ m for CAB). */
+static void cg_ystep(const double* A, int m, int n, int cab, const double* rhs, int cg_steps,
+                     double* y, double* r, double* p, double* q, double* t) {
+    b_tvec(A, m, n, cab, y, t);
+    b_vec(A, m, n, cab, t, q);
+    for (int i = 0; i < m; ++i) { r[i] = rhs[i] - q[i]; p[i] = r[i]; }
+    double rr = dot(r, r, m);
+    for (int s = 0; s < cg_steps && rr > 0.0; ++s) {
+        b_tvec(A, m, n, cab, p, t);
+        b_vec(A, m, n, cab, t, q);
+        const double pq = dot(p, q, m);
+        if (!(pq > 0.0)) break;
+        const double alpha = rr / pq;
+        for (int i = 0; i < m; ++i) { y[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        const double rr_next = dot(r, r, m);
+        const double gamma = rr_next / rr;
+        for (int i = 0; i < m; ++i) p[i] = r[i] + gamma * p[i];
+        rr = rr_next;
+    }
+}
+
 /* Dual ALM, Algorithm 2 (§V-B) with reading R1:
  *   z_{k+1} = P_[-1,1](B^T y_k + w_k / beta)                    (Eq. 38)
  *   y_{k+1} = (B B^T)^{-1} (B z_{k+1} - (B w_k - b) / beta)     (Eq. 39)
  *   w_{k+1} = w_k - beta (z_{k+1} - B^T y_{k+1}),
- * from w_1 = 0, y_1 = 0.  B B^T = A A^T (+ I for CAB) is factored once by
- * Cholesky; P1 with singular A A^T returns ORC_ERR_NOT_SPD (§V-B assumes
- * A A^T invertible).  w has length n (+ m for CAB): x = w[0:n], e = w[n:]. */
+ * from w_1 = 0, y_1 = 0.  With cg_steps = 0 the y-step is exact: B B^T =
+ * A A^T (+ I for CAB) is factored once by Cholesky, and P1 with singular
+ * A A^T returns ORC_ERR_NOT_SPD (§V-B assumes A A^T invertible).  With
+ * cg_steps > 0 it takes that many conjugate-gradient steps from y_k
+ * instead (cg_ystep).  w has length n (+ m for CAB): x = w[0:n], e = w[n:]. */
 int orc_dalm(const double* A, int m, int n, int cab, const double* b, double beta,
-             double tol, int max_iter, double* w, double* y, orc_stats* st) {
-    if (!A || !b || !w || !y || m <= 0 || n <= 0) return ORC_ERR_ARG;
+             double tol, int max_iter, int cg_steps, double* w, double* y, orc_stats* st) {
+    if (!A || !b || !w || !y || m <= 0 || n <= 0 || cg_steps < 0) return ORC_ERR_ARG;
     const int nb = cab ? n + m : n;
-    double* G = (double*)zalloc((size_t)m * m);
+    double* G = (double*)zalloc(cg_steps ? 4 * (size_t)m : (size_t)m * m);
     double* z = (double*)zalloc(nb);
     double* v = (double*)zalloc(nb);
     double* bty = (double*)zalloc(nb);
     double* rhs = (double*)zalloc(m);
     if (!G || !z || !v || !bty || !rhs) { free(G); free(z); free(v); free(bty); free(rhs); return ORC_ERR_NOMEM; }
-    /* G = A A^T (+ I) */
-    for (int i = 0; i < m; ++i)
-        for (int k = 0; k < m; ++k) {
-            double s = 0.0;
-            for (int j = 0; j < n; ++j) s += A[i + (size_t)j * m] * A[k + (size_t)j * m];
-            G[i + (size_t)k * m] = s + ((cab && i == k) ? 1.0 : 0.0);
+    /* G = A A^T (+ I) for the exact y-step; CG needs four m-vectors instead */
+    if (cg_steps == 0) {
+        for (int i = 0; i < m; ++i)
+            for (int k = 0; k < m; ++k) {
+                double s = 0.0;
+                for (int j = 0; j < n; ++j) s += A[i + (size_t)j * m] * A[k + (size_t)j * m];
+                G[i + (size_t)k * m] = s + ((cab && i == k) ? 1.0 : 0.0);
+            }
+        if (cholesky_lower(G, m) != ORC_OK) {
+            free(G); free(z); free(v); free(bty); free(rhs);
+            return ORC_ERR_NOT_SPD;
         }
-    if (cholesky_lower(G, m) != ORC_OK) {
-        free(G); free(z); free(v); free(bty); free(rhs);
-        return ORC_ERR_NOT_SPD;
     }
     if (!(beta > 0.0)) { const double b1 = nrm1(b, m); beta = b1 > 0.0 ? b1 / m : 1.0; }
     for (int j = 0; j < nb; ++j) { w[j] = 0.0; bty[j] = 0.0; }
@@ -408,7 +436,8 @@ int orc_dalm(const double* A, int m, int n, int cab, const double* b, double bet
         for (int j = 0; j < nb; ++j) v[j] = z[j] - w[j] / beta;
         b_vec(A, m, n, cab, v, rhs);
         for (int i = 0; i < m; ++i) rhs[i] += b[i] / beta;
-        cholesky_solve(G, m, rhs, y);
+        if (cg_steps == 0) cholesky_solve(G, m, rhs, y);
+        else cg_ystep(A, m, n, cab, rhs, cg_steps, y, G, G + m, G + 2 * (size_t)m, v);
         b_tvec(A, m, n, cab, y, bty);
         double d2 = 0.0, base2 = 0.0;
         for (int j = 0; j < nb; ++j) {

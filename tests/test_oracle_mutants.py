@@ -109,6 +109,13 @@ MUTANTS = [
      "s -= G[i + (size_t)k * m] * G[i + (size_t)k * m];"),
     ("cholesky_solve_transposed", "back substitution with R^T",
      "s -= R[k + (size_t)i * m] * y[k];", "s -= R[i + (size_t)k * m] * y[k];"),
+    ("cg_step_length_inverted", "CG y-step of §V-B: alpha = r^T r / p^T B B^T p",
+     "const double alpha = rr / pq;", "const double alpha = pq / rr;"),
+    ("cg_residual_sign", "CG y-step of §V-B: residual update",
+     "r[i] -= alpha * q[i]; }", "r[i] += alpha * q[i]; }"),
+    ("cg_no_conjugation", "CG y-step of §V-B: conjugate direction",
+     "for (int i = 0; i < m; ++i) p[i] = r[i] + gamma * p[i];",
+     "for (int i = 0; i < m; ++i) p[i] = r[i];"),
     ("cab_operator_sign", "R1 B = [A I]",
      "if (cab) for (int i = 0; i < m; ++i) out[i] += v[n + i];",
      "if (cab) for (int i = 0; i < m; ++i) out[i] -= v[n + i];"),

@@ -405,6 +405,48 @@ def test_lipschitz_is_spectral_norm_squared():
     assert abs(L / 1.01 - np.linalg.norm(cab["A"], 2) ** 2) <= 1e-8 * L
 
 
+# ------------------------------------------- DALM with a CG y-step (§V-B)
+
+def test_dalm_cg_with_m_steps_is_the_exact_y_step():
+    """m conjugate-gradient steps solve the m x m SPD system of Eq. 39
+    exactly (finite termination of CG), so the iteration is the exact one
+    step for step: the same iterates after a fixed number of iterations."""
+    for seed in range(4):
+        A, b = _tiny(seed, 3, 6)
+        for cab in (False, True):
+            w0, y0, _ = oracle.dalm(A, b, cab=cab, tol=0.0, max_iter=400)
+            w1, y1, _ = oracle.dalm(A, b, cab=cab, tol=0.0, max_iter=400, cg_steps=3)
+            assert np.linalg.norm(w1 - w0) <= 1e-10 * np.linalg.norm(w0), (seed, cab)
+            assert np.linalg.norm(y1 - y0) <= 1e-10 * np.linalg.norm(y0), (seed, cab)
+    p = synthetic.p1_instance(20, 40, 3, seed=5)
+    w0, _, _ = oracle.dalm(p["A"], p["b"], cab=False, tol=0.0, max_iter=60)
+    w1, _, _ = oracle.dalm(p["A"], p["b"], cab=False, tol=0.0, max_iter=60, cg_steps=20)
+    assert np.linalg.norm(w1 - w0) <= 1e-9 * np.linalg.norm(w0)
+
+
+def test_dalm_one_cg_step_recovers_gaussian_but_not_face_like():
+    """§V-B: one CG step per iteration in place of the exact y-step works on
+    random Gaussian dictionaries and fails on face-like ones.  Gaussian: the
+    §VI-A instances are recovered exactly.  Cross-and-bouquet with the
+    class-subspace dictionary: the iteration stalls far from b = A x + e
+    (the relative-change rule of §VI-C stops it there), while the exact
+    y-step reaches the constraint."""
+    for seed in range(3):
+        p = synthetic.p1_instance(200, 400, 20, seed=seed)
+        w, _, st = oracle.dalm(p["A"], p["b"], cab=False, tol=1e-10, max_iter=20000, cg_steps=1)
+        assert st["converged"]
+        assert np.linalg.norm(w - p["x0"]) <= 1e-7 * np.linalg.norm(p["x0"]), seed
+    pr = synthetic.cab_problem(256, 8, 12, 2, corrupt=0.3, seed=1300)
+    A, B = pr["A"], pr["B"]
+    n = A.shape[1]
+    for j in range(2):
+        b = B[:, j]
+        w, _, _ = oracle.dalm(A, b, cab=True, tol=1e-6, max_iter=200000, cg_steps=1)
+        assert np.linalg.norm(b - A @ w[:n] - w[n:]) >= 0.1 * np.linalg.norm(b)
+        w, _, _ = oracle.dalm(A, b, cab=True, tol=1e-6, max_iter=200000)
+        assert np.linalg.norm(b - A @ w[:n] - w[n:]) <= 1e-5 * np.linalg.norm(b)
+
+
 def test_dalm_rejects_singular_aat():
     A, b = _tiny(4, 6, 12)
     A2 = np.asfortranarray(np.vstack([A, A[:1]]))  # duplicated row: A A^T singular
