@@ -173,17 +173,20 @@ def _run_pins(lib_path: str) -> tuple[int, str]:
 
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
-    src = open(SRC).read()
+    with open(SRC) as f:
+        src = f.read()
     d = tmp_path_factory.mktemp("mutants")
     jobs = {}
-    ctl = os.path.join(d, "control.c")
-    open(ctl, "w").write(src)
-    jobs["control"] = oracle.compile_source(ctl, os.path.join(d, "control.so"))
+
+    def compile_variant(name, text):
+        path = os.path.join(d, name + ".c")
+        with open(path, "w") as f:
+            f.write(text)
+        return oracle.compile_source(path, os.path.join(d, name + ".so"))
+    jobs["control"] = compile_variant("control", src)
     for mid, _, old, new in MUTANTS:
         assert src.count(old) == 1, f"{mid}: the text to mutate must occur exactly once"
-        path = os.path.join(d, mid + ".c")
-        open(path, "w").write(src.replace(old, new))
-        jobs[mid] = oracle.compile_source(path, os.path.join(d, mid + ".so"))
+        jobs[mid] = compile_variant(mid, src.replace(old, new))
     with cf.ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
         futs = {mid: ex.submit(_run_pins, so) for mid, so in jobs.items()}
         return {mid: f.result() for mid, f in futs.items()}
