@@ -90,6 +90,61 @@ def test_host_side_argument_checks(lib):
     assert lib.l1_status_string(l1.ERR_UNSUPPORTED) == b"L1_ERR_UNSUPPORTED"
 
 
+def test_refused_combinations_before_any_cuda_call(lib):
+    """Requests the library does not implement return L1_ERR_UNSUPPORTED and
+    malformed ones L1_ERR_INVALID_ARG, from the argument checks alone."""
+    A = np.ones((4, 8), dtype=np.float32, order="F")
+    h = C.c_void_p()
+
+    def setup(mode, **kw):
+        o = l1.Options()
+        lib.l1_options_init(C.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        rc = lib.l1_setup(A.ctypes.data, 4, 8, 4, mode, C.byref(o), C.byref(h))
+        assert not h.value
+        return rc
+    U, I = l1.ERR_UNSUPPORTED, l1.ERR_INVALID_ARG
+    assert setup(l1.P1_2, solver=l1.DALM, epsilon=0.1) == U      # R10 is a PALM
+    assert setup(l1.P1_2, solver=l1.PALM, epsilon=0.0) == I      # no radius
+    for kw in (dict(solver=l1.PALM), dict(engine=l1.ENGINE_TC), dict(unroll_K=5, solver=l1.PALM)):
+        assert setup(l1.CAB, precision=l1.A_BF16, **kw) == U, kw  # low precision: batched DALM only
+    assert setup(l1.QP_LAMBDA, precision=l1.A_FP8E4M3, lambda_=0.1) == U
+    assert setup(l1.CAB, solver=l1.PALM, engine=l1.ENGINE_TC) == U
+    assert setup(l1.QP_LAMBDA, engine=l1.ENGINE_TC, lambda_=0.1) == U
+    assert setup(l1.CAB, solver=l1.PALM, unroll_K=5) == U       # unrolled PALM is P1
+    assert setup(l1.P1, solver=l1.DALM, unroll_K=5) == U
+    assert setup(l1.P1, solver=l1.PALM, unroll_K=-1) == I
+    assert setup(l1.P1, solver=7) == I
+    assert setup(l1.P1, precision=9) == I
+    assert setup(l1.P1, engine=9) == I
+    flat = np.array([0, 3, 3, 8], dtype=np.int32)  # an empty class
+    assert setup(l1.CAB, class_count=3, class_offsets=flat.ctypes.data_as(C.POINTER(C.c_int32))) == I
+    # groups: (QP_lambda) only, FP32 or BF16, positive sizes
+    ms = np.array([4, 6], dtype=np.int64)
+    ns = np.array([8, 12], dtype=np.int64)
+    o = l1.Options()
+    lib.l1_options_init(C.byref(o))
+    o.lambda_ = 0.1
+    P64 = C.POINTER(C.c_int64)
+    args = (ms.ctypes.data_as(P64), ns.ctypes.data_as(P64))
+    assert lib.l1_setup_group(None, *args, 2, l1.CAB, C.byref(o), C.byref(h)) == I
+    assert lib.l1_setup_group(None, *args, 0, l1.QP_LAMBDA, C.byref(o), C.byref(h)) == I
+    o.precision = l1.A_FP8E4M3
+    assert lib.l1_setup_group(None, *args, 2, l1.QP_LAMBDA, C.byref(o), C.byref(h)) == U
+    o.precision = l1.A_FP32
+    ms[1] = 0
+    assert lib.l1_setup_group(None, *args, 2, l1.QP_LAMBDA, C.byref(o), C.byref(h)) == I
+    o.lambda_ = 0.0
+    assert lib.l1_setup_group(None, *args, 2, l1.QP_LAMBDA, C.byref(o), C.byref(h)) == I
+    assert not h.value
+    # the allocation-free entry point checks its arguments and its size limit first
+    rho = C.c_double(0.0)
+    assert lib.l1_lipschitz_static(None, 4, 8, 4, 10, 1e-6, None, C.byref(rho)) == I
+    assert lib.l1_lipschitz_static(A.ctypes.data, 4, 8, 3, 10, 1e-6, None, C.byref(rho)) == I
+    assert lib.l1_lipschitz_static(A.ctypes.data, 1 << 20, 8, 1 << 20, 10, 1e-6, None, C.byref(rho)) == I
+
+
 def test_product_path_has_no_cpu_fallback():
     """The package never imports the oracle and has no host compute path."""
     pkg = os.path.join(ROOT, "paper_1007_3753_gb300")
