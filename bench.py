@@ -401,6 +401,7 @@ def bench_ours(args, rank, world):
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "ms_per_step_median": statistics.median(step_ms),  # rank 0's own steps
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else f"{args.precision} A, f32 arithmetic",
             "data": "synthetic",
