@@ -47,6 +47,9 @@
  *   R11 Unrolled PALM (differentiation): K inner FISTA steps in total, a
  *       multiplier update after every J inner steps, no early exit; xi and L
  *       are constants (no gradient flows through them).
+ *   R15 The inexact y-step of §V-B ("one step of conjugate gradient in the
+ *       y direction"): CG on (B B^T) y = B z - (B w - b)/beta started from
+ *       the previous y; cg_steps = 1 is the paper's variant.
  */
 #include <math.h>
 #include <stdlib.h>
