@@ -31,7 +31,7 @@
  *   R4  L in Algorithm 1 is the Lipschitz constant ||A||_2^2 of the smooth
  *       term's gradient (§IV-A), estimated by power iteration on A^T A and
  *       multiplied by a safety factor (1.01 by default).
- *   R5  Inner "while not converged": stop when ||w_{l+1} - w_l|| <=
+ *   R5  Inner loop (Algorithm 1 leaves its test open): stop when ||w_{l+1} - w_l|| <=
  *       inner_tol * ||w_l|| (with ||w_l|| = 0 only an exact zero step
  *       stops), or after inner_max steps.
  *   R6  Outer stopping rule: ||w_{k+1} - w_k|| / ||w_k|| < tol (§VI-C), where
@@ -47,9 +47,9 @@
  *   R11 Unrolled PALM (differentiation): K inner FISTA steps in total, a
  *       multiplier update after every J inner steps, no early exit; xi and L
  *       are constants (no gradient flows through them).
- *   R15 The inexact y-step of §V-B ("one step of conjugate gradient in the
- *       y direction"): CG on (B B^T) y = B z - (B w - b)/beta started from
- *       the previous y; cg_steps = 1 is the paper's variant.
+ *   R15 The inexact y-step §V-B mentions (a single conjugate-gradient step
+ *       instead of the exact solve): CG on (B B^T) y = B z - (B w - b)/beta
+ *       started from the previous y; cg_steps = 1 is that variant.
  */
 #include <math.h>
 #include <stdlib.h>
