@@ -132,6 +132,9 @@ MUTANTS = [
     # unrolled PALM and its reverse sweep, reading R11
     ("unrolled_theta_unscaled", "R11 multiplier update",
      "theta[i] += xi * (b[i] - r[i]);", "theta[i] += (b[i] - r[i]);"),
+    ("unrolled_c_sign", "R11 inner target b + theta/xi",
+     "for (int i = 0; i < m; ++i) c[i] = b[i] + theta[i] / xi;",
+     "for (int i = 0; i < m; ++i) c[i] = b[i] - theta[i] / xi;"),
     ("unrolled_momentum_index", "R11 forward FISTA momentum",
      "            const double mu = (t - 1.0) / t_new;\n            Mu[s] = mu;",
      "            const double mu = t / t_new;\n            Mu[s] = mu;"),

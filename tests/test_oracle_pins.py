@@ -558,6 +558,20 @@ def _fd(A, b, xi, L, K, J, xt, dA, db, h):
     return (lp - lm) / (2 * h)
 
 
+def test_unrolled_forward_reaches_the_p1_optimum():
+    """The unrolled forward (reading R11) is the method of multipliers of
+    Eq. 33 with J FISTA steps per multiplier update and a fixed xi; run long
+    enough it reaches the solution of (P1), here the planted x0 of exact
+    recovery (§VI-A)."""
+    for seed in (21, 22):
+        p = synthetic.p1_instance(40, 80, 4, seed=seed)
+        A, b, x0 = p["A"], p["b"], p["x0"]
+        xi = 2.0 * A.shape[0] / np.abs(b).sum()
+        x = oracle.unrolled_palm(A, b, xi, oracle.lipschitz(A), 2000, 20, np.zeros(A.shape[1]),
+                                 grad=False)[0]
+        assert np.linalg.norm(x - x0) <= 1e-10 * np.linalg.norm(x0), seed
+
+
 def test_unrolled_gradient_finite_differences():
     """Central differences in FP64 (h = 1e-3, unit-norm directions) on the
     loss 1/2||x_K - x_t||^2.  A direction counts only when the estimates at h
