@@ -96,6 +96,9 @@ def lib() -> C.CDLL:
             L.orc_dalm.restype = C.c_int
             L.orc_dalm.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_double, C.c_double,
                                    C.c_int, C.c_int, dp, dp, C.POINTER(Stats)]
+            L.orc_palm_align.restype = C.c_int
+            L.orc_palm_align.argtypes = [dp, C.c_int, C.c_int, dp, C.c_double, C.c_int, C.c_double,
+                                         dp, dp, dp, C.POINTER(Stats)]
             L.orc_classify.restype = C.c_int
             L.orc_classify.argtypes = [dp, C.c_int, C.c_int, ip, C.c_int, dp, dp, dp, dp, dp,
                                        ip, ip]
@@ -184,6 +187,23 @@ def dalm(A, b, cab: bool = True, beta: float = 0.0, tol: float = 1e-10,
     _check(lib().orc_dalm(_p(A), m, n, int(bool(cab)), _p(b), beta, tol, max_iter, int(cg_steps), _p(w),
                           _p(y), C.byref(st)), "dalm")
     return w, y, st.as_dict()
+
+
+def palm_align(B, b, tol: float = 1e-10, max_outer: int = 100000, xi0: float = 0.0):
+    """The alignment step of §II-B, min ||e||_1 s.t. b = B w + e with w not
+    penalised, by PALM with an exact least-squares w-step (reading R16).
+
+    Returns (w, e, theta, stats)."""
+    B = _f64(B, True)
+    b = _f64(b)
+    m, p = B.shape
+    w = np.zeros(p)
+    e = np.zeros(m)
+    th = np.zeros(m)
+    st = Stats()
+    _check(lib().orc_palm_align(_p(B), m, p, _p(b), tol, max_outer, xi0, _p(w), _p(e), _p(th),
+                                C.byref(st)), "palm_align")
+    return w, e, th, st.as_dict()
 
 
 def classify(A, offsets, b, x, e=None):

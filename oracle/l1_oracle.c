@@ -50,6 +50,9 @@
  *   R15 The inexact y-step §V-B mentions (a single conjugate-gradient step
  *       instead of the exact solve): CG on (B B^T) y = B z - (B w - b)/beta
  *       started from the previous y; cg_steps = 1 is that variant.
+ *   R16 The alignment step of §II-B solved by PALM: Algorithm 1 with the
+ *       x-step replaced by the exact least-squares minimiser over the
+ *       unpenalised w, and xi fixed at 2m/||b||_1.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -460,6 +463,71 @@ int orc_dalm(const double* A, int m, int n, int cab, const double* b, double bet
         st->param = beta;
     }
     free(G); free(z); free(v); free(bty); free(rhs);
+    return ORC_OK;
+}
+
+/* ------------------------------------------- alignment l1 step (§II-B) */
+
+/* The convex step of the face-alignment loop (§II-B, the last displayed
+ * problem there): min ||e||_1 s.t. b = B w + e with B = [A_i, -J_i] tall and
+ * w (coefficients and the transformation update) not penalised.  Reading R16:
+ * Algorithm 1 with its x-step replaced by the exact minimiser of the
+ * augmented Lagrangian over the unpenalised w, a least-squares solve with
+ * B^T B factored once by Cholesky:
+ *   e_{k+1} = shrink(b - B w_k + theta_k/xi, 1/xi)
+ *   w_{k+1} = (B^T B)^{-1} B^T (b - e_{k+1} + theta_k/xi)
+ *   theta_{k+1} = theta_k + xi (b - B w_{k+1} - e_{k+1}),
+ * from w = 0, e = b, theta = 0, xi fixed at 2m/||b||_1 (as for CAB, §V-A)
+ * unless xi0 > 0, stopping on R6 with w = [w; e].  B is m x p column-major;
+ * returns ORC_ERR_NOT_SPD when B^T B is singular. */
+int orc_palm_align(const double* B, int m, int p, const double* b, double tol, int max_outer,
+                   double xi0, double* w, double* e, double* theta, orc_stats* st) {
+    if (!B || !b || !w || !e || !theta || m <= 0 || p <= 0) return ORC_ERR_ARG;
+    double* G = (double*)zalloc((size_t)p * p);
+    double* Bw = (double*)zalloc(m);
+    double* t = (double*)zalloc(m);
+    double* rhs = (double*)zalloc(p);
+    double* w_next = (double*)zalloc(p);
+    double* e_next = (double*)zalloc(m);
+    if (!G || !Bw || !t || !rhs || !w_next || !e_next) {
+        free(G); free(Bw); free(t); free(rhs); free(w_next); free(e_next);
+        return ORC_ERR_NOMEM;
+    }
+    for (int i = 0; i < p; ++i)
+        for (int k = 0; k < p; ++k) G[i + (size_t)k * p] = dot(B + (size_t)i * m, B + (size_t)k * m, m);
+    if (cholesky_lower(G, p) != ORC_OK) {
+        free(G); free(Bw); free(t); free(rhs); free(w_next); free(e_next);
+        return ORC_ERR_NOT_SPD;
+    }
+    const double b1 = nrm1(b, m);
+    const double xi = xi0 > 0.0 ? xi0 : (b1 > 0.0 ? 2.0 * m / b1 : 1.0);
+    for (int j = 0; j < p; ++j) w[j] = 0.0;
+    for (int i = 0; i < m; ++i) { e[i] = b[i]; theta[i] = 0.0; Bw[i] = 0.0; }
+    int k = 0, conv = 0;
+    double rel = INFINITY;
+    for (k = 1; k <= max_outer; ++k) {
+        for (int i = 0; i < m; ++i) e_next[i] = soft(b[i] - Bw[i] + theta[i] / xi, 1.0 / xi);
+        for (int i = 0; i < m; ++i) t[i] = b[i] - e_next[i] + theta[i] / xi;
+        mat_tvec(B, m, p, t, rhs);
+        cholesky_solve(G, p, rhs, w_next);
+        mat_vec(B, m, p, w_next, Bw);
+        for (int i = 0; i < m; ++i) theta[i] += xi * (b[i] - Bw[i] - e_next[i]);
+        double d2 = 0.0, base2 = 0.0;
+        for (int j = 0; j < p; ++j) { const double d = w_next[j] - w[j]; d2 += d * d; base2 += w[j] * w[j]; }
+        for (int i = 0; i < m; ++i) { const double d = e_next[i] - e[i]; d2 += d * d; base2 += e[i] * e[i]; }
+        rel = rel_change(sqrt(d2), sqrt(base2));
+        memcpy(w, w_next, sizeof(double) * p);
+        memcpy(e, e_next, sizeof(double) * m);
+        if (rel < tol) { conv = 1; break; }
+    }
+    if (st) {
+        st->iters = k > max_outer ? max_outer : k;
+        st->inner_total = st->iters;
+        st->converged = conv;
+        st->rel_change = rel;
+        st->param = xi;
+    }
+    free(G); free(Bw); free(t); free(rhs); free(w_next); free(e_next);
     return ORC_OK;
 }
 

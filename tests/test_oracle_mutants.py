@@ -122,6 +122,20 @@ MUTANTS = [
     ("cab_adjoint_dropped", "R1 B^T = [A^T; I]",
      "if (cab) for (int i = 0; i < m; ++i) out[n + i] = y[i];",
      "if (cab) for (int i = 0; i < m; ++i) out[n + i] = 0.0;"),
+    # the alignment step of §II-B, reading R16
+    # (a wrong e threshold alone only rescales ||e||_1, the one term of this
+    # objective, so it leaves the minimiser unchanged: not a mistake a limit
+    # can show)
+    ("align_e_multiplier_sign", "R16 e-step",
+     "e_next[i] = soft(b[i] - Bw[i] + theta[i] / xi, 1.0 / xi);",
+     "e_next[i] = soft(b[i] - Bw[i] - theta[i] / xi, 1.0 / xi);"),
+    ("align_rhs_e_sign", "R16 least-squares target b - e + theta/xi",
+     "t[i] = b[i] - e_next[i] + theta[i] / xi;", "t[i] = b[i] + e_next[i] + theta[i] / xi;"),
+    ("align_theta_no_e", "R16 multiplier update",
+     "theta[i] += xi * (b[i] - Bw[i] - e_next[i]);", "theta[i] += xi * (b[i] - Bw[i]);"),
+    ("align_gram_diagonal", "R16 B^T B",
+     "G[i + (size_t)k * p] = dot(B + (size_t)i * m, B + (size_t)k * m, m);",
+     "G[i + (size_t)k * p] = dot(B + (size_t)i * m, B + (size_t)i * m, m);"),
     # classification, §II-A and Eq. 40
     ("classify_keeps_error", "§II-A residual of b - e",
      "v[i] = b[i] - (e ? e[i] : 0.0);", "v[i] = b[i];"),

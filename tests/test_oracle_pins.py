@@ -514,6 +514,53 @@ def test_invariances():
     assert np.linalg.norm(e2 - 2 * e) <= 1e-9 * np.linalg.norm(e2)
 
 
+# ----------------------------------------------- alignment step (§II-B)
+
+def _lad_instance(seed, m, p, outliers):
+    g = np.random.default_rng(seed)
+    B = np.asfortranarray(g.standard_normal((m, p)))
+    w0 = g.standard_normal(p)
+    e0 = np.zeros(m)
+    e0[g.choice(m, outliers, replace=False)] = 5.0 * g.standard_normal(outliers)
+    return B, w0, B @ w0 + e0
+
+
+def test_alignment_step_matches_the_lp_and_recovers_the_transform():
+    """The convex alignment step of §II-B, min ||e||_1 s.t. b = B w + e with w
+    free, is a linear program (least absolute deviations): HiGHS on
+    [B, I, -I] with w free and e+, e- >= 0 gives the same optimum.  With few
+    gross errors (an occluded block is 10 % of the pixels in §VI-C) the
+    minimiser is the planted w0 exactly.  A fixed number of outer steps
+    (tol = 0): as with the LP pins above, (w, e) can stand still for a few
+    steps while theta catches up, and the relative-change rule of §VI-C would
+    stop there."""
+    from scipy.optimize import linprog
+    for seed, (m, p) in enumerate([(60, 5), (60, 5), (300, 11), (300, 11)]):
+        B, w0, b = _lad_instance(seed, m, p, m // 10)
+        w, e, _, _ = oracle.palm_align(B, b, tol=0.0, max_outer=3000)
+        c = np.concatenate([np.zeros(p), np.ones(2 * m)])
+        lp = linprog(c, A_eq=np.hstack([B, np.eye(m), -np.eye(m)]), b_eq=b,
+                     bounds=[(None, None)] * p + [(0, None)] * (2 * m), method="highs")
+        assert lp.status == 0
+        assert abs(np.abs(e).sum() - lp.fun) <= 1e-8 * lp.fun, seed
+        assert np.linalg.norm(b - B @ w - e) <= 1e-9 * np.linalg.norm(b)
+        assert np.linalg.norm(w - w0) <= 1e-9 * np.linalg.norm(w0), seed
+
+
+def test_alignment_step_invariances_and_rank_check():
+    """b -> b + B v moves the minimiser to w + v with the same e (the
+    constraint absorbs B v); a rank-deficient B is refused (B^T B singular)."""
+    B, w0, b = _lad_instance(7, 80, 6, 8)
+    w, e, _, _ = oracle.palm_align(B, b, tol=0.0, max_outer=3000)
+    v = np.linspace(-1.0, 1.0, 6)
+    w2, e2, _, _ = oracle.palm_align(B, b + B @ v, tol=0.0, max_outer=3000)
+    assert np.linalg.norm(w2 - (w + v)) <= 1e-8 * np.linalg.norm(w + v)
+    assert np.linalg.norm(e2 - e) <= 1e-8 * np.linalg.norm(e)
+    Bd = np.asfortranarray(np.hstack([B, B[:, :1]]))
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.palm_align(Bd, b, tol=1e-10)
+
+
 # ----------------------------------------------------------- classification
 
 @pytest.mark.parametrize("name", ["classify_hand.json", "classify_hand_error.json"])
