@@ -547,6 +547,25 @@ def test_alignment_step_matches_the_lp_and_recovers_the_transform():
         assert np.linalg.norm(w - w0) <= 1e-9 * np.linalg.norm(w0), seed
 
 
+def test_alignment_step_with_one_column_is_the_median():
+    """B = a column of ones: min_w sum |b_i - w| is attained at the median of
+    b (unique for odd m); B = a column c > 0: at a weighted median of b_i/c_i
+    with weights c_i."""
+    g = np.random.default_rng(12)
+    for m in (5, 9, 31):
+        b = g.standard_normal(m)
+        w, _, _, _ = oracle.palm_align(np.ones((m, 1)), b, tol=0.0, max_outer=5000)
+        assert abs(w[0] - np.median(b)) <= 1e-10, m
+    c = 0.5 + g.random(15)
+    b = g.standard_normal(15)
+    r = b / c
+    order = np.argsort(r)
+    cum = np.cumsum(c[order])
+    wmed = r[order][np.searchsorted(cum, 0.5 * cum[-1])]  # generic weights: a unique minimiser
+    w, _, _, _ = oracle.palm_align(c.reshape(-1, 1), b, tol=0.0, max_outer=5000)
+    assert abs(w[0] - wmed) <= 1e-10
+
+
 def test_alignment_step_invariances_and_rank_check():
     """b -> b + B v moves the minimiser to w + v with the same e (the
     constraint absorbs B v); a rank-deficient B is refused (B^T B singular)."""
