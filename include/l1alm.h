@@ -254,24 +254,34 @@ L1_API int l1_backward(l1_handle h, const float* grad_x, int64_t N, float* grad_
  * not call cudaMalloc or cudaFree -- a process whose device memory is owned by
  * its own pool allocator, or a loop that must not stall the device while
  * memory is allocated or freed.
- *   A        device (or managed) memory, m x n, column-major, leading
- *            dimension lda >= m; on the current device; read only.
- *   stream   the work is enqueued there (NULL: the legacy default stream)
- *            and the call returns after synchronising it.
- *   rho_out  host pointer; receives the estimate.
+ *   A          device (or managed) memory, m x n, column-major, leading
+ *              dimension lda >= m; on the current device; read only.
+ *   stream     the work is enqueued there (NULL: the legacy default stream).
+ *              The call copies its state to the host and synchronises this
+ *              stream before it returns, so it must not be called while the
+ *              stream is being captured into a CUDA graph (it returns
+ *              L1_ERR_INVALID_ARG then, before enqueuing anything).
+ *   rho_out    host pointer; receives the estimate.
+ *   status_out nullable host pointer; receives L1_CONVERGED when the stopping
+ *              rule fired, L1_MAX_ITER when max_iter ran out first (rho_out
+ *              then holds the last, unconverged estimate, which is below
+ *              ||A||_2^2; close top singular values make this likely).
+ *   iters_out  nullable host pointer; receives the iterations run.
  * Scratch: one static device array of 1.34 MiB per GPU that loads this
  * library, held until the process exits; hence m <= 8192 and n <= 65536.
  * Larger sizes return L1_ERR_INVALID_ARG with a message in l1_last_error.
  * The first call on a device looks up that array's device address (once,
- * with that device current); make that first call before any stream
- * capture.  Each call initialises the scratch it reads, but every call on a
- * device shares the one array: calls that can overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
+ * with that device current).  Each call initialises the scratch it reads,
+ * but every call on a device shares the one array: calls that can overlap on
+ * the GPU (other streams, other host threads) race and must be serialised by
+ * the caller.
  * Errors: L1_ERR_INVALID_ARG (null pointer, a size <= 0 or above the limits,
- * lda < m, max_iter <= 0, rtol < 0, A not device memory), L1_ERR_CUDA.
+ * lda < m, max_iter <= 0, rtol < 0, A not device memory or on a device other
+ * than the current one, the stream being captured), L1_ERR_CUDA.
  */
 L1_API int l1_lipschitz_static(const float* A, int64_t m, int64_t n, int64_t lda, int32_t max_iter,
-                               double rtol, void* stream, double* rho_out);
+                               double rtol, void* stream, double* rho_out, int32_t* status_out,
+                               int32_t* iters_out);
 
 /* Set the stream later calls enqueue on. */
 L1_API int l1_set_stream(l1_handle h, void* stream);

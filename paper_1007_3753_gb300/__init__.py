@@ -105,7 +105,8 @@ def load() -> C.CDLL:
     L.l1_status_string.restype = C.c_char_p
     L.l1_last_error.argtypes = []
     L.l1_last_error.restype = C.c_char_p
-    L.l1_lipschitz_static.argtypes = [vp, i64, i64, i64, i32, dbl, vp, C.POINTER(dbl)]
+    L.l1_lipschitz_static.argtypes = [vp, i64, i64, i64, i32, dbl, vp, C.POINTER(dbl), C.POINTER(i32),
+                                      C.POINTER(i32)]
     L.l1_lipschitz_static.restype = C.c_int
     _lib = L
     return L
@@ -354,20 +355,38 @@ class Group:
             pass
 
 
-def lipschitz_static(A, max_iter: int = 1000, rtol: float = 1e-6, stream=None) -> float:
+def lipschitz_static(A, max_iter: int = 1000, rtol: float = 1e-6, stream=None,
+                     return_status: bool = False):
     """Power-iteration estimate of ||A||_2^2 without any allocation.
 
     ``A`` is a device-resident m x n FP32 column-major tensor (m <= 8192,
-    n <= 65536).  For callers that may not allocate device memory; every
-    call shares one static scratch array per GPU, so calls that can overlap
-    on the GPU must be serialised.  The first call on a device should come
-    before any stream capture.  A handle's L is 1.01 times this estimate."""
+    n <= 65536) on the current device.  For callers that may not allocate
+    device memory; every call shares one static scratch array per GPU, so
+    calls that can overlap on the GPU must be serialised.  The call
+    synchronises its stream, so it must not run inside a stream capture.  A
+    handle's L is 1.01 times this estimate.  With ``return_status`` the
+    result is ``(rho, converged, iterations)``."""
+    import torch
+    if not isinstance(A, torch.Tensor) or A.dtype != torch.float32:
+        raise TypeError(f"lipschitz_static: A must be a float32 torch tensor, got "
+                        f"{getattr(A, 'dtype', type(A).__name__)}")
+    if not A.is_cuda:
+        raise TypeError("lipschitz_static: A must be a CUDA tensor")
+    if A.dim() != 2:
+        raise ValueError("lipschitz_static: A must be 2-D")
+    if A.device.index is not None and A.device.index != torch.cuda.current_device():
+        raise ValueError(f"lipschitz_static: A is on cuda:{A.device.index} but cuda:"
+                         f"{torch.cuda.current_device()} is current")
     L = load()
     m, n = A.shape
     rho = C.c_double(0.0)
+    status = C.c_int32(-1)
+    iters = C.c_int32(0)
     st = _current_stream() if stream is None else C.c_void_p(stream)
-    _check(L.l1_lipschitz_static(_ptr(A), m, n, _ld(A), max_iter, rtol, st, C.byref(rho)),
-           "l1_lipschitz_static")
+    _check(L.l1_lipschitz_static(_ptr(A), m, n, _ld(A), max_iter, rtol, st, C.byref(rho),
+                                 C.byref(status), C.byref(iters)), "l1_lipschitz_static")
+    if return_status:
+        return rho.value, status.value == CONVERGED, iters.value
     return rho.value
 
 

@@ -189,7 +189,7 @@ int static_scratch(int dev, double** out) {
 extern "C" {
 
 L1_API int l1_lipschitz_static(const float* A, int64_t m, int64_t n, int64_t lda, int32_t max_iter, double rtol,
-                               void* stream, double* rho_out) {
+                               void* stream, double* rho_out, int32_t* status_out, int32_t* iters_out) {
     using namespace l1;
     if (!A || !rho_out || m <= 0 || n <= 0 || lda < m || max_iter <= 0 || !(rtol >= 0.0))
         return L1_ERR_INVALID_ARG;
@@ -205,16 +205,33 @@ L1_API int l1_lipschitz_static(const float* A, int64_t m, int64_t n, int64_t lda
         set_last_error("l1_lipschitz_static: device ordinal out of range");
         return L1_ERR_INVALID_ARG;
     }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        // the call copies the state to pageable host memory and synchronises
+        // its stream, neither of which a stream capture allows
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        L1_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            set_last_error("l1_lipschitz_static: the stream is being captured; the call synchronises it");
+            return L1_ERR_INVALID_ARG;
+        }
+    }
     cudaPointerAttributes attr{};
     L1_CUDA_TRY(cudaPointerGetAttributes(&attr, A));
     if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
         set_last_error("l1_lipschitz_static: A must be device (or managed) memory");
         return L1_ERR_INVALID_ARG;
     }
+    if (attr.type == cudaMemoryTypeDevice && attr.device != dev) {
+        // a pointer into another GPU's memory would be dereferenced as a peer
+        // address by the kernels below; refuse it instead
+        set_last_error("l1_lipschitz_static: A lives on device " + std::to_string(attr.device) +
+                       " but device " + std::to_string(dev) + " is current");
+        return L1_ERR_INVALID_ARG;
+    }
     double* base = nullptr;
     L1_TRY(static_scratch(dev, &base));
 
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int mi = (int)m, ni = (int)n;
     const int cw = (ni + kChunks - 1) / kChunks;
     const int chunks = (ni + cw - 1) / cw;
@@ -241,6 +258,8 @@ L1_API int l1_lipschitz_static(const float* A, int64_t m, int64_t n, int64_t lda
         if (state[3] != 0.0) break;
     }
     *rho_out = state[0];
+    if (status_out) *status_out = state[3] != 0.0 ? L1_CONVERGED : L1_MAX_ITER;
+    if (iters_out) *iters_out = (int32_t)state[2];
     return L1_OK;
 }
 

@@ -140,9 +140,25 @@ def test_refused_combinations_before_any_cuda_call(lib):
     assert not h.value
     # the allocation-free entry point checks its arguments and its size limit first
     rho = C.c_double(0.0)
-    assert lib.l1_lipschitz_static(None, 4, 8, 4, 10, 1e-6, None, C.byref(rho)) == I
-    assert lib.l1_lipschitz_static(A.ctypes.data, 4, 8, 3, 10, 1e-6, None, C.byref(rho)) == I
-    assert lib.l1_lipschitz_static(A.ctypes.data, 1 << 20, 8, 1 << 20, 10, 1e-6, None, C.byref(rho)) == I
+    st, it = C.c_int32(-1), C.c_int32(-1)
+    args = (None, C.byref(rho), C.byref(st), C.byref(it))
+    assert lib.l1_lipschitz_static(None, 4, 8, 4, 10, 1e-6, *args) == I
+    assert lib.l1_lipschitz_static(A.ctypes.data, 4, 8, 3, 10, 1e-6, *args) == I
+    assert lib.l1_lipschitz_static(A.ctypes.data, 1 << 20, 8, 1 << 20, 10, 1e-6, *args) == I
+    assert (st.value, it.value) == (-1, -1)  # nothing written on a refused call
+
+
+def test_static_wrapper_refuses_other_dtypes_before_any_launch(lib):
+    """lipschitz_static reads FP32: a BF16 (or FP64, or host) tensor is refused
+    in Python before the library is called, so no kernel reads past a buffer."""
+    torch = pytest.importorskip("torch")
+    for dt in (torch.bfloat16, torch.float16, torch.float64):
+        with pytest.raises(TypeError):
+            l1.lipschitz_static(torch.zeros((8, 4), dtype=dt).t())
+    with pytest.raises(TypeError):
+        l1.lipschitz_static(torch.zeros((8, 4), dtype=torch.float32).t())  # host tensor
+    with pytest.raises(TypeError):
+        l1.lipschitz_static(np.zeros((4, 8), dtype=np.float32, order="F"))
 
 
 def test_product_path_has_no_cpu_fallback():

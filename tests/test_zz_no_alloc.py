@@ -73,10 +73,42 @@ def test_static_rejects_sizes_beyond_the_scratch(l1):
     wide = torch.zeros((65537, 1), dtype=torch.float32, device="cuda").t()  # 1 x 65537
     for t, ld in ((tall, 8193), (wide, 1)):
         m, n = t.shape
-        rc = lib.l1_lipschitz_static(C.c_void_p(t.data_ptr()), m, n, ld, 100, 1e-6, None, C.byref(rho))
+        rc = lib.l1_lipschitz_static(C.c_void_p(t.data_ptr()), m, n, ld, 100, 1e-6, None, C.byref(rho),
+                                     None, None)
         assert rc == l1.ERR_INVALID_ARG
         assert b"static scratch" in lib.l1_last_error()
     # a host pointer is refused, not dereferenced
     host = np.zeros((4, 4), dtype=np.float32, order="F")
-    rc = lib.l1_lipschitz_static(C.c_void_p(host.ctypes.data), 4, 4, 4, 100, 1e-6, None, C.byref(rho))
+    rc = lib.l1_lipschitz_static(C.c_void_p(host.ctypes.data), 4, 4, 4, 100, 1e-6, None, C.byref(rho),
+                                 None, None)
     assert rc == l1.ERR_INVALID_ARG
+
+
+def test_static_reports_an_unconverged_estimate(l1):
+    """When max_iter runs out before the stopping rule fires the call still
+    returns L1_OK, but the status says so (and the estimate is low).  Two
+    top singular values 1 and 0.999 make the power iteration slow."""
+    rng = np.random.default_rng(9101)
+    m, n = 200, 120
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sv = np.linspace(0.5, 0.999, n)
+    sv[-1] = 1.0
+    a = (U * sv) @ V.T
+    d = _dev_colmajor(a)
+    rho1, conv1, it1 = l1.lipschitz_static(d, max_iter=1, rtol=1e-12, return_status=True)
+    assert not conv1 and it1 == 1
+    assert rho1 < 1.0
+    rho, conv, it = l1.lipschitz_static(d, max_iter=20000, rtol=1e-9, return_status=True)
+    assert conv and 1 < it <= 20000
+    assert abs(rho - 1.0) <= 1e-3
+    # the capture refusal and the device check fire before anything is enqueued
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin(capture_error_mode="thread_local")
+        try:
+            with pytest.raises(l1.L1Error):
+                l1.lipschitz_static(d, stream=s.cuda_stream)
+        finally:
+            g.capture_end()
