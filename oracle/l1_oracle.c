@@ -334,27 +334,36 @@ int orc_palm(const double* A, int m, int n, const double* b, const orc_palm_opts
  * matrix. */
 static int cholesky_lower(double* G, int m) {
     for (int j = 0; j < m; ++j) {
-        const double gjj = G[j + (size_t)j * m];
-        double d = gjj;
-        for (int k = 0; k < j; ++k) d -= G[j + (size_t)k * m] * G[j + (size_t)k * m];
+        /* column j: G(i, j) - sum over k = 0, ..., j-1 of R(i, k) R(j, k) for
+         * i >= j, each sum taken in that order of k (k outside i so that the
+         * inner loop walks down contiguous columns) */
+        double* gj = G + (size_t)j * m;
+        const double gjj = gj[j];
+        for (int k = 0; k < j; ++k) {
+            const double* rk = G + (size_t)k * m;
+            const double rjk = rk[j];
+            for (int i = j; i < m; ++i) gj[i] -= rk[i] * rjk;
+        }
+        const double d = gj[j];
         if (!(d > 16.0 * m * 2.220446049250313e-16 * gjj)) return ORC_ERR_NOT_SPD;
         const double rjj = sqrt(d);
-        G[j + (size_t)j * m] = rjj;
-        for (int i = j + 1; i < m; ++i) {
-            double s = G[i + (size_t)j * m];
-            for (int k = 0; k < j; ++k) s -= G[i + (size_t)k * m] * G[j + (size_t)k * m];
-            G[i + (size_t)j * m] = s / rjj;
-        }
+        gj[j] = rjj;
+        for (int i = j + 1; i < m; ++i) gj[i] = gj[i] / rjj;
     }
     return ORC_OK;
 }
 
 /* solve R R^T y = rhs with the lower factor R (forward then back substitution) */
 static void cholesky_solve(const double* R, int m, const double* rhs, double* y) {
-    for (int i = 0; i < m; ++i) {
-        double s = rhs[i];
-        for (int k = 0; k < i; ++k) s -= R[i + (size_t)k * m] * y[k];
-        y[i] = s / R[i + (size_t)i * m];
+    /* forward: y(i) = (rhs(i) - sum over k < i of R(i, k) y(k)) / R(i, i), the
+     * sum taken in increasing k; column k is applied to all rows below it
+     * once y(k) is known, so the inner loop walks down a contiguous column */
+    for (int i = 0; i < m; ++i) y[i] = rhs[i];
+    for (int k = 0; k < m; ++k) {
+        const double* rk = R + (size_t)k * m;
+        y[k] = y[k] / rk[k];
+        const double yk = y[k];
+        for (int i = k + 1; i < m; ++i) y[i] -= rk[i] * yk;
     }
     for (int i = m - 1; i >= 0; --i) {
         double s = y[i];
@@ -420,12 +429,19 @@ int orc_dalm(const double* A, int m, int n, int cab, const double* b, double bet
     if (!G || !z || !v || !bty || !rhs) { free(G); free(z); free(v); free(bty); free(rhs); return ORC_ERR_NOMEM; }
     /* G = A A^T (+ I) for the exact y-step; CG needs four m-vectors instead */
     if (cg_steps == 0) {
-        for (int i = 0; i < m; ++i)
-            for (int k = 0; k < m; ++k) {
-                double s = 0.0;
-                for (int j = 0; j < n; ++j) s += A[i + (size_t)j * m] * A[k + (size_t)j * m];
-                G[i + (size_t)k * m] = s + ((cab && i == k) ? 1.0 : 0.0);
+        /* G(i, k) = sum over j = 0, 1, ..., n-1 of A(i, j) A(k, j), summed in
+         * that order for every (i, k); the loops run j outside i so that the
+         * innermost one walks down contiguous columns */
+        for (int k = 0; k < m; ++k) {
+            double* g = G + (size_t)k * m;
+            for (int i = 0; i < m; ++i) g[i] = 0.0;
+            for (int j = 0; j < n; ++j) {
+                const double* col = A + (size_t)j * m;
+                const double akj = col[k];
+                for (int i = 0; i < m; ++i) g[i] += col[i] * akj;
             }
+            if (cab) g[k] += 1.0;
+        }
         if (cholesky_lower(G, m) != ORC_OK) {
             free(G); free(z); free(v); free(bty); free(rhs);
             return ORC_ERR_NOT_SPD;

@@ -103,10 +103,10 @@ MUTANTS = [
     ("dalm_w_sign", "Algorithm 2 w-update",
      "const double dj = -beta * (z[j] - bty[j]);", "const double dj = beta * (z[j] - bty[j]);"),
     ("dalm_gram_no_identity", "R1 B B^T = A A^T + I",
-     "G[i + (size_t)k * m] = s + ((cab && i == k) ? 1.0 : 0.0);", "G[i + (size_t)k * m] = s;"),
+     "if (cab) g[k] += 1.0;", "if (cab) g[k] += 0.0;"),
     ("cholesky_wrong_index", "Cholesky factor",
-     "s -= G[i + (size_t)k * m] * G[j + (size_t)k * m];",
-     "s -= G[i + (size_t)k * m] * G[i + (size_t)k * m];"),
+     "for (int i = j; i < m; ++i) gj[i] -= rk[i] * rjk;",
+     "for (int i = j; i < m; ++i) gj[i] -= rk[i] * rk[i];"),
     ("cholesky_solve_transposed", "back substitution with R^T",
      "s -= R[k + (size_t)i * m] * y[k];", "s -= R[i + (size_t)k * m] * y[k];"),
     ("cg_step_length_inverted", "CG y-step of §V-B: alpha = r^T r / p^T B B^T p",
