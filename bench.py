@@ -36,9 +36,20 @@ sys.path.insert(0, ROOT)
 
 import synthetic  # noqa: E402
 
-# the benchmarked configuration (tests import it to check parity in the same launch shape)
-BENCH = dict(m=1024, classes=40, per_class=30, N=1024, corrupt=0.3, seed=1000,
-             tol=1e-4, max_iter=10000, solver="DALM")
+# the cross-and-bouquet workloads (tests import them to check parity in the
+# same launch shape): 40 classes x 30 columns at m = 1024 in FP32, and
+# 100 classes x 40 columns at m = 4096 with A held in BF16 pieces on the
+# tensor cores
+CAB1024 = dict(m=1024, classes=40, per_class=30, N=1024, corrupt=0.3, seed=1000,
+               tol=1e-4, max_iter=10000, solver="DALM")
+CAB4096 = dict(m=4096, classes=100, per_class=40, N=4096, corrupt=0.3, seed=3000,
+               tol=1e-4, max_iter=10000, solver="DALM")
+BENCH = dict(CAB1024)
+
+
+def cab_workload(cfg, rank: int = 0):
+    return synthetic.cab_problem(cfg["m"], cfg["classes"], cfg["per_class"], cfg["N"],
+                                 corrupt=cfg["corrupt"], seed=cfg["seed"] + rank)
 METRIC = "solves/sec at rel. err <=1e-4 vs FP64 oracle"
 L2_FLUSH_BYTES = 512 << 20
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock

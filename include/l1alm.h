@@ -77,7 +77,10 @@ typedef enum {
     L1_ENGINE_AUTO = 0,  /* currently the same as L1_ENGINE_SIMT (the faster at
                           * every measured shape) */
     L1_ENGINE_SIMT = 1,  /* CUDA-core FP32 kernels (GEMV for N <= 8, tiled GEMM above) */
-    L1_ENGINE_TC = 2     /* tcgen05 tensor-core sweeps (batched right-hand sides) */
+    L1_ENGINE_TC = 2     /* tcgen05 BF16 tensor-core sweeps for batched DALM: A and the
+                          * panels as aligned BF16 pieces, the leading product summed
+                          * exactly, FP32 accumulation; narrow batches (tc_min_cols)
+                          * fall back to the CUDA-core sweeps */
 } l1_engine;
 
 /* ---------------------------------------------------------------- options
@@ -103,16 +106,20 @@ typedef struct {
     int32_t unroll_J;    /* multiplier update every J inner steps; 0 -> 10 */
     int32_t ckpt_every;  /* checkpoint interval of the tape; 0 -> 20 */
     int32_t profile;     /* 1: time every sweep with CUDA events (l1_info.sweep_*) */
-    int32_t tc_sweeps;   /* L1_ENGINE_TC: bit 0 A u, bit 1 y-step, bit 2 A^T y on tcgen05; 0 -> 5.
-                          * The y-step multiplies by (B B^T)^{-1}; its tensor-core
-                          * accumulation rounds with a bias that the iteration
-                          * accumulates, so by default it stays on the compensated
-                          * CUDA-core sweep. */
+    int32_t tc_pieces;   /* L1_ENGINE_TC: BF16 pieces of A and of the panels in the A u and
+                          * A^T y sweeps, 2 (three terms, about 16 bits) or 3 (six terms,
+                          * FP32-level products); 0 -> 3.
+                          * Precision BF16 runs its first phase with one piece of A
+                          * whatever this says. */
     int32_t refine;      /* precision BF16 / FP8: 0 -> after every column has met the
                           * stopping rule on the low-precision A, resume each one from
                           * its iterate on the FP32 A until the rule is met again
                           * (results and iters cover both phases); -1 -> return the
                           * low-precision answer */
+    int32_t tc_pieces_y; /* L1_ENGINE_TC: BF16 pieces of (B B^T)^{-1} and of the y-step's
+                          * right-hand side, 2 or 3; 0 -> 3 */
+    int32_t tc_min_cols; /* L1_ENGINE_TC: the tensor-core sweeps run while at least this
+                          * many columns are active, the CUDA-core sweeps below; 0 -> 128 */
 } l1_options;
 
 /* Per-instance results (host memory). */
@@ -194,7 +201,8 @@ L1_API int l1_group_load(l1_handle h, int64_t first, int64_t k, const float* con
  * at offset sum_{k<i} m[k]), x packs the solutions (offset sum_{k<i} n[k]);
  * N must equal count, ldb and ldx are ignored, y must be NULL.  res[i].resid
  * is ||b - A x||_2 and primal_obj 1/2||b - A x||^2 + lambda ||x||_1;
- * dual_obj and gap are NaN (not computed for groups).
+ * dual_obj and gap are NaN (not computed for groups).  x_init and y_init must
+ * be NULL.
  */
 
 /*
@@ -208,6 +216,16 @@ L1_API int l1_group_load(l1_handle h, int64_t first, int64_t k, const float* con
  *   y         optional (NULL) output of the dual iterate, m x N, leading
  *             dimension ldy: DALM's y, PALM's multiplier theta.
  *   res       host array of N results.
+ *   x_init    optional (NULL) warm start, laid out like x (leading dimension
+ *             ldxi): DALM's w_1 = [x; e] (Algorithm 2 starts from w_1 = 0
+ *             otherwise), PALM's x_1 and, for CAB, e_1 (Algorithm 1 takes
+ *             e_1 = b otherwise; the first e-step recomputes e from x_1),
+ *             FISTA's x_0 (Eq. 18).
+ *   y_init    optional (NULL) warm start of the dual iterate, laid out like y
+ *             (leading dimension ldyi): DALM's y_1, PALM's theta_1; zero
+ *             otherwise.  A DALM solve resumed from the x and y another solve
+ *             returned continues that solve's iteration: its first z-step
+ *             (Eq. 38) is recomputed from (w, y).
  * Each column stops on its own rule and is frozen from then on (per-instance
  * convergence masking).  Host pointers are copied in and out on the handle's
  * stream.  Errors: L1_ERR_INVALID_ARG, L1_ERR_OOM, L1_ERR_CUDA,
@@ -215,7 +233,8 @@ L1_API int l1_group_load(l1_handle h, int64_t first, int64_t k, const float* con
  */
 L1_API int l1_solve_batch(l1_handle h, const float* b, int64_t ldb, int64_t N, double tol,
                           int32_t max_iter, float* x, int64_t ldx, float* y, int64_t ldy,
-                          l1_result* res);
+                          l1_result* res, const float* x_init, int64_t ldxi, const float* y_init,
+                          int64_t ldyi);
 
 /*
  * l1_solve_batch on a handle set up with unroll_K > 0 (mode L1_P1, solver

@@ -41,7 +41,8 @@ class Options(C.Structure):
                 ("check_every", C.c_int32), ("class_count", C.c_int32),
                 ("class_offsets", C.POINTER(C.c_int32)), ("stream", C.c_void_p),
                 ("unroll_K", C.c_int32), ("unroll_J", C.c_int32), ("ckpt_every", C.c_int32),
-                ("profile", C.c_int32), ("tc_sweeps", C.c_int32), ("refine", C.c_int32)]
+                ("profile", C.c_int32), ("tc_pieces", C.c_int32), ("refine", C.c_int32),
+                ("tc_pieces_y", C.c_int32), ("tc_min_cols", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -91,7 +92,8 @@ def load() -> C.CDLL:
     L.l1_setup_group.restype = C.c_int
     L.l1_group_load.argtypes = [vp, i64, i64, vp]
     L.l1_group_load.restype = C.c_int
-    L.l1_solve_batch.argtypes = [vp, vp, i64, i64, dbl, i32, vp, i64, vp, i64, C.POINTER(Result)]
+    L.l1_solve_batch.argtypes = [vp, vp, i64, i64, dbl, i32, vp, i64, vp, i64, C.POINTER(Result), vp, i64,
+                                 vp, i64]
     L.l1_solve_batch.restype = C.c_int
     L.l1_backward.argtypes = [vp, vp, i64, vp, vp]
     L.l1_backward.restype = C.c_int
@@ -158,8 +160,9 @@ class Solver:
                  xi_growth: float = 0.0, xi_max: float = 0.0, lipschitz: float = 0.0,
                  inner_max: int = 0, inner_tol: float = 0.0, check_every: int = 0,
                  class_offsets=None, precision: int = A_FP32, engine: int = ENGINE_AUTO,
-                 profile: bool = False, tc_sweeps: int = 0, unroll_K: int = 0, unroll_J: int = 0,
-                 ckpt_every: int = 0, refine: bool = True, stream=None):
+                 profile: bool = False, tc_pieces: int = 0, tc_pieces_y: int = 0, tc_min_cols: int = 0,
+                 unroll_K: int = 0, unroll_J: int = 0, ckpt_every: int = 0, refine: bool = True,
+                 stream=None):
         L = load()
         o = Options()
         L.l1_options_init(C.byref(o))
@@ -173,7 +176,7 @@ class Solver:
             o.xi_max = xi_max
         o.lipschitz, o.inner_tol = lipschitz, inner_tol
         o.profile = 1 if profile else 0
-        o.tc_sweeps = tc_sweeps
+        o.tc_pieces, o.tc_pieces_y, o.tc_min_cols = tc_pieces, tc_pieces_y, tc_min_cols
         o.unroll_K = unroll_K
         o.refine = 0 if refine else -1
         if unroll_J:
@@ -209,13 +212,15 @@ class Solver:
             out[k] = list(v) if k.startswith("sweep_") else v
         return out
 
-    def solve(self, b, tol: float, max_iter: int, x=None, y=None, want_y: bool = False):
+    def solve(self, b, tol: float, max_iter: int, x=None, y=None, want_y: bool = False, x_init=None,
+              y_init=None):
         """Solve one problem per column of b (m x N).
 
         b may be a host numpy array or a torch tensor (device or host,
         column-major).  Outputs are allocated like b when not given: x is
         (n + m) x N for CAB ([x; e] per column), n x N otherwise; y (the dual
-        iterate) only if ``want_y`` or given.  Returns (x, y, results).
+        iterate) only if ``want_y`` or given.  ``x_init`` / ``y_init`` (laid
+        out like x / y) warm-start the iteration.  Returns (x, y, results).
         """
         L = load()
         is_np = isinstance(b, np.ndarray)
@@ -240,8 +245,14 @@ class Solver:
                 import torch
                 y = torch.empty((N, self.m), dtype=torch.float32, device=b.device).t()
         res = (Result * N)()
+        if isinstance(x_init, np.ndarray):
+            x_init = np.asfortranarray(x_init, dtype=np.float32)
+        if isinstance(y_init, np.ndarray):
+            y_init = np.asfortranarray(y_init, dtype=np.float32)
         _check(L.l1_solve_batch(self._h, _ptr(b), _ld(b), N, float(tol), int(max_iter), _ptr(x), _ld(x),
-                                _ptr(y), _ld(y) if y is not None else 0, res), "l1_solve_batch")
+                                _ptr(y), _ld(y) if y is not None else 0, res,
+                                _ptr(x_init), _ld(x_init) if x_init is not None else 0,
+                                _ptr(y_init), _ld(y_init) if y_init is not None else 0), "l1_solve_batch")
         return x, y, results_to_dict(res)
 
     def backward(self, grad_x, grad_b=None, grad_A=None, want_b: bool = True, want_A: bool = True):
@@ -334,7 +345,7 @@ class Group:
             x_packed = torch.empty(int(self.xoff[-1]), dtype=torch.float32, device=b_packed.device)
         res = (Result * self.count)()
         _check(load().l1_solve_batch(self._h, _ptr(b_packed), 0, self.count, float(tol), int(max_iter),
-                                     _ptr(x_packed), 0, None, 0, res), "l1_solve_batch(group)")
+                                     _ptr(x_packed), 0, None, 0, res, None, 0, None, 0), "l1_solve_batch(group)")
         return x_packed, results_to_dict(res)
 
     def info(self) -> dict:

@@ -5,7 +5,7 @@
 
 #include "common.cuh"
 #include "setup.cuh"
-#include "tc.cuh"
+#include "tc16.cuh"
 
 namespace l1 {
 
@@ -125,10 +125,14 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
     }
     // requests the library does not implement
     if (mode == L1_P1_2 && o.solver != L1_PALM) return L1_ERR_UNSUPPORTED;  // R10 is a PALM
-    // low-precision A: batched DALM on the CUDA-core sweeps (with refinement)
-    if (o.precision != L1_A_FP32 &&
-        (o.solver != L1_DALM || mode == L1_QP_LAMBDA || o.engine == L1_ENGINE_TC || o.unroll_K > 0))
+    // low-precision A: batched DALM with refinement (BF16 on either engine,
+    // FP8 on the CUDA-core sweeps)
+    if (o.precision != L1_A_FP32 && (o.solver != L1_DALM || mode == L1_QP_LAMBDA || o.unroll_K > 0))
         return L1_ERR_UNSUPPORTED;
+    if (o.precision == L1_A_FP8E4M3 && o.engine == L1_ENGINE_TC) return L1_ERR_UNSUPPORTED;
+    if (o.tc_pieces < 0 || o.tc_pieces > 3 || o.tc_pieces_y < 0 || o.tc_pieces_y > 3 || o.tc_min_cols < 0)
+        return L1_ERR_INVALID_ARG;
+    if (o.tc_pieces == 1 || o.tc_pieces_y == 1) return L1_ERR_UNSUPPORTED;  // a one-piece panel cannot converge
     if (o.engine == L1_ENGINE_TC && (o.solver != L1_DALM || mode == L1_QP_LAMBDA)) return L1_ERR_UNSUPPORTED;
     if (o.unroll_K < 0 || o.unroll_J < 0 || o.ckpt_every < 0) return L1_ERR_INVALID_ARG;
     if (o.unroll_K > 0) {
@@ -175,15 +179,12 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
             rc = make_lowp(h);
             if (rc) break;
         }
-        // tensor-core engine (batched DALM): TF32 pieces of both layouts of A
+        // tensor-core engine (batched DALM): aligned BF16 pieces of both
+        // layouts of A (those of (B B^T)^{-1} follow the factor below)
         h->use_tc = (o.engine == L1_ENGINE_TC) && o.solver == L1_DALM && mode != L1_QP_LAMBDA;
         if (h->use_tc) {
-            for (int k = 0; k < 2 && !rc; ++k) rc = dev_alloc_t(h, &h->A_rm_p[k], (size_t)h->ldn * m);
-            for (int k = 0; k < 2 && !rc; ++k) rc = dev_alloc_t(h, &h->A_cm_p[k], (size_t)h->ldm * n);
-            for (int k = 0; k < 3 && !rc; ++k) rc = dev_alloc_t(h, &h->F_p[k], (size_t)h->ldm * m);
-            if (!rc) rc = dev_alloc_t(h, &h->tc_err, 1);
-            if (!rc) rc = tc::split_tf32(h, h->A_rm, h->ldn * m, h->A_rm_p[0], h->A_rm_p[1], nullptr);
-            if (!rc) rc = tc::split_tf32(h, h->A_cm, h->ldm * n, h->A_cm_p[0], h->A_cm_p[1], nullptr);
+            rc = dev_alloc_t(h, &h->tc_err, 1);
+            if (!rc) rc = tc16::make_dictionary_pieces(h);
             if (rc) break;
         }
         const bool needs_L = (mode == L1_QP_LAMBDA) || (o.solver == L1_PALM);
@@ -203,6 +204,10 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
             if (rc) break;
             rc = dalm_factor(h, mode == L1_CAB ? 1.0 : 0.0);
             if (rc) break;
+            if (h->use_tc) {
+                rc = tc16::make_factor_pieces(h);
+                if (rc) break;
+            }
         }
         cudaEventRecord(ev1, h->stream);
         if (cudaEventSynchronize(ev1) != cudaSuccess) { rc = L1_ERR_CUDA; break; }
@@ -277,10 +282,11 @@ int l1_group_load(l1_handle hh, int64_t first, int64_t k, const float* const* A)
 }
 
 int l1_solve_batch(l1_handle hh, const float* b, int64_t ldb, int64_t N, double tol, int32_t max_iter, float* x,
-                   int64_t ldx, float* y, int64_t ldy, l1_result* res) {
+                   int64_t ldx, float* y, int64_t ldy, l1_result* res, const float* x_init, int64_t ldxi,
+                   const float* y_init, int64_t ldyi) {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (h && h->grp) {
-        if (!b || !x || !res || y || max_iter <= 0 || !(tol >= 0.0)) return L1_ERR_INVALID_ARG;
+        if (!b || !x || !res || y || x_init || y_init || max_iter <= 0 || !(tol >= 0.0)) return L1_ERR_INVALID_ARG;
         return group_solve(h, b, N, tol, max_iter, x, res);
     }
     if (!h || !b || !x || !res || N <= 0 || N > 65535 || max_iter <= 0 || !(tol >= 0.0)) return L1_ERR_INVALID_ARG;
@@ -288,12 +294,15 @@ int l1_solve_batch(l1_handle hh, const float* b, int64_t ldb, int64_t N, double 
     const int64_t nx = (h->mode == L1_CAB) ? h->n + h->m : h->n;
     if (ldx < nx) return L1_ERR_INVALID_ARG;
     if (y && ldy < h->m) return L1_ERR_INVALID_ARG;
-    if (h->opt.unroll_K > 0 && y) return L1_ERR_INVALID_ARG;
+    if (x_init && ldxi < nx) return L1_ERR_INVALID_ARG;
+    if (y_init && ldyi < h->m) return L1_ERR_INVALID_ARG;
+    if (h->opt.unroll_K > 0 && (y || x_init || y_init)) return L1_ERR_INVALID_ARG;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != h->device) cudaSetDevice(h->device);
-    int rc = h->opt.unroll_K > 0 ? unroll_forward(h, b, ldb, (int)N, x, ldx, res)
-                                 : solve_batch(h, b, ldb, (int)N, tol, max_iter, x, ldx, y, ldy, res);
+    int rc = h->opt.unroll_K > 0
+                 ? unroll_forward(h, b, ldb, (int)N, x, ldx, res)
+                 : solve_batch(h, b, ldb, (int)N, tol, max_iter, x, ldx, y, ldy, res, x_init, ldxi, y_init, ldyi);
     if (dev != h->device) cudaSetDevice(dev);
     return rc;
 }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -83,11 +84,10 @@ struct Workspace {
     int64_t cap_N = 0;  // columns the buffers are sized for
     PanelSet ps[2];
     float* R = nullptr;   // DALM right-hand side of Eq. 39 / PALM residual c - A z (scratch)
-    // TF32 pieces of the panels the tensor-core sweeps read (scratch)
-    float* Up[2] = {nullptr, nullptr};         // of U_x (n x N)
-    float* Rp[3] = {nullptr, nullptr, nullptr}; // of R (m x N)
-    float* Yp[2] = {nullptr, nullptr};          // of y (m x N)
-    float* Ylo = nullptr;                       // (B B^T)^{-1}_lo R (m x N)
+    // BF16 pieces of the panels the tensor-core sweeps read (scratch)
+    __nv_bfloat16* Vh[3] = {nullptr, nullptr, nullptr};  // of V_x (n x N, ld = ldn)
+    __nv_bfloat16* Dh[3] = {nullptr, nullptr, nullptr};  // of d (m x N, ld = ldm)
+    __nv_bfloat16* Yh[3] = {nullptr, nullptr, nullptr};  // of y (m x N, ld = ldm)
     // results in the caller's column order ("home")
     float* hB = nullptr;
     float* hWx = nullptr;
@@ -131,11 +131,12 @@ struct Handle {
     void* A_cm_lp = nullptr;
     float* A_rm_scale = nullptr;
     float* A_cm_scale = nullptr;
-    // tensor-core engine: TF32 pieces (p1 + p2 (+ p3) == value) of the operands
+    // tensor-core engine: aligned BF16 pieces of both layouts of A and of
+    // (B B^T)^{-1} (same leading dimensions), see gemm_bf16.cuh
     bool use_tc = false;
-    float* A_rm_p[2] = {nullptr, nullptr};
-    float* A_cm_p[2] = {nullptr, nullptr};
-    float* F_p[3] = {nullptr, nullptr, nullptr};
+    __nv_bfloat16* A_rm_h[3] = {nullptr, nullptr, nullptr};
+    __nv_bfloat16* A_cm_h[3] = {nullptr, nullptr, nullptr};
+    __nv_bfloat16* F_h[3] = {nullptr, nullptr, nullptr};
     int* tc_err = nullptr;  // device: first bounded-wait failure of a tcgen05 sweep
     // encoded TMA tensor maps, keyed by the operand pointers and shapes
     struct MapCacheEntry {

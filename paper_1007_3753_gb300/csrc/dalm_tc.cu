@@ -1,0 +1,21 @@
+// Instantiations of the tensor-core DALM sweeps (see dalm_tc.cuh).
+#include "dalm_tc.cuh"
+
+namespace l1 {
+
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcD& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active) {
+    return tc16::launch(h, M, N, K, op, tl, epi, po, part, active);
+}
+
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcY& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active) {
+    return tc16::launch(h, M, N, K, op, tl, epi, po, part, active);
+}
+
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcS& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active) {
+    return tc16::launch(h, M, N, K, op, tl, epi, po, part, active);
+}
+
+}  // namespace l1

@@ -1,0 +1,114 @@
+// DALM on the BF16 tensor-core engine: the epilogues of its three sweeps and
+// the launches (instantiated in dalm_tc.cu, apart from the rest of the
+// solver so that the two compile in parallel).
+#pragma once
+
+#include "common.cuh"
+#include "tc16.cuh"
+
+namespace l1 {
+
+// ------------------------------------- DALM epilogues of the tensor-core engine
+// Algorithm 2 with B = [A I] (CAB) or B = A (P1), the y-step of Eq. 39 taken
+// as a correction of the previous dual iterate:
+//   y_{k+1} = y_k + (B B^T)^{-1} d,   d = B z_{k+1} - (B w_k - b)/beta - B B^T y_k
+//                                      = B V + b/beta,  V = z_{k+1} - w_k/beta - B^T y_k,
+// which is the step of Eq. 39 in exact arithmetic.  Its fixed point does not
+// depend on how exactly the inverse is applied, and d vanishes as the
+// iteration converges, so the rounding of the inverse's product shrinks with
+// it.  V = clamp(v) - v with v = B^T y_k + w_k/beta.  Panels: V_x (FP32 and
+// BF16 pieces), V_e, Z = z_{k+1}, W, Y.  Each functor returns the value whose
+// BF16 pieces the next sweep reads (0 for frozen columns).
+
+// T1 (rows of A, acc = A V_x): d = acc (+ V_e) + b / beta
+struct EpiTcD {
+    static constexpr int NRED = 0;
+    const float* Ve;
+    const float* B;
+    const float* binv;
+    const int32_t* active;
+    int64_t ldm;
+    int cab;
+    __device__ float operator()(int i, int j, float acc, double*) const {
+        if (!active[j]) return 0.0f;
+        const int64_t o = (int64_t)j * ldm + i;
+        float d = fmaf(B[o], binv[j], acc);
+        if (cab) d += Ve[o];
+        return d;
+    }
+};
+
+// T2 (rows of F, acc = F d): y' = y + acc.  CAB: the e-part of the w-step
+// (B^T y' is y' there): w_e' = w_e - beta (z_e - y'), z_e' = clamp(v),
+// V_e = z_e' - v with v = y' + w_e'/beta.  red: ||dw_e||^2, ||w_e||^2.
+// Returns y'.
+struct EpiTcY {
+    static constexpr int NRED = 2;
+    float* Y;
+    float* We;
+    float* Ze;
+    float* Ve;
+    const float* beta;
+    const float* binv;
+    const int32_t* active;
+    int64_t ldm;
+    int cab;
+    __device__ float operator()(int i, int j, float acc, double* red) const {
+        if (!active[j]) return 0.0f;
+        const int64_t o = (int64_t)j * ldm + i;
+        const float y = Y[o] + acc;
+        Y[o] = y;
+        if (cab) {
+            const float we = We[o];
+            const float dw = -beta[j] * (Ze[o] - y);
+            const float wn = we + dw;
+            We[o] = wn;
+            const float v = fmaf(wn, binv[j], y);
+            const float z = clamp_unit(v);
+            Ze[o] = z;
+            Ve[o] = z - v;
+            red[0] += (double)dw * dw;
+            red[1] += (double)we * we;
+        }
+        return y;
+    }
+};
+
+// T3 (rows of A^T, acc = A^T y'): the x-part of the w-step,
+// w_x' = w_x - beta (z_x - acc), z_x' = clamp(v), V_x = z_x' - v with
+// v = acc + w_x'/beta.  red: ||dw_x||^2, ||w_x||^2.  Returns V_x.
+struct EpiTcS {
+    static constexpr int NRED = 2;
+    float* Wx;
+    float* Zx;
+    float* Vx;
+    const float* beta;
+    const float* binv;
+    const int32_t* active;
+    int64_t ldn;
+    __device__ float operator()(int i, int j, float acc, double* red) const {
+        if (!active[j]) return 0.0f;
+        const int64_t o = (int64_t)j * ldn + i;
+        const float w = Wx[o];
+        const float dw = -beta[j] * (Zx[o] - acc);
+        const float wn = w + dw;
+        Wx[o] = wn;
+        const float v = fmaf(wn, binv[j], acc);
+        const float z = clamp_unit(v);
+        Zx[o] = z;
+        const float vx = z - v;
+        Vx[o] = vx;
+        red[0] += (double)dw * dw;
+        red[1] += (double)w * w;
+        return vx;
+    }
+};
+
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcD& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active);
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcY& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active);
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcS& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active);
+
+}  // namespace l1

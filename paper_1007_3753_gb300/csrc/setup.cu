@@ -5,7 +5,6 @@
 #include "common.cuh"
 #include "gemm_simt.cuh"
 #include "setup.cuh"
-#include "tc.cuh"
 
 namespace l1 {
 
@@ -340,11 +339,6 @@ int dalm_factor(Handle* h, double diag_add) {
         syrk64_kernel<double><<<g16, dim3(16, 16), 0, s>>>(X, m, 1, m, m, G, m, 0.0);
         ++h->launches;
         to_f32_split_kernel<<<(unsigned)((h->ldm * m + 255) / 256), 256, 0, s>>>(G, m, h->F, h->F_lo, h->ldm);
-        if (h->use_tc) {
-            // three TF32 pieces (33 bits) of the FP64 inverse for the tensor-core y-step
-            int rc2 = tc::split_tf32_from_f64(h, G, m, m, m, h->ldm, h->F_p[0], h->F_p[1], h->F_p[2]);
-            if (rc2 != L1_OK) rc = rc2;
-        }
         ++h->launches;
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);

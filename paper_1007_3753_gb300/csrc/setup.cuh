@@ -34,6 +34,7 @@ void graph_cache_clear(Handle* h);
 
 // batched solve (solve.cu)
 int solve_batch(Handle* h, const float* b_dev, int64_t ldb, int N, double tol, int max_iter,
-                float* x_dev, int64_t ldx, float* y_dev, int64_t ldy, l1_result* res);
+                float* x_dev, int64_t ldx, float* y_dev, int64_t ldy, l1_result* res,
+                const float* x_init, int64_t ldxi, const float* y_init, int64_t ldyi);
 
 }  // namespace l1

@@ -8,7 +8,7 @@
 #include "gemm_simt.cuh"
 #include "setup.cuh"
 #include "solver_kernels.cuh"
-#include "tc.cuh"
+#include "tc16.cuh"
 
 namespace l1 {
 
@@ -246,8 +246,8 @@ static int ensure_workspace(Handle* h, int N) {
         old.insert(old.end(), {p.B, p.Wx, p.We, p.Ux, p.Ue, p.Y, p.X, p.Cc, p.colf, p.coli, p.cold});
     }
     old.insert(old.end(), {w.R, w.hB, w.hWx, w.hWe, w.hY, w.hUx, w.hUe, w.hcoli, w.hcold, w.hcolf, w.part, w.newpos,
-                           w.count, w.resid2, w.classl1, w.class_off, w.Up[0], w.Up[1], w.Rp[0], w.Rp[1],
-                           w.Rp[2], w.Yp[0], w.Yp[1], w.Ylo});
+                           w.count, w.resid2, w.classl1, w.class_off});
+    for (int k = 0; k < 3; ++k) old.insert(old.end(), {w.Vh[k], w.Dh[k], w.Yh[k]});
     for (void* p : old) dev_free(h, p);
     if (w.h_count) cudaFreeHost(w.h_count);
     w = Workspace{};
@@ -270,16 +270,17 @@ static int ensure_workspace(Handle* h, int N) {
     }
     L1_TRY(dev_alloc_t(h, &w.R, ldm * N));
     if (h->use_tc) {
-        for (int k = 0; k < 2; ++k) L1_TRY(dev_alloc_t(h, &w.Up[k], ldn * N));
-        for (int k = 0; k < 3; ++k) L1_TRY(dev_alloc_t(h, &w.Rp[k], ldm * N));
-        for (int k = 0; k < 2; ++k) L1_TRY(dev_alloc_t(h, &w.Yp[k], ldm * N));
-        L1_TRY(dev_alloc_t(h, &w.Ylo, ldm * N));
+        for (int k = 0; k < 3; ++k) {
+            L1_TRY(dev_alloc_t(h, &w.Vh[k], ldn * N));
+            L1_TRY(dev_alloc_t(h, &w.Dh[k], ldm * N));
+            L1_TRY(dev_alloc_t(h, &w.Yh[k], ldm * N));
+        }
     }
     L1_TRY(dev_alloc_t(h, &w.hB, ldm * N));
     L1_TRY(dev_alloc_t(h, &w.hWx, ldn * N));
     L1_TRY(dev_alloc_t(h, &w.hWe, ldm * N));
     L1_TRY(dev_alloc_t(h, &w.hY, ldm * N));
-    if (h->opt.precision != L1_A_FP32) {
+    if (h->opt.precision != L1_A_FP32 || h->use_tc) {
         L1_TRY(dev_alloc_t(h, &w.hUx, ldn * N));
         L1_TRY(dev_alloc_t(h, &w.hUe, ldm * N));
     }
@@ -411,8 +412,54 @@ static int compact(Handle* h, int q, int N_cur, int solver, double xi_max, int* 
     return L1_OK;
 }
 
+// Tensor-core sweeps: the term list of a p x p split (p pieces of each operand)
+static tc16::Terms terms_square(int p) {
+    return p >= 3 ? tc16::terms_3x3() : (p == 2 ? tc16::terms_2x2() : tc16::terms_1x1());
+}
+
+// Retiring slots of a tensor-core set carry (V, Z); their home copies must
+// hold the CUDA-core state U = Z - W/beta (the refinement restarts from it).
+// inactive_only: convert the retiring slots (before a compaction), else the
+// active ones (when the set continues on the CUDA-core sweeps).
+static int tc_to_simt(Handle* h, const PanelSet& P, const Cols& c, int N_cur, bool cab, bool inactive_only) {
+    const int m = (int)h->m, n = (int)h->n;
+    dim3 gx((unsigned)std::min(8, (n + 255) / 256), (unsigned)N_cur), ge((unsigned)std::min(8, (m + 255) / 256),
+                                                                          (unsigned)N_cur);
+    tc_state_to_simt_kernel<<<gx, 256, 0, h->stream>>>(P.Ux, P.X, P.Wx, c.binv, c.active, h->ldn, n,
+                                                        inactive_only ? 1 : 0);
+    L1_LAUNCH_CHECK(h);
+    if (cab) {
+        tc_state_to_simt_kernel<<<ge, 256, 0, h->stream>>>(P.Ue, P.Cc, P.We, c.binv, c.active, h->ldm, m,
+                                                            inactive_only ? 1 : 0);
+        L1_LAUNCH_CHECK(h);
+    }
+    return L1_OK;
+}
+
+// DALM state of the active slots from (w, y): z = clamp(B^T y + w/beta) and
+// U = z - w/beta, or with have_u the given U; for the tensor-core engine
+// (tc) also Z = z and V = z - B^T y - w/beta, and the BF16 pieces of V_x.
+// One A^T y sweep on the FP32 dictionary gives B^T y (its identity block is y).
+static int dalm_restart(Handle* h, const PanelSet& P, const Cols& c, int N_cur, bool cab, bool have_u, bool tc,
+                        double* part_n, int pieces) {
+    const int m = (int)h->m, n = (int)h->n;
+    const int rc = launch_sweep(h, n, N_cur, m, h->A_cm, h->ldm, P.Y, h->ldm,
+                                EpiDalmRestart{P.Ux, P.X, P.Wx, c.binv, c.active, h->ldn, have_u ? 1 : 0, tc ? 1 : 0},
+                                part_n, c.active);
+    if (rc < 0) return rc;
+    if (cab) {
+        dim3 ge((unsigned)std::min(8, (m + 255) / 256), (unsigned)N_cur);
+        dalm_restart_e_kernel<<<ge, 256, 0, h->stream>>>(P.Ue, P.Cc, P.We, P.Y, c.binv, c.active, h->ldm, m,
+                                                          have_u ? 1 : 0, tc ? 1 : 0);
+        L1_LAUNCH_CHECK(h);
+    }
+    if (tc) L1_TRY(tc16::split_aligned_lines(h, P.Ux, nullptr, N_cur, n, h->ldn, h->ws.Vh, pieces));
+    return L1_OK;
+}
+
 int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int max_iter,
-                float* x, int64_t ldx, float* y, int64_t ldy, l1_result* res) {
+                float* x, int64_t ldx, float* y, int64_t ldy, l1_result* res,
+                const float* x_init, int64_t ldxi, const float* y_init, int64_t ldyi) {
     L1_TRY(ensure_workspace(h, N));
     Workspace& w = h->ws;
     cudaStream_t s = h->stream;
@@ -445,6 +492,22 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     } else {
         L1_CUDA_TRY(cudaMemsetAsync(P->We, 0, pm, s));
     }
+    // warm start: x_init = w_0 ([x; e] for CAB), y_init = y_0 (DALM) or
+    // theta_0 (PALM); PALM and FISTA start their first inner loop at z = x_0
+    if (x_init) {
+        L1_CUDA_TRY(cudaMemcpy2DAsync(P->Wx, ldn * sizeof(float), x_init, ldxi * sizeof(float), n * sizeof(float),
+                                      N, cudaMemcpyDefault, s));
+        if (solver == L1_PALM) {
+            L1_CUDA_TRY(cudaMemcpyAsync(P->X, P->Wx, pn, cudaMemcpyDeviceToDevice, s));
+            L1_CUDA_TRY(cudaMemcpyAsync(P->Ux, P->Wx, pn, cudaMemcpyDeviceToDevice, s));
+        }
+        if (cab)
+            L1_CUDA_TRY(cudaMemcpy2DAsync(P->We, ldm * sizeof(float), x_init + n, ldxi * sizeof(float),
+                                          m * sizeof(float), N, cudaMemcpyDefault, s));
+    }
+    if (y_init)
+        L1_CUDA_TRY(cudaMemcpy2DAsync(P->Y, ldm * sizeof(float), y_init, ldyi * sizeof(float), m * sizeof(float), N,
+                                      cudaMemcpyDefault, s));
     Cols c = make_cols(h, 0, N);
     init_cols_kernel<<<N, 128, 0, s>>>(c, P->B, ldm, m, mode, o.beta, o.xi0, xi_max, o.lambda);
     L1_LAUNCH_CHECK(h);
@@ -463,86 +526,83 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     const int64_t round_cap = (solver == L1_DALM || mode == L1_QP_LAMBDA) ? (int64_t)max_iter
                                                                           : (int64_t)max_iter * inner_max;
     int64_t rounds = 0;
-    bool pieces_valid = false;  // TF32 pieces of U_x match the current set
     // low-precision A: phase 1 sweeps the BF16 / FP8 copy, phase 2 (refinement)
     // resumes every column on the FP32 A
     const bool lowp = o.precision != L1_A_FP32;
     int phase = 1;
     int32_t* iters1 = w.hcoli + 5 * w.cap_N;
+    // tensor-core engine (batched DALM): BF16 pieces of A and the panels
+    const int tc_min = o.tc_min_cols > 0 ? o.tc_min_cols : 128;
+    const int tcp = o.tc_pieces > 0 ? std::min(o.tc_pieces, 3) : 3;      // A sweeps
+    const int tcy = o.tc_pieces_y > 0 ? std::min(o.tc_pieces_y, 3) : 3;  // y-step
+    bool tc_mode = h->use_tc && solver == L1_DALM && N_cur >= tc_min;
+    if (solver == L1_DALM && (x_init || y_init || tc_mode)) {
+        // the state z_1 (and V_1) of the first iteration from (w_0, y_0); a
+        // cold start is all zeros either way, but the pieces of V are written
+        if (x_init || y_init) L1_TRY(dalm_restart(h, *P, c, N_cur, cab, false, tc_mode, part_n, tcp));
+        else L1_TRY(tc16::split_aligned_lines(h, P->Ux, nullptr, N_cur, n, ldn, w.Vh, tcp));
+    }
     while (true) {
         P = &w.ps[q];
         c = make_cols(h, q, N_cur);
         const bool lowp_now = lowp && phase == 1;
         const double na = N_cur;
-        // tensor-core sweeps while the batch fills at least half a 64-column tile
-        const bool tc_now = h->use_tc && solver == L1_DALM && N_cur >= 32;
-        if (tc_now && !pieces_valid) {
-            L1_TRY(tc::split_tf32(h, P->Ux, ldn * (int64_t)N_cur, w.Up[0], w.Up[1], nullptr));
-            pieces_valid = true;
-        }
         auto run_chunk = [&](cudaStream_t s) -> int {
         for (int r = 0; r < check_every; ++r) {
-            if (solver == L1_DALM) {
-                // Algorithm 2: three sweeps per iteration.  On tcgen05 the
-                // products are split-TF32 (three terms; six for the y-step so
-                // the inverse carries 33 bits), see tc.cuh; the epilogues also
-                // write the TF32 pieces the next tensor-core sweep reads.
-                // default: the two A sweeps on tensor cores, the y-step on the
-                // compensated CUDA-core sweep (see l1_options.tc_sweeps)
-                const int mask = o.tc_sweeps ? o.tc_sweeps : 5;
-                const bool t1 = tc_now && (mask & 1), t2 = tc_now && (mask & 2), t3 = tc_now && (mask & 4);
-                const Pieces rp = h->use_tc ? Pieces{{w.Rp[0], w.Rp[1], w.Rp[2]}} : Pieces{{nullptr, nullptr, nullptr}};
-                const Pieces yp = h->use_tc ? Pieces{{w.Yp[0], w.Yp[1], nullptr}} : Pieces{{nullptr, nullptr, nullptr}};
-                const Pieces up = h->use_tc ? Pieces{{w.Up[0], w.Up[1], nullptr}} : Pieces{{nullptr, nullptr, nullptr}};
-                const EpiDalmRhs e1{w.R, P->Ue, P->B, c.binv, c.active, ldm, cab ? 1 : 0, rp};
-                const EpiDalmY e2{P->Y, P->We, P->Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0, yp};
-                const EpiDalmS e3{P->Wx, P->Ux, c.beta, c.binv, c.active, ldn, up};
+            if (solver == L1_DALM && tc_mode) {
+                // Algorithm 2 on the BF16 tensor cores, the y-step as a
+                // correction (EpiTcD / EpiTcY / EpiTcS): pa pieces of A (one,
+                // the BF16 A itself, in the first phase of a BF16 solve), tcp
+                // pieces of the panels V_x and y, tcy of F and d
+                const int pa = lowp_now ? 1 : tcp;
+                const tc16::Terms ta = lowp_now ? tc16::terms_1xN(tcp) : terms_square(tcp);
+                tc16::Operands o1{{h->A_rm_h[0], h->A_rm_h[1], h->A_rm_h[2]}, pa,
+                                  {w.Vh[0], w.Vh[1], w.Vh[2]}, tcp, ldn, ldn};
+                tc16::PieceOut po1{{w.Dh[0], w.Dh[1], w.Dh[2]}, tcy, ldm};
+                prof.start(0, 2.0 * m * n * na);
+                int rc = tc_sweep(h, m, N_cur, n, o1, ta, EpiTcD{P->Ue, P->B, c.binv, c.active, ldm, cab ? 1 : 0},
+                                      po1, nullptr, c.active);
+                prof.stop();
+                if (rc < 0) return rc;
+                tc16::Operands o2{{h->F_h[0], h->F_h[1], h->F_h[2]}, tcy, {w.Dh[0], w.Dh[1], w.Dh[2]}, tcy, ldm, ldm};
+                tc16::PieceOut po2{{w.Yh[0], w.Yh[1], w.Yh[2]}, tcp, ldm};
+                prof.start(1, 2.0 * m * m * na);
+                const int np_e = tc_sweep(
+                    h, m, N_cur, m, o2, terms_square(tcy),
+                    EpiTcY{P->Y, P->We, P->Cc, P->Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0}, po2, part_m,
+                    c.active);
+                prof.stop();
+                if (np_e < 0) return np_e;
+                tc16::Operands o3{{h->A_cm_h[0], h->A_cm_h[1], h->A_cm_h[2]}, pa,
+                                  {w.Yh[0], w.Yh[1], w.Yh[2]}, tcp, ldm, ldm};
+                tc16::PieceOut po3{{w.Vh[0], w.Vh[1], w.Vh[2]}, tcp, ldn};
+                prof.start(2, 2.0 * m * n * na);
+                const int np_x = tc_sweep(h, n, N_cur, m, o3, ta,
+                                              EpiTcS{P->Wx, P->X, P->Ux, c.beta, c.binv, c.active, ldn}, po3, part_n,
+                                              c.active);
+                prof.stop();
+                if (np_x < 0) return np_x;
+                ctrl_dalm_kernel<<<N_cur, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e, part_n, np_x, tol, max_iter);
+                L1_LAUNCH_CHECK(h);
+            } else if (solver == L1_DALM) {
+                // Algorithm 2: three sweeps per iteration on the CUDA cores
+                const EpiDalmRhs e1{w.R, P->Ue, P->B, c.binv, c.active, ldm, cab ? 1 : 0};
+                const EpiDalmY e2{P->Y, P->We, P->Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0};
+                const EpiDalmS e3{P->Wx, P->Ux, c.beta, c.binv, c.active, ldn};
                 prof.start(0, 2.0 * m * n * na);
                 int rc;
-                if (t1) {
-                    const float* ap[2] = {h->A_rm_p[0], h->A_rm_p[1]};
-                    const float* xp[2] = {w.Up[0], w.Up[1]};
-                    rc = tc::launch(h, m, N_cur, n, ap, 2, xp, 2, tc::terms_split3(), ldn, ldn, e1, part_m, c.active);
-                } else if (lowp_now) {
-                    rc = sweep_lowp(h, true, m, N_cur, n, P->Ux, ldn, e1, part_m, c.active);
-                } else {
-                    rc = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Ux, ldn, e1, part_m, c.active);
-                }
+                if (lowp_now) rc = sweep_lowp(h, true, m, N_cur, n, P->Ux, ldn, e1, part_m, c.active);
+                else rc = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Ux, ldn, e1, part_m, c.active);
                 prof.stop();
                 if (rc < 0) return rc;
                 prof.start(1, 2.0 * m * m * na);  // algorithmic: one m x m product per column
-                int np_e;
-                if (t2) {
-                    const float* ap[3] = {h->F_p[0], h->F_p[1], h->F_p[2]};
-                    const float* xp[3] = {w.Rp[0], w.Rp[1], w.Rp[2]};
-                    np_e = tc::launch(h, m, N_cur, m, ap, 3, xp, 3, tc::terms_split6(), ldm, ldm, e2, part_m, c.active);
-                } else if (tc_now) {
-                    // F_lo R is a 2^-24-relative correction: one TF32 product on
-                    // tensor cores is exact enough; F_hi R runs on the
-                    // compensated CUDA-core sweep, which adds the correction
-                    const float* ap[1] = {h->F_lo};
-                    const float* xp[1] = {w.R};
-                    const int rc_lo = tc::launch(h, m, N_cur, m, ap, 1, xp, 1, tc::terms_single(), ldm, ldm,
-                                                 EpiStorePanel{w.Ylo, c.active, ldm}, nullptr, c.active);
-                    if (rc_lo < 0) return rc_lo;
-                    np_e = launch_sweep(h, m, N_cur, m, h->F, ldm, w.R, ldm, EpiAddPanel<EpiDalmY>{w.Ylo, ldm, e2},
-                                        part_m, c.active);
-                } else {
-                    np_e = launch_sweep(h, m, N_cur, m, h->F, ldm, w.R, ldm, e2, part_m, c.active, h->F_lo);
-                }
+                const int np_e = launch_sweep(h, m, N_cur, m, h->F, ldm, w.R, ldm, e2, part_m, c.active, h->F_lo);
                 prof.stop();
                 if (np_e < 0) return np_e;
                 prof.start(2, 2.0 * m * n * na);
                 int np_x;
-                if (t3) {
-                    const float* ap[2] = {h->A_cm_p[0], h->A_cm_p[1]};
-                    const float* xp[2] = {w.Yp[0], w.Yp[1]};
-                    np_x = tc::launch(h, n, N_cur, m, ap, 2, xp, 2, tc::terms_split3(), ldm, ldm, e3, part_n, c.active);
-                } else if (lowp_now) {
-                    np_x = sweep_lowp(h, false, n, N_cur, m, P->Y, ldm, e3, part_n, c.active);
-                } else {
-                    np_x = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, P->Y, ldm, e3, part_n, c.active);
-                }
+                if (lowp_now) np_x = sweep_lowp(h, false, n, N_cur, m, P->Y, ldm, e3, part_n, c.active);
+                else np_x = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, P->Y, ldm, e3, part_n, c.active);
                 prof.stop();
                 if (np_x < 0) return np_x;
                 ctrl_dalm_kernel<<<N_cur, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e, part_n, np_x, tol, max_iter);
@@ -570,7 +630,9 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
         }
         return L1_OK;
         };
-        if (h->use_tc) {
+        if (tc_mode) {
+            // the tensor-core sweeps run directly (a chunk of them takes
+            // milliseconds; launch overhead does not matter)
             L1_TRY(run_chunk(s));
         } else {
             // capture the chunk once (on the private stream, so that the
@@ -641,11 +703,23 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                 fill_i32_kernel<<<(N_cur + 255) / 256, 256, 0, s>>>(c.active, N_cur, 0);
                 L1_LAUNCH_CHECK(h);
             }
+            // retiring slots of a tensor-core set go home in the CUDA-core form
+            if (tc_mode) L1_TRY(tc_to_simt(h, *P, c, N_cur, cab, true));
             int cnt = 0;
             L1_TRY(compact(h, q, N_cur, solver, xi_max, &cnt));
             q ^= 1;
             N_cur = cnt;
-            pieces_valid = false;
+            if (tc_mode && !done && N_cur > 0) {
+                const PanelSet& Pn = w.ps[q];
+                if (N_cur < tc_min) {
+                    // too narrow for the tensor-core tiles: continue on the
+                    // CUDA-core sweeps from the equivalent state
+                    L1_TRY(tc_to_simt(h, Pn, make_cols(h, q, N_cur), N_cur, cab, false));
+                    tc_mode = false;
+                } else {
+                    L1_TRY(tc16::split_aligned_lines(h, Pn.Ux, nullptr, N_cur, n, ldn, w.Vh, tcp));
+                }
+            }
         }
         if (done && lowp && phase == 1 && o.refine >= 0) {
             // refinement: reload every column's state (w, z - w/beta, y) from
@@ -667,6 +741,8 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
             refine_restart_kernel<<<(N + 255) / 256, 256, 0, s>>>(c, hr1.status, hr1.iters, iters1, N);
             L1_LAUNCH_CHECK(h);
             N_cur = N;
+            tc_mode = h->use_tc && solver == L1_DALM && N_cur >= tc_min;
+            if (tc_mode) L1_TRY(dalm_restart(h, *P, c, N_cur, cab, true, true, part_n, tcp));
             continue;
         }
         if (done) break;

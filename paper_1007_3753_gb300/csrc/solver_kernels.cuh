@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dalm_tc.cuh"
 #include "gemm_simt.cuh"
 
 namespace l1 {
@@ -62,22 +63,6 @@ __device__ __forceinline__ float xi_for_phase(int ph, float xi, float growth, fl
 // z_{k+1} - w_k/beta, so the right-hand side of Eq. 39 is
 //   B z_{k+1} - (B w_k - b)/beta = A U_x (+ U_e) + b/beta.
 
-// TF32 pieces of a value for the tensor-core sweeps that read the panel
-// next (see tc.cuh); p[k] may be null (pieces not needed).
-struct Pieces {
-    float* p[3];
-    __device__ __forceinline__ void store(int64_t o, float v) const {
-        if (!p[0]) return;
-        // round-to-nearest TF32 pieces (unbiased remainders), v == a + b + (r - b)
-        const float a = __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
-        const float r = v - a;
-        const float b = __uint_as_float((__float_as_uint(r) + 0x1000u) & 0xFFFFE000u);
-        p[0][o] = a;
-        p[1][o] = b;
-        if (p[2]) p[2][o] = r - b;
-    }
-};
-
 // G1: R = A U_x (+ U_e) + b / beta
 struct EpiDalmRhs {
     static constexpr int NRED = 0;
@@ -88,14 +73,12 @@ struct EpiDalmRhs {
     const int32_t* active;
     int64_t ldm;
     int cab;
-    Pieces pc;
     __device__ void operator()(int i, int j, float acc, double*) const {
         if (!active[j]) return;
         const int64_t o = (int64_t)j * ldm + i;
         float v = fmaf(B[o], binv[j], acc);
         if (cab) v += Ue[o];
         R[o] = v;
-        pc.store(o, v);
     }
 };
 
@@ -113,12 +96,10 @@ struct EpiDalmY {
     const int32_t* active;
     int64_t ldm;
     int cab;
-    Pieces pc;
     __device__ void operator()(int i, int j, float acc, double* red) const {
         if (!active[j]) return;
         const int64_t o = (int64_t)j * ldm + i;
         Y[o] = acc;
-        pc.store(o, acc);
         if (!cab) return;
         const float bi = binv[j], be = beta[j];
         const float we = We[o];
@@ -133,30 +114,6 @@ struct EpiDalmY {
     }
 };
 
-// Store a sweep's result (active columns only): out = acc.
-struct EpiStorePanel {
-    static constexpr int NRED = 0;
-    float* out;
-    const int32_t* active;
-    int64_t ld;
-    __device__ void operator()(int i, int j, float acc, double*) const {
-        if (active[j]) out[(int64_t)j * ld + i] = acc;
-    }
-};
-
-// Add a panel to the accumulator before an inner epilogue: the y-step as
-// (F_hi R) + (F_lo R) with the two products from different sweeps.
-template <class E>
-struct EpiAddPanel {
-    static constexpr int NRED = E::NRED;
-    const float* add;
-    int64_t ld;
-    E inner;
-    __device__ void operator()(int i, int j, float acc, double* red) const {
-        inner(i, j, acc + add[(int64_t)j * ld + i], red);
-    }
-};
-
 // G3: s = A^T y_{k+1}; the x-part of the w-step and the next z - w/beta.
 // red: ||dw_x||^2, ||w_x||^2.
 struct EpiDalmS {
@@ -167,7 +124,6 @@ struct EpiDalmS {
     const float* binv;
     const int32_t* active;
     int64_t ldn;
-    Pieces pc;
     __device__ void operator()(int i, int j, float acc, double* red) const {
         if (!active[j]) return;
         const int64_t o = (int64_t)j * ldn + i;
@@ -180,11 +136,68 @@ struct EpiDalmS {
         const float wb = wn * bi;
         const float u = clamp_unit(acc + wb) - wb;
         Ux[o] = u;
-        pc.store(o, u);
         red[0] += (double)dw * dw;
         red[1] += (double)w * w;
     }
 };
+
+// The state of the tensor-core engine (V, Z) -> the state of the CUDA-core
+// sweeps (U = z - w/beta = Z - W/beta), in place: the active slots, or with
+// inactive_only the frozen ones (before they are written home).
+__global__ void tc_state_to_simt_kernel(float* U, const float* Z, const float* W, const float* binv,
+                                        const int32_t* active, int64_t ld, int rows, int inactive_only) {
+    const int j = blockIdx.y;
+    if ((active[j] != 0) == (inactive_only != 0)) return;
+    const float bi = binv[j];
+    const int64_t o = (int64_t)j * ld;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x)
+        U[o + i] = Z[o + i] - W[o + i] * bi;
+}
+
+// DALM state from (w, y) with acc = (A^T y)_j (a warm start, or the restart
+// of a refinement phase): z = clamp(acc + w/beta) -- or, with have_u, the
+// carried U gives z = U + w/beta -- then U = z - w/beta in place, or for the
+// tensor-core engine (tc) Z = z and V = z - (acc + w/beta) in U's place.
+__device__ __forceinline__ void dalm_restart_elem(float* U, float* Z, float w, float bi, float acc, int64_t o,
+                                                  int have_u, int tc) {
+    const float wb = w * bi;
+    const float z = have_u ? U[o] + wb : clamp_unit(acc + wb);
+    if (tc) {
+        Z[o] = z;
+        U[o] = z - (acc + wb);
+    } else {
+        U[o] = z - wb;
+    }
+}
+
+struct EpiDalmRestart {
+    static constexpr int NRED = 0;
+    float* Ux;
+    float* Zx;
+    const float* Wx;
+    const float* binv;
+    const int32_t* active;
+    int64_t ldn;
+    int have_u;
+    int tc;
+    __device__ void operator()(int i, int j, float acc, double*) const {
+        if (!active[j]) return;
+        const int64_t o = (int64_t)j * ldn + i;
+        dalm_restart_elem(Ux, Zx, Wx[o], binv[j], acc, o, have_u, tc);
+    }
+};
+
+// the e-part of the same (B^T y there is y itself)
+__global__ void dalm_restart_e_kernel(float* Ue, float* Ze, const float* We, const float* Y, const float* binv,
+                                      const int32_t* active, int64_t ldm, int m, int have_u, int tc) {
+    const int j = blockIdx.y;
+    if (!active[j]) return;
+    const float bi = binv[j];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int64_t o = (int64_t)j * ldm + i;
+        dalm_restart_elem(Ue, Ze, We[o], bi, Y[o], o, have_u, tc);
+    }
+}
 
 // ------------------------------------------------------------ PALM epilogues
 // Algorithm 1 (§V-A) as a per-column state machine over two sweeps per inner

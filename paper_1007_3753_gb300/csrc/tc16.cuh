@@ -1,0 +1,128 @@
+// Host side of the BF16 tcgen05 sweeps (gemm_bf16.cuh): tensor maps of the
+// BF16 operand pieces, cached per handle, and the launch.
+#pragma once
+
+#include "common.cuh"
+#include "gemm_bf16.cuh"
+#include "tc.cuh"
+#include "tcgen05.cuh"
+
+namespace l1 {
+namespace tc16 {
+
+// BF16 operand pieces of one sweep: K-major A pieces (row pitch lda
+// elements), K-major X pieces (column pitch ldx elements).
+struct Operands {
+    const __nv_bfloat16* a[kMaxPieces];
+    int npa;
+    const __nv_bfloat16* x[kMaxPieces];
+    int npx;
+    int64_t lda, ldx;
+};
+
+// Term lists: which piece products a sweep issues (i-th term a_{ia} x_{ix}).
+inline Terms terms_1x1() { return Terms{1, {0}, {0}}; }
+// x split in two or three pieces, a single (BF16) A: a0 x0 + a0 x1 (+ a0 x2)
+inline Terms terms_1xN(int npx) {
+    Terms t{npx, {0, 0, 0}, {0, 1, 2}};
+    return t;
+}
+// 16-bit products: a0 x0 + a0 x1 + a1 x0
+inline Terms terms_2x2() { return Terms{3, {0, 0, 1}, {0, 1, 0}}; }
+// FP32-level products of three-piece operands: every term of order <= 2^-16
+inline Terms terms_3x3() { return Terms{6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 2, 1, 0}}; }
+// three-piece A, two-piece x: a0 x0 + a0 x1 + a1 x0 + a1 x1 + a2 x0
+inline Terms terms_3x2() { return Terms{5, {0, 0, 1, 1, 2}, {0, 1, 0, 1, 0}}; }
+
+inline int get_maps(Handle* h, int M, int N, int K, const Operands& op, int bn, Maps* out) {
+    std::array<uint64_t, 16> key{};
+    key[0] = (uint64_t)M | ((uint64_t)N << 32);
+    key[1] = (uint64_t)K | ((uint64_t)op.npa << 32) | ((uint64_t)op.npx << 40) | ((uint64_t)bn << 48) |
+             (uint64_t)0xB0ull << 56;  // BF16 maps
+    key[2] = (uint64_t)op.lda;
+    key[3] = (uint64_t)op.ldx;
+    for (int p = 0; p < op.npa; ++p) key[4 + p] = reinterpret_cast<uint64_t>(op.a[p]);
+    for (int p = 0; p < op.npx; ++p) key[8 + p] = reinterpret_cast<uint64_t>(op.x[p]);
+    for (const auto& e : h->map_cache) {
+        if (e.key == key) {
+            for (int p = 0; p < op.npa; ++p) out->a[p] = e.maps[p];
+            for (int p = 0; p < op.npx; ++p) out->x[p] = e.maps[op.npa + p];
+            return L1_OK;
+        }
+    }
+    std::memset(out, 0, sizeof(*out));
+    for (int p = 0; p < op.npa; ++p)
+        L1_TRY(tc::make_map_bf16(&out->a[p], op.a[p], (uint64_t)K, (uint64_t)M, (uint64_t)op.lda * 2, kBM));
+    for (int p = 0; p < op.npx; ++p)
+        L1_TRY(tc::make_map_bf16(&out->x[p], op.x[p], (uint64_t)K, (uint64_t)N, (uint64_t)op.ldx * 2, bn));
+    Handle::MapCacheEntry e;
+    e.key = key;
+    for (int p = 0; p < op.npa; ++p) e.maps.push_back(out->a[p]);
+    for (int p = 0; p < op.npx; ++p) e.maps.push_back(out->x[p]);
+    if (h->map_cache.size() > 64) h->map_cache.erase(h->map_cache.begin());
+    h->map_cache.push_back(std::move(e));
+    return L1_OK;
+}
+
+// One BF16 tensor-core sweep sum_t a_{ia(t)} x_{ix(t)} with epilogue epi
+// (gemm_bf16.cuh): operands split on the aligned grid of 128-element K
+// blocks, exactly one leading term (0, 0); the functor returns the value
+// that goes to the piece sink po (po.np = 0: none).  Returns the number of
+// row blocks (partials per column) or a negative error code.
+template <class E, int NPA, int NPX>
+int launch_inst(Handle* h, const Maps& maps, const Terms& tl, int M, int N, int K, const E& epi,
+                 const PieceOut& po, double* part, const int32_t* active) {
+    using S = Cfg<128, NPA, NPX>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        L1_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<E, NPA, NPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         S::kBytes));
+        attr_set = true;
+    }
+    dim3 grid((N + 127) / 128, (M + kBM - 1) / kBM);
+    sweep_kernel<E, NPA, NPX><<<grid, kThreads, S::kBytes, h->stream>>>(maps, tl, M, N, K, epi, po, part, active,
+                                                                          h->tc_err);
+    L1_LAUNCH_CHECK(h);
+    return (int)grid.y;
+}
+
+// Piece counts (npa, npx) a launch may use: square splits of two or three
+// pieces, and one-piece A with a two- or three-piece panel.
+template <class E>
+int launch(Handle* h, int M, int N, int K, const Operands& op, const Terms& tl, const E& epi, const PieceOut& po,
+           double* part, const int32_t* active) {
+    if (tl.n < 1 || tl.n > kMaxTerms) return L1_ERR_INVALID_ARG;
+    int nhi = 0;
+    for (int t = 0; t < tl.n; ++t) {
+        if (tl.ia[t] < 0 || tl.ia[t] >= op.npa || tl.ix[t] < 0 || tl.ix[t] >= op.npx) return L1_ERR_INVALID_ARG;
+        nhi += (tl.ia[t] | tl.ix[t]) == 0;
+    }
+    if (nhi != 1) return L1_ERR_INVALID_ARG;  // exactly one leading term a_0 x_0
+    if ((op.lda & 7) || (op.ldx & 7) || po.np < 0 || po.np > kMaxPieces || (po.np > 0 && (po.ld < M)))
+        return L1_ERR_INVALID_ARG;
+    Maps maps;
+    L1_TRY(get_maps(h, M, N, K, op, 128, &maps));
+    switch (op.npa * 10 + op.npx) {
+        case 12: return launch_inst<E, 1, 2>(h, maps, tl, M, N, K, epi, po, part, active);
+        case 13: return launch_inst<E, 1, 3>(h, maps, tl, M, N, K, epi, po, part, active);
+        case 22: return launch_inst<E, 2, 2>(h, maps, tl, M, N, K, epi, po, part, active);
+        case 33: return launch_inst<E, 3, 3>(h, maps, tl, M, N, K, epi, po, part, active);
+        default: return L1_ERR_UNSUPPORTED;
+    }
+}
+
+inline int row_blocks(int M) { return (M + kBM - 1) / kBM; }
+
+// Aligned pieces (split_aligned, 128-element blocks along K) of `lines`
+// lines of K elements, `ld` apart: the value is hi (+ lo, an FP32 pair,
+// nullable); p[0 .. np) receive the pieces with the same layout.
+int split_aligned_lines(Handle* h, const float* hi, const float* lo, int64_t lines, int K, int64_t ld,
+                        __nv_bfloat16* const* p, int np);
+
+// Three pieces of both layouts of A (h->A_rm_h, h->A_cm_h) and of
+// (B B^T)^{-1} = F + F_lo (h->F_h).
+int make_dictionary_pieces(Handle* h);
+int make_factor_pieces(Handle* h);
+
+}  // namespace tc16
+}  // namespace l1

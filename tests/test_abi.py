@@ -83,7 +83,7 @@ def test_host_side_argument_checks(lib):
     assert lib.l1_setup(A.ctypes.data, 4, 8, 4, l1.CAB, C.byref(o), C.byref(h)) == l1.ERR_INVALID_ARG
     assert not h.value
     res = (l1.Result * 1)()
-    assert lib.l1_solve_batch(None, None, 4, 1, 1e-6, 10, None, 8, None, 0, res) == l1.ERR_INVALID_ARG
+    assert lib.l1_solve_batch(None, None, 4, 1, 1e-6, 10, None, 8, None, 0, res, None, 0, None, 0) == l1.ERR_INVALID_ARG
     assert lib.l1_backward(None, None, 1, None, None) == l1.ERR_INVALID_ARG
     assert lib.l1_destroy(None) == l1.OK
     assert lib.l1_status_string(l1.ERR_NOT_SPD) == b"L1_ERR_NOT_SPD"
@@ -107,8 +107,13 @@ def test_refused_combinations_before_any_cuda_call(lib):
     U, I = l1.ERR_UNSUPPORTED, l1.ERR_INVALID_ARG
     assert setup(l1.P1_2, solver=l1.DALM, epsilon=0.1) == U      # R10 is a PALM
     assert setup(l1.P1_2, solver=l1.PALM, epsilon=0.0) == I      # no radius
-    for kw in (dict(solver=l1.PALM), dict(engine=l1.ENGINE_TC), dict(unroll_K=5, solver=l1.PALM)):
+    for kw in (dict(solver=l1.PALM), dict(unroll_K=5, solver=l1.PALM)):
         assert setup(l1.CAB, precision=l1.A_BF16, **kw) == U, kw  # low precision: batched DALM only
+    assert setup(l1.CAB, precision=l1.A_FP8E4M3, engine=l1.ENGINE_TC) == U  # FP8: CUDA-core sweeps only
+    assert setup(l1.CAB, engine=l1.ENGINE_TC, tc_pieces=1) == U       # a one-piece panel cannot converge
+    assert setup(l1.CAB, engine=l1.ENGINE_TC, tc_pieces_y=1) == U
+    assert setup(l1.CAB, engine=l1.ENGINE_TC, tc_pieces=4) == I
+    assert setup(l1.CAB, engine=l1.ENGINE_TC, tc_min_cols=-1) == I
     assert setup(l1.QP_LAMBDA, precision=l1.A_FP8E4M3, lambda_=0.1) == U
     assert setup(l1.CAB, solver=l1.PALM, engine=l1.ENGINE_TC) == U
     assert setup(l1.QP_LAMBDA, engine=l1.ENGINE_TC, lambda_=0.1) == U

@@ -61,12 +61,13 @@ def test_lowp_refined_exact_recovery(l1, prec):
     assert min(errs_raw) > 10 * X_TOL
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "bf16-tc"])
 def test_lowp_cab_labels_match_oracle(l1, prec):
-    p = l1.A_BF16 if prec == "bf16" else l1.A_FP8E4M3
+    p = l1.A_FP8E4M3 if prec == "fp8" else l1.A_BF16
+    eng = dict(engine=l1.ENGINE_TC, tc_min_cols=1) if prec == "bf16-tc" else {}
     pr = synthetic.cab_problem(256, 8, 12, 24, corrupt=0.3, seed=1300)
     A, B, off = pr["A"], pr["B"].astype(np.float32), pr["offsets"]
-    s = l1.Solver(A, mode=l1.CAB, solver=l1.DALM, class_offsets=off, precision=p)
+    s = l1.Solver(A, mode=l1.CAB, solver=l1.DALM, class_offsets=off, precision=p, **eng)
     x, _, res = s.solve(B, tol=1e-4, max_iter=20000)
     assert np.all(res["status"] == l1.CONVERGED)
     worst = 0.0
@@ -84,8 +85,10 @@ def test_lowp_cab_labels_match_oracle(l1, prec):
 
 def test_lowp_rejected_where_unsupported(l1):
     A = synthetic.gaussian_dictionary(16, 32, synthetic.rng(2))
-    for kw in (dict(mode=l1.CAB, solver=l1.PALM), dict(mode=l1.QP_LAMBDA, solver=l1.PALM, lam=0.1),
-               dict(mode=l1.CAB, solver=l1.DALM, engine=l1.ENGINE_TC)):
+    for kw in (dict(mode=l1.CAB, solver=l1.PALM), dict(mode=l1.QP_LAMBDA, solver=l1.PALM, lam=0.1)):
         with pytest.raises(l1.L1Error) as e:
             l1.Solver(A, precision=l1.A_BF16, **kw)
         assert e.value.code == l1.ERR_UNSUPPORTED
+    with pytest.raises(l1.L1Error) as e:
+        l1.Solver(A, mode=l1.CAB, solver=l1.DALM, precision=l1.A_FP8E4M3, engine=l1.ENGINE_TC)
+    assert e.value.code == l1.ERR_UNSUPPORTED

@@ -3,10 +3,17 @@
 Tolerances (stated by the task for floating point):
   ||x - x_oracle|| / ||x_oracle|| <= 1e-4, objective relative error <= 1e-5,
   class labels identical.
-The iterations are compared at the oracle's stopping tolerance, or -- where
-the relative-change rule hovers near tol and a one-step difference in the
-stopping iteration would dominate -- after the same number of iterations
-(tol = 0 runs exactly max_iter iterations on both sides).
+Two kinds of comparison:
+  * after the same number of iterations (tol = 0 runs exactly max_iter
+    iterations on both sides): the trajectories agree;
+  * at the stopping tolerance (check_at_tolerance): every sampled column is
+    compared, none is left out.  The relative-change rule fixes the answer only
+    up to the iteration at which it fires, and one iteration moves w by
+    rel_change * ||w|| (just below tol * ||w||), so two correct runs whose
+    rounding differs can stop one iteration apart.  Each GPU column must stop
+    within one iteration of the oracle's own stop, and its x must agree with
+    the oracle's iterate at the GPU's stopping iteration to the tolerances
+    above.
 """
 import concurrent.futures as cf
 
@@ -70,6 +77,26 @@ class Errs:
         assert xs.max() <= X_TOL and os_.max() <= OBJ_TOL, msg
 
 
+def check_at_tolerance(what, res, x, cols, run_oracle, max_stop_diff=1):
+    """The at-tolerance parity check described above.  run_oracle(j, tol_on,
+    iters) runs the oracle on column j: with tol_on at the solve's tol (and
+    its max_iter), else exactly `iters` iterations; it returns (w, stats)."""
+    first = _pmap(lambda j: run_oracle(j, True, 0), cols)
+    need = [(k, j) for k, (j, (w, st)) in enumerate(zip(cols, first)) if res["iters"][j] != st["iters"]]
+    again = dict(zip([k for k, _ in need],
+                     _pmap(lambda kj: run_oracle(kj[1], False, int(res["iters"][kj[1]])), need)))
+    ex = Errs(what)
+    stops = []
+    for k, (j, (w, st)) in enumerate(zip(cols, first)):
+        stops.append(int(res["iters"][j]) - int(st["iters"]))
+        w_at = again[k][0] if k in again else w
+        ex.add(x[:, j], w_at, res["primal_obj"][j])
+    print(f"{what}: GPU stop - oracle stop per column {stops}")
+    assert max(abs(d) for d in stops) <= max_stop_diff, stops
+    ex.check()
+    return first
+
+
 # ------------------------------------------------------------ CAB (Eq. 5)
 
 @pytest.mark.parametrize("N", [1, 5, 37])
@@ -105,17 +132,13 @@ def test_cab_dalm_matches_oracle_at_tolerance(l1):
     s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off)
     x, _, res = s.solve(_dev(B), tol=tol, max_iter=20000)
     x = x.cpu().numpy()
-    outs = _pmap(lambda j: oracle.dalm(A, B[:, j], cab=True, tol=tol, max_iter=20000), range(24))
-    same = 0
-    ex = Errs("CAB DALM at tol 1e-3")
-    for j, (w, yo, st) in enumerate(outs):
-        assert res["status"][j] == l1.CONVERGED
-        assert abs(res["iters"][j] - st["iters"]) <= 2, (j, res["iters"][j], st["iters"])
-        if res["iters"][j] == st["iters"]:
-            same += 1
-            ex.add(x[:, j], w, res["primal_obj"][j])
-    ex.check()
-    assert same >= 20
+    assert np.all(res["status"] == l1.CONVERGED)
+
+    def run(j, tol_on, iters):
+        w, _, st = oracle.dalm(A, B[:, j], cab=True, tol=tol if tol_on else 0.0,
+                               max_iter=20000 if tol_on else iters)
+        return w, st
+    check_at_tolerance("CAB DALM at tol 1e-3", res, x, list(range(24)), run)
     s.close()
 
 
@@ -243,64 +266,113 @@ def test_edge_cases(l1):
 # ------------------------------------- the benchmarked launch configuration
 
 def test_bench_configuration_sampled_against_oracle(l1):
-    """Full 1024 x 1200 (+I) cross-and-bouquet batch of 1024 right-hand sides,
-    solved exactly as bench.py times it; a sample of columns is checked
-    against the oracle run one by one at the same tolerance."""
+    """Full 1024 x 1200 (+I) cross-and-bouquet batch of 1024 right-hand sides
+    on the CUDA-core sweeps at the stopping tolerance; a sample of columns is
+    checked against the oracle run one by one (every sampled column)."""
     import bench
-    cfg = bench.BENCH
-    p = bench.workload(0)
+    cfg = bench.CAB1024
+    p = bench.cab_workload(cfg)
     A, B, off = p["A"], p["B"], p["offsets"]
     n = A.shape[1]
-    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off)
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=l1.ENGINE_SIMT)
     x, _, res = s.solve(_dev(B), tol=cfg["tol"], max_iter=cfg["max_iter"])
     x = x.cpu().numpy()
     assert np.mean(res["status"] == l1.CONVERGED) >= 0.99
     sample = [0, 1, 2, 3, 511, 767, 1022, 1023]
-    outs = _pmap(lambda j: oracle.dalm(A, B[:, j], cab=True, tol=cfg["tol"], max_iter=cfg["max_iter"]),
-                 sample)
-    ex = Errs("bench configuration sample")
-    for j, (w, yo, st) in zip(sample, outs):
-        assert abs(res["iters"][j] - st["iters"]) <= 2, (j, res["iters"][j], st["iters"])
-        if res["iters"][j] == st["iters"]:
-            ex.add(x[:, j], w, res["primal_obj"][j])
+
+    def run(j, tol_on, iters):
+        w, _, st = oracle.dalm(A, B[:, j], cab=True, tol=cfg["tol"] if tol_on else 0.0,
+                               max_iter=cfg["max_iter"] if tol_on else iters)
+        return w, st
+    first = check_at_tolerance("bench configuration sample (CUDA cores)", res, x, sample, run)
+    for j, (w, st) in zip(sample, first):
         lab, slab, r, _ = oracle.classify(A, off, B[:, j], w[:n], w[n:])
         assert res["label"][j] == lab and res["sci_label"][j] == slab
-    ex.check()
     s.close()
 
 
 # ------------------------------------------------ tensor-core (tcgen05) engine
 
-@pytest.mark.parametrize("N", [40, 100])
-def test_cab_dalm_tensor_core_engine_matches_oracle(l1, N):
-    """Split-TF32 tcgen05 sweeps (ragged M tiles: 256 and 300 rows; ragged
-    64-column N tiles) against the FP64 oracle after a fixed iteration count."""
+@pytest.mark.parametrize("N,pieces", [(40, 3), (200, 3), (200, 2)])
+def test_cab_dalm_tensor_core_engine_matches_oracle(l1, N, pieces):
+    """BF16 tcgen05 sweeps (A and the panels as aligned BF16 pieces, the
+    leading product summed exactly) against the FP64 oracle after a fixed
+    iteration count: ragged M tiles (256 and 300 rows), a ragged 128-column
+    tile, two tiles; three pieces (FP32-level) and two (16-bit) per operand."""
     p = synthetic.cab_problem(256, 10, 30, N, seed=21)
     A, B, off = p["A"], p["B"], p["offsets"]
     n = A.shape[1]
     iters = 300
-    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=l1.ENGINE_TC)
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=l1.ENGINE_TC,
+                  tc_min_cols=1, tc_pieces=pieces, tc_pieces_y=pieces)
     x, y, res = s.solve(_dev(B), tol=0.0, max_iter=iters, want_y=True)
     x = x.cpu().numpy()
     y = y.cpu().numpy()
     assert np.all(res["iters"] == iters)
     cols = list(range(0, N, max(1, N // 12)))
     outs = _pmap(lambda j: oracle.dalm(A, B[:, j], cab=True, tol=0.0, max_iter=iters), cols)
-    ex, ey = Errs(f"TC CAB DALM N={N} x"), Errs(f"TC CAB DALM N={N} y")
+    ex, ey = Errs(f"TC CAB DALM N={N} pieces={pieces} x"), Errs(f"TC CAB DALM N={N} pieces={pieces} y")
     for j, (w, yo, st) in zip(cols, outs):
         ex.add(x[:, j], w, res["primal_obj"][j])
         ey.add(y[:, j], yo)
         lab, slab, r, _ = oracle.classify(A, off, B[:, j], w[:n], w[n:])
         assert res["label"][j] == lab and res["sci_label"][j] == slab
+    if pieces == 3:
+        ex.check()
+        ey.check()
+    else:
+        # 16-bit products: reported, and held to a looser bound
+        print(f"two pieces: x err max {max(ex.x):.2e}, y err max {max(ey.x):.2e}")
+        assert max(ex.x) <= 1e-2
+    s.close()
+
+
+def test_p1_dalm_tensor_core_engine_matches_oracle(l1):
+    """P1 (B = A, no identity block) on the tensor-core engine."""
+    pr = synthetic.p1_instance(200, 400, 20, seed=3)
+    A = pr["A"]
+    g = np.random.default_rng(0)
+    B = np.stack([A @ np.where(g.random(400) < 0.05, g.standard_normal(400), 0) for _ in range(19)], 1)
+    iters = 80
+    s = l1.Solver(_dev(A), mode=l1.P1, solver=l1.DALM, engine=l1.ENGINE_TC, tc_min_cols=1)
+    x, _, res = s.solve(_dev(B), tol=0.0, max_iter=iters)
+    x = x.cpu().numpy()
+    ex = Errs("TC P1 DALM")
+    for j in range(19):
+        w, _, _ = oracle.dalm(A, B[:, j], cab=False, tol=0.0, max_iter=iters)
+        ex.add(x[:, j], w)
     ex.check()
-    ey.check()
+    s.close()
+
+
+def test_tensor_core_engine_at_tolerance_with_fallback(l1):
+    """At the stopping tolerance: 300 columns start on the tensor-core sweeps
+    and, as columns retire, the set falls below tc_min_cols and continues on
+    the CUDA-core sweeps (state converted); every sampled column is checked."""
+    p = synthetic.cab_problem(256, 10, 30, 300, seed=22)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    tol = 1e-3
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=l1.ENGINE_TC,
+                  tc_min_cols=160)
+    x, _, res = s.solve(_dev(B), tol=tol, max_iter=20000)
+    x = x.cpu().numpy()
+    assert np.all(res["status"] == l1.CONVERGED)
+    its = np.sort(res["iters"])
+    print("iterations: first retire", its[0], "median", its[150], "last", its[-1])
+    cols = [int(j) for j in np.argsort(res["iters"])[::25]]  # spread over early and late retirements
+
+    def run(j, tol_on, iters):
+        w, _, st = oracle.dalm(A, B[:, j], cab=True, tol=tol if tol_on else 0.0,
+                               max_iter=20000 if tol_on else iters)
+        return w, st
+    check_at_tolerance("TC engine at tol 1e-3 with fallback", res, x, cols, run)
     s.close()
 
 
 def test_bench_configuration_tensor_core_engine(l1):
     import bench
-    cfg = bench.BENCH
-    p = bench.workload(0)
+    cfg = bench.CAB1024
+    p = bench.cab_workload(cfg)
     A, B, off = p["A"], p["B"], p["offsets"]
     n = A.shape[1]
     s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=l1.ENGINE_TC)
@@ -309,15 +381,61 @@ def test_bench_configuration_tensor_core_engine(l1):
     assert np.mean(res["status"] == l1.CONVERGED) >= 0.99
     assert np.mean(res["label"] == p["labels"]) >= 0.99
     sample = [0, 5, 600, 1023]
-    outs = _pmap(lambda j: oracle.dalm(A, B[:, j], cab=True, tol=cfg["tol"], max_iter=cfg["max_iter"]),
-                 sample)
-    ex = Errs("TC bench configuration sample")
-    for j, (w, yo, st) in zip(sample, outs):
-        assert abs(res["iters"][j] - st["iters"]) <= 2, (j, res["iters"][j], st["iters"])
-        if res["iters"][j] == st["iters"]:
-            ex.add(x[:, j], w, res["primal_obj"][j])
+
+    def run(j, tol_on, iters):
+        w, _, st = oracle.dalm(A, B[:, j], cab=True, tol=cfg["tol"] if tol_on else 0.0,
+                               max_iter=cfg["max_iter"] if tol_on else iters)
+        return w, st
+    first = check_at_tolerance("TC bench configuration sample", res, x, sample, run)
+    for j, (w, st) in zip(sample, first):
         lab, slab, r, _ = oracle.classify(A, off, B[:, j], w[:n], w[n:])
         assert res["label"][j] == lab
+    s.close()
+
+
+# ------------------------------------------------------------ warm start
+
+@pytest.mark.parametrize("engine", ["simt", "tc"])
+def test_dalm_warm_start_continues_the_iteration(l1, engine):
+    """A DALM solve stopped after k1 iterations and resumed from its (x, y)
+    for k2 more equals k1 + k2 iterations of the oracle (and of an
+    uninterrupted solve)."""
+    p = synthetic.cab_problem(256, 10, 30, 140, seed=31)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    eng = dict(engine=l1.ENGINE_TC, tc_min_cols=1) if engine == "tc" else dict(engine=l1.ENGINE_SIMT)
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, **eng)
+    k1, k2 = 120, 80
+    x1, y1, _ = s.solve(_dev(B), tol=0.0, max_iter=k1, want_y=True)
+    x2, y2, r2 = s.solve(_dev(B), tol=0.0, max_iter=k2, want_y=True, x_init=x1, y_init=y1)
+    xf, _, _ = s.solve(_dev(B), tol=0.0, max_iter=k1 + k2)
+    x2, xf = x2.cpu().numpy(), xf.cpu().numpy()
+    cols = [0, 7, 70, 139]
+    outs = _pmap(lambda j: oracle.dalm(A, B[:, j], cab=True, tol=0.0, max_iter=k1 + k2), cols)
+    ex = Errs(f"DALM warm start ({engine})")
+    for j, (w, _, _) in zip(cols, outs):
+        ex.add(x2[:, j], w, r2["primal_obj"][j])
+        assert _rel(x2[:, j], xf[:, j]) <= 1e-5
+    ex.check()
+    s.close()
+
+
+def test_palm_warm_start_continues_the_iteration(l1):
+    """CAB PALM (fixed xi) resumed from (x, e, theta) after k1 outer
+    iterations equals k1 + k2 outer iterations of the oracle."""
+    p = synthetic.cab_problem(192, 6, 30, 9, seed=32)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    L = oracle.lipschitz(A)
+    inner = 20
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.PALM, class_offsets=off, lipschitz=L, inner_max=inner)
+    k1, k2 = 5, 7
+    x1, y1, _ = s.solve(_dev(B), tol=0.0, max_iter=k1, want_y=True)
+    x2, _, r2 = s.solve(_dev(B), tol=0.0, max_iter=k2, want_y=True, x_init=x1, y_init=y1)
+    x2 = x2.cpu().numpy()
+    outs = _pmap(lambda j: oracle.palm(A, B[:, j], mode=oracle.MODE_CAB, tol=0.0, max_outer=k1 + k2,
+                                       inner_max=inner, L=L), range(9))
+    ex = Errs("PALM warm start")
+    for j, (xo, eo, th, st) in enumerate(outs):
+        ex.add(x2[:, j], np.concatenate([xo, eo]), r2["primal_obj"][j])
     ex.check()
     s.close()
 
