@@ -74,8 +74,8 @@ typedef enum {
 } l1_precision;
 
 typedef enum {
-    L1_ENGINE_AUTO = 0,  /* currently the same as L1_ENGINE_SIMT (the faster at
-                          * every measured shape) */
+    L1_ENGINE_AUTO = 0,  /* DALM (P1, CAB) with an FP32 or BF16 dictionary: L1_ENGINE_TC;
+                          * everything else: L1_ENGINE_SIMT */
     L1_ENGINE_SIMT = 1,  /* CUDA-core FP32 kernels (GEMV for N <= 8, tiled GEMM above) */
     L1_ENGINE_TC = 2     /* tcgen05 BF16 tensor-core sweeps for batched DALM: A and the
                           * panels as aligned BF16 pieces, the leading product summed
@@ -119,7 +119,10 @@ typedef struct {
     int32_t tc_pieces_y; /* L1_ENGINE_TC: BF16 pieces of (B B^T)^{-1} and of the y-step's
                           * right-hand side, 2 or 3; 0 -> 3 */
     int32_t tc_min_cols; /* L1_ENGINE_TC: the tensor-core sweeps run while at least this
-                          * many columns are active, the CUDA-core sweeps below; 0 -> 128 */
+                          * many columns are active, the CUDA-core sweeps below; 0 -> 1
+                          * (the tensor-core products track the FP64 iteration more
+                          * closely than the CUDA-core FP32 ones, so by default they
+                          * run to the last column) */
 } l1_options;
 
 /* Per-instance results (host memory). */

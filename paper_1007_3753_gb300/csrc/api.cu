@@ -181,7 +181,11 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
         }
         // tensor-core engine (batched DALM): aligned BF16 pieces of both
         // layouts of A (those of (B B^T)^{-1} follow the factor below)
-        h->use_tc = (o.engine == L1_ENGINE_TC) && o.solver == L1_DALM && mode != L1_QP_LAMBDA;
+        // (the automatic choice for DALM: its products track the FP64
+        // iteration more closely than the CUDA-core FP32 sweeps and run faster
+        // at width; FP8 dictionaries stay on the CUDA cores)
+        h->use_tc = (o.engine == L1_ENGINE_TC || (o.engine == L1_ENGINE_AUTO && o.precision != L1_A_FP8E4M3)) &&
+                    o.solver == L1_DALM && mode != L1_QP_LAMBDA && o.unroll_K == 0;
         if (h->use_tc) {
             rc = dev_alloc_t(h, &h->tc_err, 1);
             if (!rc) rc = tc16::make_dictionary_pieces(h);

@@ -18,7 +18,8 @@ namespace l1 {
 // iteration converges, so the rounding of the inverse's product shrinks with
 // it.  V = clamp(v) - v with v = B^T y_k + w_k/beta.  Panels: V_x (FP32 and
 // BF16 pieces), V_e, Z = z_{k+1}, W, Y.  Each functor returns the value whose
-// BF16 pieces the next sweep reads (0 for frozen columns).
+// BF16 pieces the next sweep reads (0 for frozen columns); its per-column
+// reduction terms are FP32 (summed over 32 rows in FP32, above that in FP64).
 
 // T1 (rows of A, acc = A V_x): d = acc (+ V_e) + b / beta
 struct EpiTcD {
@@ -29,7 +30,7 @@ struct EpiTcD {
     const int32_t* active;
     int64_t ldm;
     int cab;
-    __device__ float operator()(int i, int j, float acc, double*) const {
+    __device__ float operator()(int i, int j, float acc, float*) const {
         if (!active[j]) return 0.0f;
         const int64_t o = (int64_t)j * ldm + i;
         float d = fmaf(B[o], binv[j], acc);
@@ -53,7 +54,7 @@ struct EpiTcY {
     const int32_t* active;
     int64_t ldm;
     int cab;
-    __device__ float operator()(int i, int j, float acc, double* red) const {
+    __device__ float operator()(int i, int j, float acc, float* red) const {
         if (!active[j]) return 0.0f;
         const int64_t o = (int64_t)j * ldm + i;
         const float y = Y[o] + acc;
@@ -67,8 +68,8 @@ struct EpiTcY {
             const float z = clamp_unit(v);
             Ze[o] = z;
             Ve[o] = z - v;
-            red[0] += (double)dw * dw;
-            red[1] += (double)we * we;
+            red[0] += dw * dw;
+            red[1] += we * we;
         }
         return y;
     }
@@ -86,7 +87,7 @@ struct EpiTcS {
     const float* binv;
     const int32_t* active;
     int64_t ldn;
-    __device__ float operator()(int i, int j, float acc, double* red) const {
+    __device__ float operator()(int i, int j, float acc, float* red) const {
         if (!active[j]) return 0.0f;
         const int64_t o = (int64_t)j * ldn + i;
         const float w = Wx[o];
@@ -98,8 +99,8 @@ struct EpiTcS {
         Zx[o] = z;
         const float vx = z - v;
         Vx[o] = vx;
-        red[0] += (double)dw * dw;
-        red[1] += (double)w * w;
+        red[0] += dw * dw;
+        red[1] += w * w;
         return vx;
     }
 };

@@ -22,9 +22,10 @@
 //               thread issues every tcgen05.mma; tcgen05.commit frees ring
 //               slots and hands each finished 128-K chunk to the epilogue
 //   warps 2..9  epilogue: warp w reads TMEM lane quarter w % 4 (32 output
-//               rows) and one half of the columns; FP32 sums of the chunks, then the functor per element, deterministic
-//               per-column reductions (one partial per row block and column)
-//               and the aligned pieces of the returned values
+//               rows) and one half of the columns; FP32 sums of the chunks,
+//               then the functor per element, deterministic per-column
+//               reductions (one partial per row block and column) and the
+//               aligned pieces of the returned values
 // Tiles whose columns are all inactive write zero partials and return.
 // Every mbarrier wait is bounded; a wait that runs out records an error code
 // in *err, the CTA leaves its loops, waits (bounded) for its own copies and
@@ -102,10 +103,10 @@ __host__ __device__ __forceinline__ float bf16_rn(float x) {
 // hi[b]; the other terms (2^-8 and smaller) go to lo[b], whose rounding is
 // 2^-8 below the result.  After every K block of 128 the epilogue drains
 // hi[b] + lo[b] into FP32 register sums (round to nearest: unbiased) while
-// the MMA warp fills the other buffer pair (b ^ 1).  Accumulating the whole K range in one TMEM
-// accumulator instead rounds every MMA toward zero (measured: a relative
-// bias of 3e-7 for one term and 2e-6 for six at K = 256), which a slowly
-// converging iteration accumulates.
+// the MMA warp fills the other buffer pair (b ^ 1).  Accumulating the whole
+// K range in one TMEM accumulator instead rounds every MMA toward zero
+// (measured: a relative bias of 3e-7 for one term and 2e-6 for six at
+// K = 256), which a slowly converging iteration accumulates.
 constexpr int kChunk = 128;            // K elements per drain (= the exponent block)
 constexpr int kKBPerChunk = kChunk / kKB;
 
@@ -137,8 +138,8 @@ __device__ __forceinline__ void split_aligned(float v, float bmax, float& p0, fl
 
 template <int BN, int NPA, int NPX>
 struct Cfg {
-    static constexpr int kATile = kBM * 128;  // 16 KB
-    static constexpr int kXTile = BN * 128;
+    static constexpr int kATile = kBM * kKB * 2;  // 16 KB
+    static constexpr int kXTile = BN * kKB * 2;
     static constexpr int kStage = NPA * kATile + NPX * kXTile;
     static constexpr int kStages = (200 * 1024 / kStage) > 6 ? 6 : (200 * 1024 / kStage);
     static_assert(kStages >= 2, "two ring stages must fit");
@@ -146,6 +147,7 @@ struct Cfg {
 };
 
 constexpr int kEpiWarps = 8;                  // two per TMEM lane quarter
+constexpr int kGroupM = 16;                   // row tiles per group of the tile order
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 template <class E, int NPA, int NPX>
@@ -179,12 +181,23 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
     static_assert(BN * kBM * 4 + 4 * BN * NR * 8 + BN * 4 <= kStages * S::kStage, "epilogue scratch");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+    // tile order: groups of kGroupM row tiles, column tiles within a group, so
+    // that the CTAs resident at one time share row panels of A and column
+    // panels of X in L2 (row-major order streams every column panel once per
+    // wave)
+    const int tiles_m = (M + kBM - 1) / kBM, tiles_n = (N + BN - 1) / BN;
+    const int per_group = kGroupM * tiles_n;
+    const int group = blockIdx.x / per_group, first_m = group * kGroupM;
+    const int gsz = min(kGroupM, tiles_m - first_m);
+    const int in_group = blockIdx.x % per_group;
+    const int tile_m = first_m + in_group % gsz, tile_n = in_group / gsz;
+    const int m0 = tile_m * kBM, n0 = tile_n * BN;
     const int kblocks = (K + kKB - 1) / kKB;
     const int nchunks = (kblocks + kKBPerChunk - 1) / kKBPerChunk;
     const int nterms = tl.n;
     bool has_lo = false;
-    for (int t = 0; t < nterms; ++t) has_lo |= (tl.ia[t] | tl.ix[t]) != 0;
+#pragma unroll
+    for (int t = 0; t < kMaxTerms; ++t) has_lo |= t < nterms && (tl.ia[t] | tl.ix[t]) != 0;
 
     if (threadIdx.x == 0) {
         flags[0] = 0;
@@ -202,7 +215,7 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
         if constexpr (E::NRED > 0) {
             for (int c = threadIdx.x; c < BN; c += blockDim.x)
                 if (n0 + c < N)
-                    for (int r = 0; r < NR; ++r) part[((int64_t)blockIdx.y * N + n0 + c) * kPartStride + r] = 0.0;
+                    for (int r = 0; r < NR; ++r) part[((int64_t)tile_m * N + n0 + c) * kPartStride + r] = 0.0;
         }
         return;
     }
@@ -284,7 +297,11 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t st = smem_u32(smem + s * S::kStage);
-                    for (int t = 0; t < nterms; ++t) {
+                    // unrolled over the term slots so that the term list is
+                    // read from the kernel parameters, not from a local copy
+#pragma unroll
+                    for (int t = 0; t < kMaxTerms; ++t) {
+                        if (t >= nterms) break;
                         const bool hi = (tl.ia[t] | tl.ix[t]) == 0;
                         const uint32_t a_addr = st + tl.ia[t] * S::kATile;
                         const uint32_t x_addr = st + NPA * S::kATile + tl.ix[t] * S::kXTile;
@@ -355,20 +372,26 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
         if (ok) {
 #pragma unroll
             for (int c = 0; c < CPT; ++c) my[(cb + c) * kBM] = sum[c];
-#pragma unroll 2
+            // unrolled so that several columns' global loads (the functor's
+            // state) are in flight at once
+#pragma unroll 8
             for (int c = 0; c < CPT; ++c) {
                 const int j = n0 + cb + c;
-                double rv[NR];
+                // per-element reduction terms and their sum over the warp's 32
+                // rows in FP32 (FP64 arithmetic runs at a small fraction of the
+                // FP32 rate on this part); the partial sums above that level
+                // are FP64, all in a fixed order
+                float rv[NR];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) rv[r] = 0.0;
+                for (int r = 0; r < NR; ++r) rv[r] = 0.0f;
                 float ret = 0.0f;
                 if (i < M && j < N) ret = epi(i, j, my[(cb + c) * kBM], rv);
                 my[(cb + c) * kBM] = ret;
                 if constexpr (E::NRED > 0) {
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
-                        const double sv = warp_sum(rv[r]);
-                        if (lane == 0) red_s[((q * BN) + cb + c) * NR + r] = sv;
+                        const float sv = warp_sum_f(rv[r]);
+                        if (lane == 0) red_s[((q * BN) + cb + c) * NR + r] = (double)sv;
                     }
                 }
             }
@@ -420,7 +443,7 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
                 if (j < N) {
                     double s = 0.0;
                     for (int qq = 0; qq < 4; ++qq) s += red_s[((qq * BN) + c) * NR + r];
-                    part[((int64_t)blockIdx.y * N + j) * kPartStride + r] = s;
+                    part[((int64_t)tile_m * N + j) * kPartStride + r] = s;
                 }
             }
         }

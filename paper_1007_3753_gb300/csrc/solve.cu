@@ -532,7 +532,7 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     int phase = 1;
     int32_t* iters1 = w.hcoli + 5 * w.cap_N;
     // tensor-core engine (batched DALM): BF16 pieces of A and the panels
-    const int tc_min = o.tc_min_cols > 0 ? o.tc_min_cols : 128;
+    const int tc_min = o.tc_min_cols > 0 ? o.tc_min_cols : 1;
     const int tcp = o.tc_pieces > 0 ? std::min(o.tc_pieces, 3) : 3;      // A sweeps
     const int tcy = o.tc_pieces_y > 0 ? std::min(o.tc_pieces_y, 3) : 3;  // y-step
     bool tc_mode = h->use_tc && solver == L1_DALM && N_cur >= tc_min;

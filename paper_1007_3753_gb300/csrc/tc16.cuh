@@ -79,11 +79,11 @@ int launch_inst(Handle* h, const Maps& maps, const Terms& tl, int M, int N, int 
                                          S::kBytes));
         attr_set = true;
     }
-    dim3 grid((N + 127) / 128, (M + kBM - 1) / kBM);
-    sweep_kernel<E, NPA, NPX><<<grid, kThreads, S::kBytes, h->stream>>>(maps, tl, M, N, K, epi, po, part, active,
-                                                                          h->tc_err);
+    const int tiles_m = (M + kBM - 1) / kBM, tiles = tiles_m * ((N + 127) / 128);
+    sweep_kernel<E, NPA, NPX><<<tiles, kThreads, S::kBytes, h->stream>>>(maps, tl, M, N, K, epi, po, part, active,
+                                                                         h->tc_err);
     L1_LAUNCH_CHECK(h);
-    return (int)grid.y;
+    return tiles_m;
 }
 
 // Piece counts (npa, npx) a launch may use: square splits of two or three
