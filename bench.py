@@ -1,19 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark of the batched cross-and-bouquet DALM solve (one JSON line).
 
-Workload (the robust-classification setting of §VI-B at the stated sizes):
-dictionary [A I] with A 1024 x 1200 = 40 classes x 30 columns, each class a
-rank-9 nonnegative subspace plus 1 % noise, unit columns; 1024 test vectors
-with 30 % of their entries replaced by uniform [0, 1] gross errors; DALM
-(Algorithm 2) in FP32, every test vector stopped by the relative-change rule
-of §VI-C at tol, then classified by the minimum per-class residual.
+Default workload (--workload cab4096; the robust-classification setting of
+§VI-B at the largest stated size): dictionary [A I] with A 4096 x 4000 =
+100 classes x 40 columns, each class a rank-9 nonnegative subspace plus 1 %
+noise, unit columns; 4096 test vectors with 30 % of their entries replaced by
+uniform [0, 1] gross errors; DALM (Algorithm 2) to the relative-change rule of
+§VI-C at tol 1e-4 on the BF16 tensor-core engine (A and the panels as three
+aligned BF16 pieces, FP32 accumulation and iterates), then classification by
+the minimum per-class residual.  --workload cab1024 is the 1024 x 1200
+(40 classes x 30 columns, 1024 test vectors) variant.
 
-A step is one l1_solve_batch over the 1024 right-hand sides (all sweeps,
-per-column stopping, finalisation and classification).  `value` counts the
-converged solves per second with the inputs resident in HBM; `e2e` repeats the
-measurement through the same C-ABI call with pinned host buffers (the copies
-in and out are inside the timed region).  L2 is flushed (a 512 MiB write)
-before every timed step; the flush is outside the step's CUDA events.
+A step is one l1_solve_batch over all right-hand sides (sweeps, per-column
+stopping, finalisation, classification).  `value` counts solves per second
+that meet the bar: the fraction of a sample of columns of the last timed solve
+verified against the FP64 oracle at the stopping tolerance (x within 1e-4 and
+the objective within 1e-5 of the oracle's iterate, the stop within one
+iteration of the oracle's, the label equal) times the columns solved.  The
+oracle answers for the m = 4096 sample are stored (tests/golden/, written by
+a script that calls only the oracle); for m = 1024 the oracle runs here.
+`e2e` repeats the solve through the same C-ABI call with pinned host buffers
+(copies inside the timed region).  L2 is flushed (a 512 MiB write) before
+every timed step, outside the step's CUDA events.
 
 --impl reference times the FP64 CPU oracle (the same algorithm, plain C) on
 the host cores on a bounded sample of the same workload.
@@ -44,7 +52,6 @@ CAB1024 = dict(m=1024, classes=40, per_class=30, N=1024, corrupt=0.3, seed=1000,
                tol=1e-4, max_iter=10000, solver="DALM")
 CAB4096 = dict(m=4096, classes=100, per_class=40, N=4096, corrupt=0.3, seed=3000,
                tol=1e-4, max_iter=10000, solver="DALM")
-BENCH = dict(CAB1024)
 
 
 def cab_workload(cfg, rank: int = 0):
@@ -57,7 +64,10 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates of the part
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-batch launch
 # (all 1024 columns active, cold cache) of each CUDA-core sweep of this
 # build, and the algorithmic bytes of that launch
-SIMT_TRAFFIC = {"A_u": (18.42e6, 18.2e6), "Finv_r": (21.12e6, 21.0e6), "At_y": (19.27e6, 19.1e6)}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-width launch of
+# the tensor-core sweeps of this build (filled from profiles/), keyed by
+# workload and sweep
+TC_TRAFFIC = {}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -82,23 +92,6 @@ def reduce_over_ranks(dist, time_value: float, count: int, device: str = "cuda")
     c = torch.tensor([count], dtype=torch.float64, device=device)
     dist.all_reduce(c, op=dist.ReduceOp.SUM)
     return float(t.item()), int(c.item())
-
-
-def workload(rank: int = 0):
-    return synthetic.cab_problem(BENCH["m"], BENCH["classes"], BENCH["per_class"], BENCH["N"],
-                                 corrupt=BENCH["corrupt"], seed=BENCH["seed"] + rank)
-
-
-def config_dict(extra=None):
-    d = {"workload": f"cab_dalm_m{BENCH['m']}_n{BENCH['classes'] * BENCH['per_class']}_N{BENCH['N']}",
-         "m": BENCH["m"], "n": BENCH["classes"] * BENCH["per_class"], "classes": BENCH["classes"],
-         "rhs_per_gpu": BENCH["N"], "solver": BENCH["solver"], "tol": BENCH["tol"],
-         "max_iter": BENCH["max_iter"], "corrupt_fraction": BENCH["corrupt"],
-         "l2": (f"flushed (512 MiB write) before each timed step; A ({BENCH['m'] * BENCH['classes'] * BENCH['per_class'] * 4 / 1e6:.1f} MB FP32) "
-                "and F (the inverse of A A^T + I) stay in L2 within a solve when they fit (129 MB)")}
-    if extra:
-        d.update(extra)
-    return d
 
 
 class ClockSampler:
@@ -177,52 +170,165 @@ def run_cpu_oracle(p, cols, threads, tol, max_iter):
     return conv, dt, outs
 
 
-def oracle_agreement(p, cols, x_gpu, obj_gpu, label_gpu, outs, bar=1e-4):
-    """Per sampled test vector j: ||x_gpu - w_j|| / ||w_j|| and the relative
-    objective error against the oracle's w_j = [x; e] (same tol and
-    max_iter), and whether the class labels agree.  x_gpu holds the sampled
-    columns of the GPU solve in the order of cols."""
+def oracle_rate_sample(p, threads, extra_iters, mean_iters):
+    """The FP64 oracle on the host cores, bounded: half the threads run
+    orc_dalm for one iteration (its one-time Cholesky setup and one step),
+    the other half for 1 + extra_iters iterations, one test vector each, all
+    at once.  Gives the setup time and the time per iteration, and from them
+    the solves per second of all `threads` cores on solves of mean_iters
+    iterations (each oracle solve factors B B^T itself)."""
+    import concurrent.futures as cf
+
     import oracle
-    A, B, off = p["A"], p["B"], p["offsets"]
-    n = A.shape[1]
-    ex, eo, labels = [], [], 0
-    for k, (j, (w, _, _)) in enumerate(zip(cols, outs)):
-        nw = np.linalg.norm(w)
-        ex.append(float(np.linalg.norm(np.asarray(x_gpu[:, k], np.float64) - w) / nw) if nw > 0 else 0.0)
-        f = float(np.abs(w).sum())
-        eo.append(abs(float(obj_gpu[k]) - f) / f if f > 0 else 0.0)
-        labels += int(oracle.classify(A, off, B[:, j], w[:n], w[n:])[0] == int(label_gpu[k]))
-    return {"sample": f"test vectors {cols[0]}..{cols[-1]} of the last timed solve, oracle at the same tol/max_iter",
-            "max_rel_err_x": max(ex), "max_rel_err_obj": max(eo),
-            "within_bar": sum(1 for e in ex if e <= bar), "bar": bar, "of": len(ex),
-            "labels_equal": labels}
+    oracle.build()
+    A, B = p["A"], p["B"]
+    half = max(1, threads // 2)
+
+    def one(args):
+        j, it = args
+        t = time.perf_counter()
+        oracle.dalm(A, B[:, j], cab=True, tol=0.0, max_iter=it)
+        return it, time.perf_counter() - t
+
+    jobs = [(j, 1) for j in range(half)] + [(half + j, 1 + extra_iters) for j in range(half)]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=2 * half) as ex:
+        outs = list(ex.map(one, jobs))
+    wall = time.perf_counter() - t0
+    t1 = statistics.mean(t for it, t in outs if it == 1)
+    tk = statistics.mean(t for it, t in outs if it > 1)
+    t_iter = max(0.0, (tk - t1) / extra_iters)
+    t_setup = max(0.0, t1 - t_iter)
+    rate = 2 * half / (t_setup + mean_iters * t_iter)
+    return {"value": rate, "unit": "solves/s", "cores": 2 * half, "kind": "oracle",
+            "sample": (f"{half} threads x orc_dalm for 1 iteration and {half} x for {1 + extra_iters}, "
+                       f"one test vector each, at once ({wall:.0f} s): setup {t_setup:.1f} s, "
+                       f"{1e3 * t_iter:.1f} ms per iteration; solves/s of {2 * half} cores on solves of "
+                       f"{mean_iters:.0f} iterations (the GPU run's mean), setup included")}
+
+
+GOLDEN4096 = os.path.join(ROOT, "tests", "golden", "cab4096_dalm_oracle.npz")
+
+
+def golden_oracle(p, path=GOLDEN4096):
+    """Stored FP64-oracle answers of sampled columns (written by
+    tests/golden/make_cab4096_golden.py, which calls only the oracle), after a
+    check that this machine generates the same inputs."""
+    g = np.load(path)
+    A, B = p["A"], p["B"]
+    ok = (abs(float(g["a_sum"]) - A.sum()) <= 1e-9 * abs(A.sum()) and
+          abs(float(g["a_sq"]) - (A * A).sum()) <= 1e-9 * (A * A).sum() and
+          all(abs(float(bs) - B[:, int(j)].sum()) <= 1e-9 * abs(B[:, int(j)].sum())
+              for j, bs in zip(g["cols"], g["b_sums"])))
+    if not ok:
+        raise RuntimeError("the generated inputs differ from those the stored oracle answers were made for")
+    out = {}
+    for k, j in enumerate(g["cols"]):
+        ws = g["w_stop"][:, k].astype(np.float64)
+        ko = int(g["stop_iters"][k])
+        out[int(j)] = {"stop": ko, "label": int(g["label"][k]), "sci_label": int(g["sci_label"][k]),
+                       "at": {ko: ws, ko - 1: ws + g["d_before"][:, k].astype(np.float64),
+                              ko + 1: ws + g["d_after"][:, k].astype(np.float64)}}
+    return out
+
+
+def verify_columns(cols, x_gpu, iters_gpu, obj_gpu, label_gpu, stop_of, iterate_at, label_of, bar=1e-4,
+                   obj_bar=1e-5, sample=""):
+    """At-tolerance parity of sampled GPU columns with the FP64 oracle.  The
+    relative-change rule fixes an answer only up to the iteration at which it
+    fires (one step moves w by about tol * ||w||), so a column counts as
+    verified when it stopped within one iteration of the oracle's own stop,
+    its x = [x; e] is within `bar` (relative) and its objective within
+    `obj_bar` of the oracle's iterate at the GPU's stopping iteration, and its
+    class label equals the oracle's.  stop_of(j) -> oracle stopping iteration;
+    iterate_at(j, k) -> the oracle's w after k iterations (None if unknown);
+    label_of(j) -> the oracle's label."""
+    per, ok = [], 0
+    for k, j in enumerate(cols):
+        kg, ko = int(iters_gpu[k]), int(stop_of(j))
+        w = iterate_at(j, kg) if abs(kg - ko) <= 1 else None
+        xe = oe = None
+        if w is not None:
+            nw = np.linalg.norm(w)
+            xe = float(np.linalg.norm(np.asarray(x_gpu[:, k], np.float64) - w) / nw) if nw > 0 else 0.0
+            f = float(np.abs(w).sum())
+            oe = abs(float(obj_gpu[k]) - f) / f if f > 0 else 0.0
+        lab = int(label_of(j)) == int(label_gpu[k])
+        good = w is not None and xe <= bar and oe <= obj_bar and lab
+        ok += int(good)
+        per.append({"col": int(j), "stop_gpu_minus_oracle": kg - ko, "rel_err_x": xe, "rel_err_obj": oe,
+                    "label_equal": lab, "verified": good})
+    xs = [d["rel_err_x"] for d in per if d["rel_err_x"] is not None]
+    os_ = [d["rel_err_obj"] for d in per if d["rel_err_obj"] is not None]
+    return {"sample": sample, "of": len(cols), "within_bar": ok, "bar_x": bar, "bar_obj": obj_bar,
+            "max_rel_err_x": max(xs) if xs else None, "max_rel_err_obj": max(os_) if os_ else None,
+            "labels_equal": sum(int(d["label_equal"]) for d in per), "per_instance": per}
+
+
+def workload_cfg(args):
+    return CAB4096 if args.workload == "cab4096" else CAB1024
+
+
+def workload_name(cfg):
+    return f"cab_dalm_m{cfg['m']}_n{cfg['classes'] * cfg['per_class']}_N{cfg['N']}"
+
+
+def config_dict(cfg, extra=None):
+    n = cfg["classes"] * cfg["per_class"]
+    d = {"workload": workload_name(cfg), "m": cfg["m"], "n": n, "classes": cfg["classes"],
+         "rhs_per_gpu": cfg["N"], "solver": cfg["solver"], "tol": cfg["tol"], "max_iter": cfg["max_iter"],
+         "corrupt_fraction": cfg["corrupt"], "seed": cfg["seed"],
+         "l2": "flushed (512 MiB write) before each timed step"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# mean DALM iterations per column of the GPU solves (the oracle's stopping
+# iterations agree within one), used to scale the bounded oracle sample
+MEAN_ITERS = {"cab4096": 1718.0, "cab1024": 1784.0}
+
+
+def cpu_oracle_line(args, cfg, p, mean_iters):
+    """The FP64 oracle on the host cores: full solves of the first test
+    vectors (m = 1024), or the bounded setup + iterations sample (m = 4096,
+    where one oracle solve takes minutes)."""
+    threads = min(os.cpu_count() or 1, 16)
+    if cfg["m"] <= 1024:
+        sample = list(range(min(threads, cfg["N"])))
+        conv, dt, outs = run_cpu_oracle(p, sample, threads, cfg["tol"], cfg["max_iter"])
+        return {"value": conv / dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                "sample": f"first {len(sample)} of {cfg['N']} test vectors, one per thread, to the stopping rule"}, outs
+    return oracle_rate_sample(p, threads, 20, mean_iters), None
 
 
 def bench_reference(args, rank, world):
     """FP64 CPU oracle on the host cores (the comparison arm)."""
     if rank != 0:
         return 0
-    p = workload(0)
-    threads = min(os.cpu_count() or 1, 16)
-    sample = list(range(threads))  # one instance per core per step
-    for _ in range(max(0, min(args.warmup, 1))):
-        pass  # the oracle has no warm-up state
-    total_conv, total_t = 0, 0.0
+    cfg = workload_cfg(args)
+    p = cab_workload(cfg)
+    vals, mss = [], []
+    cpu = None
     for _ in range(args.steps):
-        conv, dt, _ = run_cpu_oracle(p, sample, threads, BENCH["tol"], BENCH["max_iter"])
-        total_conv += conv
-        total_t += dt
-    value = total_conv / total_t
+        t0 = time.perf_counter()
+        cpu, _ = cpu_oracle_line(args, cfg, p, MEAN_ITERS[args.workload])
+        mss.append(1e3 * (time.perf_counter() - t0))
+        vals.append(cpu["value"])
+    value = statistics.mean(vals)
+    cpu = dict(cpu, value=value)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": statistics.mean(mss), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict({"sample": f"{len(sample)} of {BENCH['N']} test vectors per step"}),
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{len(sample)} test vectors per step, one per thread"},
+            "config": config_dict(cfg, {"sample": cpu["sample"]}),
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+SAMPLE1024 = [0, 1, 2, 3, 255, 511, 767, 1023]
 
 
 def bench_ours(args, rank, world):
@@ -239,7 +345,8 @@ def bench_ours(args, rank, world):
         dist.init_process_group("nccl")
     build.build()
     l1.load()
-    p = workload(rank)
+    cfg = workload_cfg(args)
+    p = cab_workload(cfg, rank)
     A, B, off = p["A"], p["B"], p["offsets"]
     m, n = A.shape
     N = B.shape[1]
@@ -248,22 +355,22 @@ def bench_ours(args, rank, world):
     B_d = torch.from_numpy(np.ascontiguousarray(B.T, dtype=np.float32)).cuda().t()
     x_d = torch.empty((N, n + m), dtype=torch.float32, device="cuda").t()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    solver = l1.DALM if BENCH["solver"] == "DALM" else l1.PALM
-    engine = l1.ENGINE_TC if args.engine == "tc" else l1.ENGINE_SIMT
+    engine = {"auto": l1.ENGINE_AUTO, "tc": l1.ENGINE_TC, "simt": l1.ENGINE_SIMT}[args.engine]
+    prec = {"fp32": l1.A_FP32, "bf16": l1.A_BF16, "fp8": l1.A_FP8E4M3}[args.precision]
     # two handles on the same dictionary: the last timed step runs on the one
     # that times every sweep with CUDA events (the roofline), the others on
     # the one without events
-    prec = {"fp32": l1.A_FP32, "bf16": l1.A_BF16, "fp8": l1.A_FP8E4M3}[args.precision]
-    s = l1.Solver(A_d, mode=l1.CAB, solver=solver, class_offsets=off, profile=False, engine=engine,
-                  precision=prec, stream=stream.cuda_stream)
-    sp = l1.Solver(A_d, mode=l1.CAB, solver=solver, class_offsets=off, profile=True, engine=engine,
-                   precision=prec, stream=stream.cuda_stream)
+    s = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec,
+                  stream=stream.cuda_stream)
+    sp = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec,
+                   profile=True, stream=stream.cuda_stream)
     setup_ms = s.info()["setup_ms"]
-    tol, max_iter = BENCH["tol"], BENCH["max_iter"]
+    tc = l1.load() is not None and engine != l1.ENGINE_SIMT and args.precision != "fp8"
+    tol, max_iter = cfg["tol"], cfg["max_iter"]
 
     for _ in range(args.warmup):
         s.solve(B_d, tol, max_iter, x=x_d)
-        sp.solve(B_d, tol, max_iter, x=x_d)
+    sp.solve(B_d, tol, max_iter, x=x_d)
     torch.cuda.synchronize()
     info0, infop0 = s.info(), sp.info()
 
@@ -277,7 +384,6 @@ def bench_ours(args, rank, world):
     if sampler:
         sampler.start()
     step_ms, conv, iters, labels_ok = [], 0, [], 0
-    check_cols = min(os.cpu_count() or 1, 16, N)
     for step in range(args.steps):
         flush.fill_(1.0)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -292,28 +398,61 @@ def bench_ours(args, rank, world):
         labels_ok += int(np.sum(res["label"] == p["labels"]))
     barrier()
     clocks = sampler.stop() if sampler else None
-    # the first columns of the last timed solve, for the comparison with the
-    # oracle below (later calls reuse x_d)
-    x_check = x_d[:, :check_cols].cpu().numpy()
-    res_check = {k: np.asarray(res[k][:check_cols]) for k in ("primal_obj", "label")}
     info1, infop1 = s.info(), sp.info()
+
+    # ---- verification of a sample of the last timed solve against the
+    # FP64 oracle at the stopping tolerance (stored answers for m = 4096)
+    sample = sorted(golden_oracle(p).keys()) if cfg is CAB4096 else SAMPLE1024
+    xs = x_d[:, sample].cpu().numpy()
+    agreement = None
+    outs_cpu = None
+    cpu = None
+    if rank == 0:
+        mean_it = statistics.mean(iters)
+        if cfg is CAB4096:
+            gold = golden_oracle(p)
+            agreement = verify_columns(
+                sample, xs, res["iters"][sample], res["primal_obj"][sample], res["label"][sample],
+                lambda j: gold[j]["stop"], lambda j, k: gold[j]["at"].get(k), lambda j: gold[j]["label"],
+                sample=f"test vectors {sample} of the last timed solve; stored FP64-oracle answers "
+                       "(tests/golden/cab4096_dalm_oracle.npz)")
+            if not args.no_cpu_baseline:
+                cpu, _ = cpu_oracle_line(args, cfg, p, mean_it)
+        else:
+            import oracle
+            conv_o, dt_o, outs_cpu = run_cpu_oracle(p, sample, len(sample), tol, max_iter)
+            stops = {j: st["iters"] for j, (_, _, st) in zip(sample, outs_cpu)}
+            ws = {j: w for j, (w, _, _) in zip(sample, outs_cpu)}
+
+            def at(j, k):
+                if k == stops[j]:
+                    return ws[j]
+                return oracle.dalm(A, B[:, j], cab=True, tol=0.0, max_iter=k)[0]
+            agreement = verify_columns(
+                sample, xs, res["iters"][sample], res["primal_obj"][sample], res["label"][sample],
+                lambda j: stops[j], at, lambda j: oracle.classify(A, off, B[:, j], ws[j][:n], ws[j][n:])[0],
+                sample=f"test vectors {sample} of the last timed solve; FP64 oracle run here")
+            if not args.no_cpu_baseline:
+                cpu = {"value": conv_o / dt_o, "unit": "solves/s", "cores": len(sample), "kind": "oracle",
+                       "sample": f"test vectors {sample}, one per thread, to the stopping rule"}
+    frac_ok = agreement["within_bar"] / agreement["of"] if agreement else 0.0
+
     total_ms = sum(step_ms)
     total_ms, conv = reduce_over_ranks(dist, total_ms, conv)
-    value = conv / (total_ms / 1e3)
+    # solves per second that meet the bar: the verified fraction of the
+    # sample times the columns solved
+    value = frac_ok * N * world * args.steps / (total_ms / 1e3)
 
     # ---- end to end through the same call with pinned host buffers
     Bh = torch.from_numpy(np.ascontiguousarray(B.T, dtype=np.float32)).pin_memory().t()
     xh = torch.empty((N, n + m), dtype=torch.float32).pin_memory().t()
-    s.solve(Bh, tol, max_iter, x=xh)  # warm
     barrier()
     t0 = time.perf_counter()
-    e2e_conv = 0
     for _ in range(args.steps):
-        _, _, res = s.solve(Bh, tol, max_iter, x=xh)
-        e2e_conv += int(np.sum(res["status"] == l1.CONVERGED))
+        s.solve(Bh, tol, max_iter, x=xh)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_s, e2e_conv = reduce_over_ranks(dist, e2e_s, e2e_conv)
+    e2e_s, _ = reduce_over_ranks(dist, e2e_s, 0)
 
     if rank != 0:
         s.close()
@@ -322,105 +461,84 @@ def bench_ours(args, rank, world):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant sweep over the timed region
-    names = ["A_u", "Finv_r", "At_y", "other"]
-    d_ms = [infop1["sweep_ms"][k] - infop0["sweep_ms"][k] for k in range(4)]
-    d_fl = [infop1["sweep_flop"][k] - infop0["sweep_flop"][k] for k in range(4)]
-    d_ln = [infop1["sweep_launches"][k] - infop0["sweep_launches"][k] for k in range(4)]
+    # ---- roofline of the dominant sweep over the profiled timed solve
+    names = ["A_V", "Finv_d", "At_y"] if tc else ["A_u", "Finv_r", "At_y"]
+    d_ms = [infop1["sweep_ms"][k] - infop0["sweep_ms"][k] for k in range(3)]
+    d_fl = [infop1["sweep_flop"][k] - infop0["sweep_flop"][k] for k in range(3)]
+    d_ln = [infop1["sweep_launches"][k] - infop0["sweep_launches"][k] for k in range(3)]
     k = int(np.argmax(d_ms))
     achieved = d_fl[k] / (d_ms[k] / 1e3) / 1e12 if d_ms[k] > 0 else 0.0
-    # with --engine tc, A u and A^T y run on tcgen05 and the y-step stays on
-    # the compensated CUDA-core sweep (the library's default tc_sweeps)
-    on_tc = args.engine == "tc" and names[k] in ("A_u", "At_y")
-    if on_tc:
-        # split-TF32 tcgen05 sweeps: 3 TF32 products per FP32 product (6 for the
-        # y-step); peak = measured sustained BF16 x the nominal TF32/BF16 ratio
-        peaks = measured_peaks()
-        terms = [3, 6, 3, 1][k]
-        peak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
-        roofline = {"bound": "tensor", "kernel": f"sweep {names[k]} (gemm_tc_kernel, tcgen05 kind::tf32)",
+    peaks = measured_peaks()
+    if tc:
+        terms = 6
+        peak = peaks["bf16_tflops_sustained"]
+        tr = TC_TRAFFIC.get((workload_name(cfg), names[k]))
+        roofline = {"bound": "tensor",
+                    "kernel": f"sweep {names[k]} (tc16::sweep_kernel, tcgen05 kind::f16, 3 x 3 BF16 pieces)",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None,
-                    "peak_note": (f"of measured: bf16_tflops_sustained {peaks['bf16_tflops_sustained']} x "
-                                  f"{TF32_PER_BF16:.4f} (nominal TF32 1.1 / BF16 2.25 PFLOP/s); "
-                                  f"achieved counts algorithmic FP32 FLOPs 2*M*K*N"),
-                    "executed_tf32_tflops": achieved * terms, "executed_frac": achieved * terms / peak,
+                    "traffic": tr,
+                    "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-width launch" if tr else None,
+                    "peak_note": ("of measured bf16_tflops_sustained; achieved counts the algorithmic FP32 "
+                                  "products 2*M*K*(active columns)"),
+                    "executed_tflops": achieved * terms, "executed_frac": achieved * terms / peak,
+                    "executed_note": "six BF16 products per algorithmic product (three aligned pieces per operand)",
                     "launches": d_ln[k], "avg_launch_us": 1e3 * d_ms[k] / max(1, d_ln[k]),
                     "share_of_sweep_time": d_ms[k] / max(1e-9, sum(d_ms))}
     else:
-        # the y-step multiplies by the FP32 pair F_hi + F_lo: two products per
-        # algorithmic one
-        terms = [1, 2, 1, 1][k]
-        default_size = (BENCH["m"], BENCH["classes"], BENCH["per_class"], BENCH["N"]) == (1024, 40, 30, 1024)
-        tr = SIMT_TRAFFIC.get(names[k]) if default_size and args.precision == "fp32" else None
+        terms = [1, 2, 1][k]
         roofline = {"bound": "alu", "kernel": f"sweep {names[k]} (gemm_simt_kernel / split-K pair)",
                     "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": tr[0] if tr else None,
-                    "traffic_note": ("bytes of one full-batch launch (N = 1024, cold cache) from ncu; "
-                                     f"algorithmic bytes of that launch {tr[1]:.3g}") if tr else None,
+                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived, no measured FP32 peak)",
                     "executed_tflops": achieved * terms, "executed_frac": achieved * terms / FP32_SIMT_PEAK_TFLOPS,
                     "launches": d_ln[k], "avg_launch_us": 1e3 * d_ms[k] / max(1, d_ln[k]),
                     "share_of_sweep_time": d_ms[k] / max(1e-9, sum(d_ms))}
 
-    # ---- the dominant sweep at full width: 100 iterations with every column
-    # active (the timed solves above also contain the narrow launches of the
-    # last columns, which are latency-bound)
+    # ---- the dominant sweep at full width: 32 iterations, every column active
     fw0 = sp.info()
-    sp.solve(B_d, 0.0, 100, x=x_d)
+    sp.solve(B_d, 0.0, 32, x=x_d)
     torch.cuda.synchronize()
     fw1 = sp.info()
     fms = fw1["sweep_ms"][k] - fw0["sweep_ms"][k]
     ffl = fw1["sweep_flop"][k] - fw0["sweep_flop"][k]
     fach = ffl / (fms / 1e3) / 1e12 if fms > 0 else 0.0
-    fterms = [3, 6, 3, 1][k] if on_tc else [1, 2, 1, 1][k]
-    fpeak = roofline["peak"]
     roofline_full = {"bound": roofline["bound"], "kernel": roofline["kernel"], "achieved": fach,
-                     "peak": fpeak, "unit": "TFLOP/s", "frac": fach / fpeak,
-                     "executed_frac": fach * fterms / fpeak,
-                     "note": f"100 iterations, all {N} columns active, same handle and events"}
+                     "peak": roofline["peak"], "unit": "TFLOP/s", "frac": fach / roofline["peak"],
+                     "executed_frac": fach * terms / roofline["peak"],
+                     "avg_launch_us": 1e3 * fms / 32.0,
+                     "note": f"32 iterations, all {N} columns active, same handle and events"}
 
-    # ---- the same solver one right-hand side at a time (no batching): the
-    # first 16 test vectors, each its own l1_solve_batch with N = 1
+    # ---- the plain per-instance FP32 GPU solver (l1_solve_plain: one right-
+    # hand side, one simple kernel per step, no batching or fusion)
+    n_single = 4
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    single_conv = 0
-    n_single = min(16, N)
+    single_conv, single_iters = 0, []
     for j in range(n_single):
-        _, _, r1 = s.solve(B_d[:, j:j + 1], tol, max_iter)
-        single_conv += int(r1["status"][0] == l1.CONVERGED)
+        _, r1 = s.solve_plain(B_d[:, j].contiguous(), tol, max_iter)
+        single_conv += int(r1["status"] == l1.CONVERGED)
+        single_iters.append(int(r1["iters"]))
     torch.cuda.synchronize()
     single_rate = single_conv / (time.perf_counter() - t0)
     per_instance = {"value": single_rate, "unit": "solves/s",
-                    "sample": f"first {n_single} test vectors, one l1_solve_batch each (N = 1)",
-                    "batched_over_per_instance": value / single_rate if single_rate > 0 else None}
+                    "sample": f"first {n_single} test vectors, l1_solve_plain each (FP32, unfused, unbatched)",
+                    "mean_iters": statistics.mean(single_iters),
+                    "batched_over_per_instance": (conv / (total_ms / 1e3)) / single_rate if single_rate > 0 else None}
 
-    # ---- CPU oracle on a bounded sample of the same workload
-    cpu = None
-    agreement = None
-    if not args.no_cpu_baseline:
-        threads = min(os.cpu_count() or 1, 16)
-        sample = list(range(min(threads, N)))
-        c_conv, c_dt, outs = run_cpu_oracle(p, sample, threads, tol, max_iter)
-        cpu = {"value": c_conv / c_dt, "unit": "solves/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {len(sample)} of {N} test vectors, one per thread, same tol/max_iter"}
-        try:
-            agreement = oracle_agreement(p, sample, x_check, res_check["primal_obj"], res_check["label"],
-                                         outs)
-        except Exception as exc:  # reported in the line, never fatal to it
-            agreement = {"error": f"{type(exc).__name__}: {exc}"}
-
+    dtype = ("bf16 tensor-core products (A and the panels as three aligned BF16 pieces), f32 accumulation "
+             "and iterates" if tc and args.precision == "fp32" else
+             ("f32" if args.precision == "fp32" else f"{args.precision} A, f32 arithmetic"))
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "ms_per_step_median": statistics.median(step_ms),  # rank 0's own steps
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else f"{args.precision} A, f32 arithmetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic",
-            "config": config_dict({"parallelism": f"replicas{world}" if world > 1 else "single",
-                                   "engine": args.engine, "precision": args.precision, "setup_ms": setup_ms,
-                                   "mean_iters": statistics.mean(iters),
-                                   "label_accuracy_vs_planted": labels_ok / (args.steps * N)}),
-            "e2e": {"value": e2e_conv / e2e_s, "unit": "solves/s",
+            "config": config_dict(cfg, {"parallelism": f"replicas{world}" if world > 1 else "single",
+                                        "engine": "tc" if tc else "simt", "precision": args.precision,
+                                        "setup_ms": setup_ms, "mean_iters": statistics.mean(iters),
+                                        "converged_solves_per_s": conv / (total_ms / 1e3),
+                                        "label_accuracy_vs_planted": labels_ok / (args.steps * N)}),
+            "e2e": {"value": frac_ok * N * world * args.steps / e2e_s, "unit": "solves/s",
                     "h2d_bytes_per_step": 4 * m * N,
                     "d2h_bytes_per_step": 4 * (n + m) * N + 72 * N},
             "gpu_launches": int((info1["gpu_launches"] - info0["gpu_launches"]) +
@@ -688,40 +806,35 @@ def bench_p1(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--tol", type=float, default=None)
-    ap.add_argument("--max-iter", type=int, default=None)
-    ap.add_argument("--engine", choices=["tc", "simt"], default="simt")
-    ap.add_argument("--workload", choices=["cab", "qp-group", "unrolled", "p1"], default="cab")
+    ap.add_argument("--engine", choices=["auto", "tc", "simt"], default="auto",
+                    help="cab: the library's automatic choice (the tensor-core engine for DALM) or a forced one")
+    ap.add_argument("--workload", choices=["cab4096", "cab1024", "qp-group", "unrolled", "p1"], default="cab4096")
     ap.add_argument("--count", type=int, default=None, help="qp-group: number of instances")
-    ap.add_argument("--m", type=int, default=None, help="cab: rows of A")
-    ap.add_argument("--classes", type=int, default=None, help="cab: classes")
-    ap.add_argument("--per-class", type=int, default=None, help="cab: columns per class")
-    ap.add_argument("--N", type=int, default=None, help="cab: right-hand sides")
+    ap.add_argument("--max-iter", type=int, default=None, help="qp-group: iteration cap")
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32",
                     help="cab: stored precision of A (bf16 / fp8 add the FP32 refinement phase)")
-    ap.add_argument("--no-cpu-baseline", action="store_true", help="cab: skip the CPU oracle leg")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="cab: skip the CPU oracle timing")
     args = ap.parse_args()
-    for key, val in (("m", args.m), ("classes", args.classes), ("per_class", args.per_class), ("N", args.N)):
-        if val is not None:
-            BENCH[key] = val
-    if args.tol is not None:
-        BENCH["tol"] = args.tol
-    if args.max_iter is not None:
-        BENCH["max_iter"] = args.max_iter
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "qp-group":
+        return bench_group(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
+    if args.workload == "unrolled":
+        return bench_unrolled(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
+    if args.workload == "p1":
+        return bench_p1(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
     if args.impl == "reference":
         return bench_reference(args, rank, world)
-    if args.workload == "qp-group":
-        return bench_group(args, rank, world)
-    if args.workload == "unrolled":
-        return bench_unrolled(args, rank, world)
-    if args.workload == "p1":
-        return bench_p1(args, rank, world)
     return bench_ours(args, rank, world)
+
+
+def unavailable_reference(args):
+    print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm is timed on the cab workloads only, "
+                                                          f"not on {args.workload}"}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -305,6 +305,23 @@ L1_API int l1_lipschitz_static(const float* A, int64_t m, int64_t n, int64_t lda
                                double rtol, void* stream, double* rho_out, int32_t* status_out,
                                int32_t* iters_out);
 
+/*
+ * l1_solve_plain -- DALM (Algorithm 2, reading R1) for ONE right-hand side b
+ * (m floats, host or device) on a DALM handle (modes P1 and CAB), in plain
+ * FP32: one simple kernel per step of the iteration (z-step of Eq. 38, the
+ * products A u, (B B^T)^{-1} r with the FP32 inverse, A^T y, the w-step), and
+ * the relative-change rule of §VI-C read on the host after every iteration.
+ * It is the unbatched, unfused baseline the batched solver is measured
+ * against.  x (n + m floats for CAB, n for P1, host or device) receives w;
+ * res gets status, iters, rel_change, primal_obj = ||w||_1 and param = beta
+ * (dual_obj, gap and resid are NaN, labels -1).  The call allocates its
+ * work buffers and synchronises the handle's stream.
+ * Errors: L1_ERR_INVALID_ARG, L1_ERR_UNSUPPORTED (not a DALM handle in P1 or
+ * CAB mode, a group or an unrolled handle), L1_ERR_OOM, L1_ERR_CUDA.
+ */
+L1_API int l1_solve_plain(l1_handle h, const float* b, double tol, int32_t max_iter, float* x,
+                          l1_result* res);
+
 /* Set the stream later calls enqueue on. */
 L1_API int l1_set_stream(l1_handle h, void* stream);
 

@@ -30,7 +30,7 @@ CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
 # every symbol include/l1alm.h declares
 EXPORTS = ("l1_options_init", "l1_setup", "l1_setup_group", "l1_group_load", "l1_solve_batch",
            "l1_backward", "l1_set_stream", "l1_get_info", "l1_destroy", "l1_status_string",
-           "l1_last_error", "l1_lipschitz_static")
+           "l1_last_error", "l1_lipschitz_static", "l1_solve_plain")
 
 
 class Options(C.Structure):
@@ -110,6 +110,8 @@ def load() -> C.CDLL:
     L.l1_lipschitz_static.argtypes = [vp, i64, i64, i64, i32, dbl, vp, C.POINTER(dbl), C.POINTER(i32),
                                       C.POINTER(i32)]
     L.l1_lipschitz_static.restype = C.c_int
+    L.l1_solve_plain.argtypes = [vp, vp, dbl, i32, vp, C.POINTER(Result)]
+    L.l1_solve_plain.restype = C.c_int
     _lib = L
     return L
 
@@ -254,6 +256,25 @@ class Solver:
                                 _ptr(x_init), _ld(x_init) if x_init is not None else 0,
                                 _ptr(y_init), _ld(y_init) if y_init is not None else 0), "l1_solve_batch")
         return x, y, results_to_dict(res)
+
+    def solve_plain(self, b, tol: float, max_iter: int, x=None):
+        """l1_solve_plain: DALM for one right-hand side b (m) with plain,
+        unfused FP32 kernels (the baseline of the batched solve).  Returns
+        (x, result dict)."""
+        L = load()
+        is_np = isinstance(b, np.ndarray)
+        if is_np:
+            b = np.ascontiguousarray(b, dtype=np.float32).reshape(-1)
+        nx = self.n + self.m if self.mode == CAB else self.n
+        if x is None:
+            if is_np:
+                x = np.zeros(nx, dtype=np.float32)
+            else:
+                import torch
+                x = torch.empty(nx, dtype=torch.float32, device=b.device)
+        res = (Result * 1)()
+        _check(L.l1_solve_plain(self._h, _ptr(b), float(tol), int(max_iter), _ptr(x), res), "l1_solve_plain")
+        return x, {k: v[0] for k, v in results_to_dict(res).items()}
 
     def backward(self, grad_x, grad_b=None, grad_A=None, want_b: bool = True, want_A: bool = True):
         """l1_backward after an unrolled forward: grad_x is n x N (column-major,

@@ -137,6 +137,7 @@ struct Handle {
     __nv_bfloat16* A_rm_h[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16* A_cm_h[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16* F_h[3] = {nullptr, nullptr, nullptr};
+    float* tc_wk = nullptr;  // split-K slices of the narrow tensor-core sweeps (SMs x 128 x 128 floats)
     int* tc_err = nullptr;  // device: first bounded-wait failure of a tcgen05 sweep
     // encoded TMA tensor maps, keyed by the operand pointers and shapes
     struct MapCacheEntry {

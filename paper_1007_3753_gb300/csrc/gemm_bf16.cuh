@@ -150,10 +150,98 @@ constexpr int kEpiWarps = 8;                  // two per TMEM lane quarter
 constexpr int kGroupM = 16;                   // row tiles per group of the tile order
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
+// The epilogue of one 128 x BN tile whose values are in tile_s (column-
+// major [BN][128]): the functor per element -- its per-column reduction terms
+// summed over each warp's 32 rows in FP32 (FP64 arithmetic runs at a small
+// fraction of the FP32 rate on this part) into red_s[4][BN][NR] -- then the
+// aligned pieces of the values it returns (po).  Run by the kEpiWarps warps
+// of a CTA (etid = 0 .. 32 kEpiWarps - 1): warp w covers rows q*32 + lane of
+// the tile (q = w mod 4) and the columns cb .. cb + BN/2 - 1.  The warps meet
+// at named barrier 1 when pieces are written (an aborted CTA skips the work,
+// ok = false, but not the barriers).
+template <class E, int BN>
+__device__ __forceinline__ void tile_epilogue(const E& epi, const PieceOut& po, bool ok, int i, int M, int N,
+                                              int n0, int q, int cb, int lane, int etid, float* tile_s,
+                                              double* red_s, float* max_s) {
+    constexpr int NR = E::NRED > 0 ? E::NRED : 1;
+    constexpr int CPT = BN / 2;
+    float* my = tile_s + q * 32 + lane;
+    if (ok) {
+        // unrolled so that several columns' global loads (the functor's
+        // state) are in flight at once
+#pragma unroll 8
+        for (int c = 0; c < CPT; ++c) {
+            const int j = n0 + cb + c;
+            float rv[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) rv[r] = 0.0f;
+            float ret = 0.0f;
+            if (i < M && j < N) ret = epi(i, j, my[(cb + c) * kBM], rv);
+            my[(cb + c) * kBM] = ret;
+            if constexpr (E::NRED > 0) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const float sv = warp_sum_f(rv[r]);
+                    if (lane == 0) red_s[((q * BN) + cb + c) * NR + r] = (double)sv;
+                }
+            }
+        }
+    }
+    if (po.np > 0) {
+        // the largest magnitude of each column over the tile's 128 rows sets
+        // the grid of its pieces; two threads scan each column
+        constexpr int kEpiThreads = 32 * kEpiWarps;
+        static_assert(kEpiThreads == 2 * BN, "two threads per column");
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+        const int col = etid >> 1, half = etid & 1;
+        float mx = 0.0f;
+        if (ok) {
+            const float4* cp = reinterpret_cast<const float4*>(tile_s + col * kBM + half * 64);
+#pragma unroll 4
+            for (int t = 0; t < 16; ++t) {
+                const float4 f = cp[t];
+                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(f.x), fabsf(f.y)), fmaxf(fabsf(f.z), fabsf(f.w))));
+            }
+        }
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        if (half == 0) max_s[col] = mx;
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+        if (ok && i < M) {
+#pragma unroll 2
+            for (int c = 0; c < CPT; ++c) {
+                const int j = n0 + cb + c;
+                if (j >= N) break;
+                float p0, p1, p2;
+                split_aligned(my[(cb + c) * kBM], max_s[cb + c], p0, p1, p2);
+                const int64_t o = (int64_t)j * po.ld + i;
+                po.p[0][o] = __float2bfloat16_rn(p0);
+                if (po.np > 1) po.p[1][o] = __float2bfloat16_rn(p1);
+                if (po.np > 2) po.p[2][o] = __float2bfloat16_rn(p2);
+            }
+        }
+    }
+}
+
+// Sum over the tile's four row quarters of red_s, one partial per (row block,
+// column): part[(row_block * N + j) * 4 + r].
+template <int BN, int NR>
+__device__ __forceinline__ void write_partials(const double* red_s, double* part, int tile_m, int n0, int N) {
+    for (int idx = threadIdx.x; idx < BN * NR; idx += blockDim.x) {
+        const int c = idx / NR, r = idx % NR;
+        const int j = n0 + c;
+        if (j < N) {
+            double s = 0.0;
+            for (int qq = 0; qq < 4; ++qq) s += red_s[((qq * BN) + c) * NR + r];
+            part[((int64_t)tile_m * N + j) * kPartStride + r] = s;
+        }
+    }
+}
+
 template <class E, int NPA, int NPX>
 __global__ void __launch_bounds__(kThreads, 1)
 sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, int K, E epi, PieceOut po,
-              double* __restrict__ part, const int32_t* __restrict__ active, int* __restrict__ err) {
+             double* __restrict__ part, const int32_t* __restrict__ active, int* __restrict__ err, int ksplit,
+             float* __restrict__ wk) {
     constexpr int BN = 128;
     constexpr int NR = E::NRED > 0 ? E::NRED : 1;
     constexpr int kMmaPerBlock = kKB / kMmaK;  // 4
@@ -186,14 +274,22 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
     // panels of X in L2 (row-major order streams every column panel once per
     // wave)
     const int tiles_m = (M + kBM - 1) / kBM, tiles_n = (N + BN - 1) / BN;
+    // split K (ksplit > 1): CTA z of a tile takes the chunks [c0, c1) and
+    // leaves its FP32 sums in wk for finish_kernel
+    const int ntiles = tiles_m * tiles_n;
+    const int z = blockIdx.x / ntiles, tid = blockIdx.x - z * ntiles;
     const int per_group = kGroupM * tiles_n;
-    const int group = blockIdx.x / per_group, first_m = group * kGroupM;
+    const int group = tid / per_group, first_m = group * kGroupM;
     const int gsz = min(kGroupM, tiles_m - first_m);
-    const int in_group = blockIdx.x % per_group;
+    const int in_group = tid % per_group;
     const int tile_m = first_m + in_group % gsz, tile_n = in_group / gsz;
     const int m0 = tile_m * kBM, n0 = tile_n * BN;
     const int kblocks = (K + kKB - 1) / kKB;
     const int nchunks = (kblocks + kKBPerChunk - 1) / kKBPerChunk;
+    const int cps = (nchunks + ksplit - 1) / ksplit;
+    const int c0 = min(nchunks, z * cps), c1 = min(nchunks, c0 + cps);
+    const int kb0 = c0 * kKBPerChunk, kb1 = min(kblocks, c1 * kKBPerChunk);
+    const bool split = ksplit > 1;
     const int nterms = tl.n;
     bool has_lo = false;
 #pragma unroll
@@ -212,6 +308,7 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
     }
     __syncthreads();
     if (!flags[0]) {
+        if (split) return;  // finish_kernel writes the partials
         if constexpr (E::NRED > 0) {
             for (int c = threadIdx.x; c < BN; c += blockDim.x)
                 if (n0 + c < N)
@@ -249,9 +346,10 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
 #pragma unroll
             for (int p = 0; p < NPX; ++p) prefetch_map(&maps.x[p]);
             int issued = 0;
-            for (int kb = 0; kb < kblocks; ++kb) {
-                const int s = kb % kStages;
-                const uint32_t ph = (uint32_t)(kb / kStages) & 1u;
+            for (int lk = 0; lk < kb1 - kb0; ++lk) {
+                const int kb = kb0 + lk;
+                const int s = lk % kStages;
+                const uint32_t ph = (uint32_t)(lk / kStages) & 1u;
                 if (!mbar_wait(&empty[s], ph ^ 1u)) {
                     atomicCAS(err, ERR_NONE, ERR_WAIT_EMPTY);
                     atomicExch(&flags[1], 1);
@@ -265,19 +363,19 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
 #pragma unroll
                 for (int p = 0; p < NPX; ++p)
                     tma_load_2d(st + NPA * S::kATile + p * S::kXTile, &maps.x[p], &full[s], kb * kKB, n0);
-                issued = kb + 1;
+                issued = lk + 1;
             }
-            for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
-                mbar_wait(&full[kb % kStages], (uint32_t)(kb / kStages) & 1u);
+            for (int lk = (issued > kStages ? issued - kStages : 0); lk < issued; ++lk)
+                mbar_wait(&full[lk % kStages], (uint32_t)(lk / kStages) & 1u);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
             bool ok = true;
-            for (int c = 0; c < nchunks && ok; ++c) {
-                const int b = c & 1;
+            for (int lc = 0; lc < c1 - c0 && ok; ++lc) {
+                const int c = c0 + lc, b = lc & 1;
                 // the epilogue has drained this buffer pair (chunk c - 2)
-                if (!mbar_wait(&acc_empty[b], ((uint32_t)(c >> 1) & 1u) ^ 1u)) {
+                if (!mbar_wait(&acc_empty[b], ((uint32_t)(lc >> 1) & 1u) ^ 1u)) {
                     atomicCAS(err, ERR_NONE, ERR_WAIT_ACC);
                     atomicExch(&flags[1], 1);
                     ok = false;
@@ -288,8 +386,9 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
                 bool first_hi = true, first_lo = true;
                 const int kb_end = min(kblocks, (c + 1) * kKBPerChunk);
                 for (int kb = c * kKBPerChunk; kb < kb_end; ++kb) {
-                    const int s = kb % kStages;
-                    if (!mbar_wait(&full[s], (uint32_t)(kb / kStages) & 1u)) {
+                    const int lk = kb - kb0;
+                    const int s = lk % kStages;
+                    if (!mbar_wait(&full[s], (uint32_t)(lk / kStages) & 1u)) {
                         atomicCAS(err, ERR_NONE, ERR_WAIT_FULL);
                         atomicExch(&flags[1], 1);
                         ok = false;
@@ -339,7 +438,7 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
 #pragma unroll
         for (int c = 0; c < CPT; ++c) sum[c] = 0.0f;
         bool ok = true;
-        for (int ch = 0; ch < nchunks; ++ch) {
+        for (int ch = 0; ch < c1 - c0; ++ch) {
             const int b = ch & 1;
             bool ready = true;
             if (lane == 0) ready = mbar_wait(&acc_full[b], (uint32_t)(ch >> 1) & 1u);
@@ -365,93 +464,90 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
-        // the tile's values go to shared memory (the ring is idle: every MMA,
-        // and so every copy it waited for, has completed), where the functor
-        // pass reads them with a loop index and leaves the values it returns
-        float* my = tile_s + q * 32 + lane;
-        if (ok) {
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) my[(cb + c) * kBM] = sum[c];
-            // unrolled so that several columns' global loads (the functor's
-            // state) are in flight at once
-#pragma unroll 8
-            for (int c = 0; c < CPT; ++c) {
-                const int j = n0 + cb + c;
-                // per-element reduction terms and their sum over the warp's 32
-                // rows in FP32 (FP64 arithmetic runs at a small fraction of the
-                // FP32 rate on this part); the partial sums above that level
-                // are FP64, all in a fixed order
-                float rv[NR];
-#pragma unroll
-                for (int r = 0; r < NR; ++r) rv[r] = 0.0f;
-                float ret = 0.0f;
-                if (i < M && j < N) ret = epi(i, j, my[(cb + c) * kBM], rv);
-                my[(cb + c) * kBM] = ret;
-                if constexpr (E::NRED > 0) {
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        const float sv = warp_sum_f(rv[r]);
-                        if (lane == 0) red_s[((q * BN) + cb + c) * NR + r] = (double)sv;
-                    }
-                }
-            }
-        }
-        if (po.np > 0) {
-            // aligned pieces: the largest magnitude of each column over the
-            // tile's 128 rows sets the grid.  The eight epilogue warps meet at
-            // a named barrier (an aborted CTA skips the work but not the
-            // barriers); two threads scan each column.
-            constexpr int kEpiThreads = 32 * kEpiWarps;
-            static_assert(kEpiThreads == 2 * BN, "two threads per column");
-            asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
-            const int et = threadIdx.x - 64;
-            const int col = et >> 1, half = et & 1;
-            float mx = 0.0f;
+        if (split) {
+            // this slice's sums; finish_kernel adds the slices in order
+            const int64_t Mp = (int64_t)tiles_m * kBM;
             if (ok) {
-                const float4* cp = reinterpret_cast<const float4*>(tile_s + col * kBM + half * 64);
-#pragma unroll 4
-                for (int t = 0; t < 16; ++t) {
-                    const float4 f = cp[t];
-                    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(f.x), fabsf(f.y)), fmaxf(fabsf(f.z), fabsf(f.w))));
-                }
-            }
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            if (half == 0) max_s[col] = mx;
-            asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
-            if (ok && i < M) {
-#pragma unroll 2
+#pragma unroll
                 for (int c = 0; c < CPT; ++c) {
                     const int j = n0 + cb + c;
-                    if (j >= N) break;
-                    float p0, p1, p2;
-                    split_aligned(my[(cb + c) * kBM], max_s[cb + c], p0, p1, p2);
-                    const int64_t o = (int64_t)j * po.ld + i;
-                    po.p[0][o] = __float2bfloat16_rn(p0);
-                    if (po.np > 1) po.p[1][o] = __float2bfloat16_rn(p1);
-                    if (po.np > 2) po.p[2][o] = __float2bfloat16_rn(p2);
+                    if (j < N) wk[((int64_t)z * N + j) * Mp + i] = sum[c];
                 }
             }
+        } else {
+            // the tile's values go to shared memory (the ring is idle: every
+            // MMA, and so every copy it waited for, has completed)
+            float* my = tile_s + q * 32 + lane;
+            if (ok) {
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) my[(cb + c) * kBM] = sum[c];
+            }
+            tile_epilogue<E, BN>(epi, po, ok, i, M, N, n0, q, cb, lane, threadIdx.x - 64, tile_s, red_s, max_s);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if constexpr (E::NRED > 0) {
-        if (!flags[1]) {
-            for (int idx = threadIdx.x; idx < BN * NR; idx += blockDim.x) {
-                const int c = idx / NR, r = idx % NR;
-                const int j = n0 + c;
-                if (j < N) {
-                    double s = 0.0;
-                    for (int qq = 0; qq < 4; ++qq) s += red_s[((qq * BN) + c) * NR + r];
-                    part[((int64_t)tile_m * N + j) * kPartStride + r] = s;
-                }
-            }
-        }
+        if (!flags[1] && !split) write_partials<BN, NR>(red_s, part, tile_m, n0, N);
     }
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
+}
+
+
+// The second half of a split-K sweep: one CTA of kEpiWarps warps per 128 x 128
+// output tile adds the ksplit slices of wk in slice order (FP32) and runs the
+// same tile epilogue.  Dynamic shared memory: finish_smem<NR>() bytes.
+template <int NR>
+constexpr int finish_smem() { return 128 * kBM * 4 + 4 * 128 * NR * 8 + 128 * 4; }
+
+template <class E>
+__global__ void __launch_bounds__(32 * kEpiWarps, 1)
+finish_kernel(int M, int N, int ksplit, const float* __restrict__ wk, E epi, PieceOut po,
+              double* __restrict__ part, const int32_t* __restrict__ active) {
+    constexpr int BN = 128;
+    constexpr int NR = E::NRED > 0 ? E::NRED : 1;
+    constexpr int CPT = BN / 2;
+    extern __shared__ __align__(16) uint8_t fsm[];
+    float* tile_s = reinterpret_cast<float*>(fsm);
+    double* red_s = reinterpret_cast<double*>(tile_s + BN * kBM);
+    float* max_s = reinterpret_cast<float*>(red_s + 4 * BN * NR);
+    __shared__ int any_active;
+    const int tiles_m = (M + kBM - 1) / kBM;
+    const int tile_m = blockIdx.x % tiles_m, tile_n = blockIdx.x / tiles_m;
+    const int m0 = tile_m * kBM, n0 = tile_n * BN;
+    if (threadIdx.x == 0) any_active = active == nullptr ? 1 : 0;
+    __syncthreads();
+    if (active != nullptr)
+        for (int c = threadIdx.x; c < BN; c += blockDim.x)
+            if (n0 + c < N && active[n0 + c]) any_active = 1;
+    __syncthreads();
+    if (!any_active) {
+        if constexpr (E::NRED > 0) {
+            for (int c = threadIdx.x; c < BN; c += blockDim.x)
+                if (n0 + c < N)
+                    for (int r = 0; r < NR; ++r) part[((int64_t)tile_m * N + n0 + c) * kPartStride + r] = 0.0;
+        }
+        return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3, cb = (warp >> 2) * CPT;
+    const int i = m0 + q * 32 + lane;
+    const int64_t Mp = (int64_t)tiles_m * kBM;
+    float* my = tile_s + q * 32 + lane;
+#pragma unroll 4
+    for (int c = 0; c < CPT; ++c) {
+        const int j = n0 + cb + c;
+        float v = 0.0f;
+        if (j < N)
+            for (int z = 0; z < ksplit; ++z) v += wk[((int64_t)z * N + j) * Mp + i];
+        my[(cb + c) * kBM] = v;
+    }
+    tile_epilogue<E, BN>(epi, po, true, i, M, N, n0, q, cb, lane, threadIdx.x, tile_s, red_s, max_s);
+    __syncthreads();
+    if constexpr (E::NRED > 0) write_partials<BN, NR>(red_s, part, tile_m, n0, N);
 }
 
 }  // namespace tc16

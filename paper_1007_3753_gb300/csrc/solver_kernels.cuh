@@ -683,11 +683,14 @@ __global__ void classify_resid_kernel(const float* A_rm, int64_t lda_rm, int m,
     const float* x = Wx + (int64_t)j * ldn;
     double acc = 0.0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        // the class's part of row i in FP32 (FP64 arithmetic runs at a small
+        // fraction of the FP32 rate on this part; a class has tens of
+        // columns), the residual's square summed in FP64
         const float* arow = A_rm + (int64_t)i * lda_rm;
-        double s = 0.0;
-        for (int k = c0; k < c1; ++k) s += (double)arow[k] * (double)x[k];
-        const double v = (double)B[(int64_t)j * ldm + i] - (E ? (double)E[(int64_t)j * ldm + i] : 0.0) - s;
-        acc += v * v;
+        float s = 0.0f;
+        for (int k = c0; k < c1; ++k) s = fmaf(arow[k], x[k], s);
+        const float v = B[(int64_t)j * ldm + i] - (E ? E[(int64_t)j * ldm + i] : 0.0f) - s;
+        acc += (double)v * v;
     }
     double l1v = 0.0;
     for (int k = c0 + threadIdx.x; k < c1; k += blockDim.x) l1v += fabs((double)x[k]);

@@ -67,6 +67,8 @@ int make_dictionary_pieces(Handle* h) {
         L1_TRY(dev_alloc_t(h, &h->A_rm_h[p], (size_t)h->ldn * m));
         L1_TRY(dev_alloc_t(h, &h->A_cm_h[p], (size_t)h->ldm * n));
     }
+    const int sms = h->sms > 0 ? h->sms : 152;
+    L1_TRY(dev_alloc_t(h, &h->tc_wk, (size_t)sms * 128 * 128));
     // A u: K = n along the rows of A; A^T y: K = m along the columns of A
     L1_TRY(split_aligned_lines(h, h->A_rm, nullptr, m, n, h->ldn, h->A_rm_h, kMaxPieces));
     L1_TRY(split_aligned_lines(h, h->A_cm, nullptr, n, m, h->ldm, h->A_cm_h, kMaxPieces));

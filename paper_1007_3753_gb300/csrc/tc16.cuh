@@ -64,6 +64,22 @@ inline int get_maps(Handle* h, int M, int N, int K, const Operands& op, int bn, 
     return L1_OK;
 }
 
+// K slices of a sweep with fewer output tiles than SMs (a narrow batch, or a
+// small dictionary): enough to give every SM one CTA, each slice whole
+// 128-element chunks; the slices' sums are added in slice order by
+// finish_kernel (deterministic for a given batch width).  Their scratch holds
+// ksplit x tiles x 128 x 128 floats <= SMs x 128 x 128.
+inline int ksplit(const Handle* h, int tiles, int K) {
+    const int sms = h->sms > 0 ? h->sms : 152;
+    const int chunks = (K + kChunk - 1) / kChunk;
+    // (measured: two slices of the 64 tiles of a 1024 x 1024 batch lose to
+    // one, the finish pass costing more than the second wave of CTAs saves)
+    if (!h->tc_wk || 4 * tiles > sms || chunks < 4) return 1;
+    int ks = std::min(std::min(sms / tiles, chunks), 16);
+    const int cps = (chunks + ks - 1) / ks;
+    return (chunks + cps - 1) / cps;  // no empty slice
+}
+
 // One BF16 tensor-core sweep sum_t a_{ia(t)} x_{ix(t)} with epilogue epi
 // (gemm_bf16.cuh): operands split on the aligned grid of 128-element K
 // blocks, exactly one leading term (0, 0); the functor returns the value
@@ -71,18 +87,27 @@ inline int get_maps(Handle* h, int M, int N, int K, const Operands& op, int bn, 
 // row blocks (partials per column) or a negative error code.
 template <class E, int NPA, int NPX>
 int launch_inst(Handle* h, const Maps& maps, const Terms& tl, int M, int N, int K, const E& epi,
-                 const PieceOut& po, double* part, const int32_t* active) {
+                const PieceOut& po, double* part, const int32_t* active) {
     using S = Cfg<128, NPA, NPX>;
+    constexpr int NR = E::NRED > 0 ? E::NRED : 1;
     static bool attr_set = false;
     if (!attr_set) {
         L1_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<E, NPA, NPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          S::kBytes));
+        L1_CUDA_TRY(cudaFuncSetAttribute(finish_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         finish_smem<NR>()));
         attr_set = true;
     }
     const int tiles_m = (M + kBM - 1) / kBM, tiles = tiles_m * ((N + 127) / 128);
-    sweep_kernel<E, NPA, NPX><<<tiles, kThreads, S::kBytes, h->stream>>>(maps, tl, M, N, K, epi, po, part, active,
-                                                                         h->tc_err);
+    const int ks = ksplit(h, tiles, K);
+    sweep_kernel<E, NPA, NPX><<<tiles * ks, kThreads, S::kBytes, h->stream>>>(maps, tl, M, N, K, epi, po, part,
+                                                                              active, h->tc_err, ks, h->tc_wk);
     L1_LAUNCH_CHECK(h);
+    if (ks > 1) {
+        finish_kernel<E><<<tiles, 32 * kEpiWarps, finish_smem<NR>(), h->stream>>>(M, N, ks, h->tc_wk, epi, po, part,
+                                                                                 active);
+        L1_LAUNCH_CHECK(h);
+    }
     return tiles_m;
 }
 

@@ -478,3 +478,30 @@ def test_profiled_solve_reports_sweep_times(l1, engine):
     assert all(v > 0 for v in info["sweep_launches"][:3]) and all(v > 0 for v in info["sweep_ms"][:3])
     s0.close()
     s1.close()
+
+
+# ---------------------------------------- the plain per-instance FP32 solver
+
+def test_plain_per_instance_solver_tracks_the_oracle(l1):
+    """l1_solve_plain (one right-hand side, one simple FP32 kernel per step,
+    the FP32 inverse without its low part) against the oracle after a fixed
+    iteration count, and to the stopping rule with the oracle's labels."""
+    p = synthetic.cab_problem(256, 10, 30, 3, seed=41)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    n = A.shape[1]
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off)
+    errs = []
+    for j in range(3):
+        x, r = s.solve_plain(_dev(B[:, j:j + 1])[:, 0].contiguous(), 0.0, 300)
+        w, _, _ = oracle.dalm(A, B[:, j], cab=True, tol=0.0, max_iter=300)
+        assert r["iters"] == 300 and r["status"] == l1.MAX_ITER
+        errs.append(_rel(x.cpu().numpy(), w))
+        x, r = s.solve_plain(B[:, j].astype(np.float32), 1e-3, 20000)  # host in, host out
+        assert r["status"] == l1.CONVERGED
+        wo, _, st = oracle.dalm(A, B[:, j], cab=True, tol=1e-3, max_iter=20000)
+        assert abs(r["iters"] - st["iters"]) <= 2
+        lab = oracle.classify(A, off, B[:, j], wo[:n], wo[n:])[0]
+        assert oracle.classify(A, off, B[:, j], x[:n].astype(np.float64), x[n:].astype(np.float64))[0] == lab
+    print(f"plain per-instance FP32 solver, 300 iterations: x rel. err max {max(errs):.2e}")
+    assert max(errs) <= 1e-3
+    s.close()
