@@ -21,21 +21,31 @@ namespace l1 {
 // BF16 pieces the next sweep reads (0 for frozen columns); its per-column
 // reduction terms are FP32 (summed over 32 rows in FP32, above that in FP64).
 
+// Each functor has two halves so that the epilogue can issue the state loads
+// of several columns before the first store: load(i, j) reads what element
+// (i, j) needs (whether or not its column is active), apply(i, j, acc, st,
+// red) does the rest and returns the value for the piece sink.
+
 // T1 (rows of A, acc = A V_x): d = acc (+ V_e) + b / beta
 struct EpiTcD {
     static constexpr int NRED = 0;
+    struct State {
+        float b, ve;
+        int act;
+    };
     const float* Ve;
     const float* B;
     const float* binv;
     const int32_t* active;
     int64_t ldm;
     int cab;
-    __device__ float operator()(int i, int j, float acc, float*) const {
-        if (!active[j]) return 0.0f;
+    __device__ State load(int i, int j) const {
         const int64_t o = (int64_t)j * ldm + i;
-        float d = fmaf(B[o], binv[j], acc);
-        if (cab) d += Ve[o];
-        return d;
+        return State{B[o], cab ? Ve[o] : 0.0f, active[j]};
+    }
+    __device__ float apply(int, int j, float acc, const State& st, float*) const {
+        if (!st.act) return 0.0f;
+        return fmaf(st.b, binv[j], acc) + st.ve;
     }
 };
 
@@ -45,6 +55,10 @@ struct EpiTcD {
 // Returns y'.
 struct EpiTcY {
     static constexpr int NRED = 2;
+    struct State {
+        float y, we, ze;
+        int act;
+    };
     float* Y;
     float* We;
     float* Ze;
@@ -54,22 +68,25 @@ struct EpiTcY {
     const int32_t* active;
     int64_t ldm;
     int cab;
-    __device__ float operator()(int i, int j, float acc, float* red) const {
-        if (!active[j]) return 0.0f;
+    __device__ State load(int i, int j) const {
         const int64_t o = (int64_t)j * ldm + i;
-        const float y = Y[o] + acc;
+        return State{Y[o], cab ? We[o] : 0.0f, cab ? Ze[o] : 0.0f, active[j]};
+    }
+    __device__ float apply(int i, int j, float acc, const State& st, float* red) const {
+        if (!st.act) return 0.0f;
+        const int64_t o = (int64_t)j * ldm + i;
+        const float y = st.y + acc;
         Y[o] = y;
         if (cab) {
-            const float we = We[o];
-            const float dw = -beta[j] * (Ze[o] - y);
-            const float wn = we + dw;
+            const float dw = -beta[j] * (st.ze - y);
+            const float wn = st.we + dw;
             We[o] = wn;
             const float v = fmaf(wn, binv[j], y);
             const float z = clamp_unit(v);
             Ze[o] = z;
             Ve[o] = z - v;
             red[0] += dw * dw;
-            red[1] += we * we;
+            red[1] += st.we * st.we;
         }
         return y;
     }
@@ -80,6 +97,10 @@ struct EpiTcY {
 // v = acc + w_x'/beta.  red: ||dw_x||^2, ||w_x||^2.  Returns V_x.
 struct EpiTcS {
     static constexpr int NRED = 2;
+    struct State {
+        float w, z;
+        int act;
+    };
     float* Wx;
     float* Zx;
     float* Vx;
@@ -87,12 +108,15 @@ struct EpiTcS {
     const float* binv;
     const int32_t* active;
     int64_t ldn;
-    __device__ float operator()(int i, int j, float acc, float* red) const {
-        if (!active[j]) return 0.0f;
+    __device__ State load(int i, int j) const {
         const int64_t o = (int64_t)j * ldn + i;
-        const float w = Wx[o];
-        const float dw = -beta[j] * (Zx[o] - acc);
-        const float wn = w + dw;
+        return State{Wx[o], Zx[o], active[j]};
+    }
+    __device__ float apply(int i, int j, float acc, const State& st, float* red) const {
+        if (!st.act) return 0.0f;
+        const int64_t o = (int64_t)j * ldn + i;
+        const float dw = -beta[j] * (st.z - acc);
+        const float wn = st.w + dw;
         Wx[o] = wn;
         const float v = fmaf(wn, binv[j], acc);
         const float z = clamp_unit(v);
@@ -100,7 +124,7 @@ struct EpiTcS {
         const float vx = z - v;
         Vx[o] = vx;
         red[0] += dw * dw;
-        red[1] += w * w;
+        red[1] += st.w * st.w;
         return vx;
     }
 };

@@ -151,7 +151,8 @@ constexpr int kGroupM = 16;                   // row tiles per group of the tile
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 // The epilogue of one 128 x BN tile whose values are in tile_s (column-
-// major [BN][128]): the functor per element -- its per-column reduction terms
+// major [BN][128]): the functor per element (E::load, then E::apply, see
+// dalm_tc.cuh) -- its per-column reduction terms
 // summed over each warp's 32 rows in FP32 (FP64 arithmetic runs at a small
 // fraction of the FP32 rate on this part) into red_s[4][BN][NR] -- then the
 // aligned pieces of the values it returns (po).  Run by the kEpiWarps warps
@@ -167,22 +168,32 @@ __device__ __forceinline__ void tile_epilogue(const E& epi, const PieceOut& po, 
     constexpr int CPT = BN / 2;
     float* my = tile_s + q * 32 + lane;
     if (ok) {
-        // unrolled so that several columns' global loads (the functor's
-        // state) are in flight at once
-#pragma unroll 8
-        for (int c = 0; c < CPT; ++c) {
-            const int j = n0 + cb + c;
-            float rv[NR];
+        // groups of G columns: the state loads of the whole group are issued
+        // before any of the group's stores, so that they are in flight at once
+        constexpr int G = 8;
+        static_assert(CPT % G == 0, "column groups");
+        for (int c0 = 0; c0 < CPT; c0 += G) {
+            typename E::State st[G];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) rv[r] = 0.0f;
-            float ret = 0.0f;
-            if (i < M && j < N) ret = epi(i, j, my[(cb + c) * kBM], rv);
-            my[(cb + c) * kBM] = ret;
-            if constexpr (E::NRED > 0) {
+            for (int u = 0; u < G; ++u) {
+                const int j = n0 + cb + c0 + u;
+                if (i < M && j < N) st[u] = epi.load(i, j);
+            }
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const float sv = warp_sum_f(rv[r]);
-                    if (lane == 0) red_s[((q * BN) + cb + c) * NR + r] = (double)sv;
+            for (int u = 0; u < G; ++u) {
+                const int c = c0 + u, j = n0 + cb + c;
+                float rv[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) rv[r] = 0.0f;
+                float ret = 0.0f;
+                if (i < M && j < N) ret = epi.apply(i, j, my[(cb + c) * kBM], st[u], rv);
+                my[(cb + c) * kBM] = ret;
+                if constexpr (E::NRED > 0) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const float sv = warp_sum_f(rv[r]);
+                        if (lane == 0) red_s[((q * BN) + cb + c) * NR + r] = (double)sv;
+                    }
                 }
             }
         }
