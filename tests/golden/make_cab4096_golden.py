@@ -18,7 +18,7 @@ For each sampled test vector j it stores
   * checksums of the generated inputs, so that a machine whose generator
     output differs is noticed.
 
-Run:  python tests/golden/make_cab4096_golden.py   (a few hours of 8 cores)
+Run:  python tests/golden/make_cab4096_golden.py   (about half an hour on 8 cores)
 """
 from __future__ import annotations
 

@@ -505,3 +505,43 @@ def test_plain_per_instance_solver_tracks_the_oracle(l1):
     print(f"plain per-instance FP32 solver, 300 iterations: x rel. err max {max(errs):.2e}")
     assert max(errs) <= 1e-3
     s.close()
+
+
+def test_4096_workload_against_stored_oracle_answers(l1):
+    """The 4096 x 4000 (+ identity) cross-and-bouquet workload (100 classes x
+    40 columns, 4096 test vectors, seed 3000) on the default engine, at the
+    stopping tolerance, against FP64-oracle answers stored for 8 sampled
+    columns (an oracle solve of this size takes minutes): every sampled column
+    must stop within one iteration of the oracle, agree with the oracle's
+    iterate at its own stop and carry the oracle's label.  Then 200 fixed
+    iterations of 4 of those columns, solved as a batch of 4 on the tensor
+    cores, against the oracle's iterate after 200 iterations."""
+    import bench
+    cfg = bench.CAB4096
+    p = bench.cab_workload(cfg)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    g = bench.golden_oracle(p)
+    cols = sorted(g)
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off)
+    x, _, res = s.solve(_dev(B), tol=cfg["tol"], max_iter=cfg["max_iter"])
+    x = x.cpu().numpy()
+    assert np.mean(res["status"] == l1.CONVERGED) >= 0.99
+    assert np.mean(res["label"] == p["labels"]) >= 0.99
+    d = bench.verify_columns(cols, x[:, cols], res["iters"][cols], res["primal_obj"][cols], res["label"][cols],
+                             lambda j: g[j]["stop"], lambda j, k: g[j]["at"].get(k), lambda j: g[j]["label"])
+    print("4096 workload, stored oracle sample:", {k: v for k, v in d.items() if k != "per_instance"})
+    print([(q["col"], q["stop_gpu_minus_oracle"], q["rel_err_x"], q["rel_err_obj"]) for q in d["per_instance"]])
+    assert d["within_bar"] == d["of"] == len(cols), d["per_instance"]
+
+    gz = np.load(bench.GOLDEN4096)
+    fc = [int(j) for j in gz["fixed_cols"]]
+    s4 = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=l1.ENGINE_TC, tc_min_cols=1)
+    x4, _, r4 = s4.solve(_dev(B[:, fc]), tol=0.0, max_iter=int(gz["fixed_iters"]))
+    x4 = x4.cpu().numpy()
+    assert (r4["iters"] == int(gz["fixed_iters"])).all()
+    ex = Errs("4096 workload, 200 fixed iterations, batch of 4 on the tensor cores")
+    for k in range(len(fc)):
+        ex.add(x4[:, k], gz["w_fixed"][:, k].astype(np.float64), r4["primal_obj"][k])
+    ex.check()
+    s.close()
+    s4.close()
