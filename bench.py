@@ -813,7 +813,10 @@ def main():
                     help="cab: the library's automatic choice (the tensor-core engine for DALM) or a forced one")
     ap.add_argument("--workload", choices=["cab4096", "cab1024", "qp-group", "unrolled", "p1"], default="cab4096")
     ap.add_argument("--count", type=int, default=None, help="qp-group: number of instances")
-    ap.add_argument("--max-iter", type=int, default=None, help="qp-group: iteration cap")
+    ap.add_argument("--max-iter", type=int, default=None, help="qp-group, or cab with --solve-only: iteration cap")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="cab: set up and run ONE untimed solve, print its iteration statistics, exit (the command "
+                         "the profiler summaries under profiles/ are taken on)")
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32",
                     help="cab: stored precision of A (bf16 / fp8 add the FP32 refinement phase)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="cab: skip the CPU oracle timing")
@@ -828,7 +831,41 @@ def main():
         return bench_p1(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
     if args.impl == "reference":
         return bench_reference(args, rank, world)
+    if args.solve_only:
+        return solve_once(args)
     return bench_ours(args, rank, world)
+
+
+def solve_once(args):
+    """--solve-only: one solve of the cab workload with nothing around it (no
+    warm-up, oracle, flush or second handle), for profilers."""
+    import torch
+
+    import paper_1007_3753_gb300 as l1
+    from paper_1007_3753_gb300 import build
+
+    build.build()
+    l1.load()
+    cfg = workload_cfg(args)
+    p = cab_workload(cfg)
+    A, B, off = p["A"], p["B"], p["offsets"]
+    engine = {"auto": l1.ENGINE_AUTO, "tc": l1.ENGINE_TC, "simt": l1.ENGINE_SIMT}[args.engine]
+    prec = {"fp32": l1.A_FP32, "bf16": l1.A_BF16, "fp8": l1.A_FP8E4M3}[args.precision]
+    A_d = torch.from_numpy(np.ascontiguousarray(A.T, dtype=np.float32)).cuda().t()
+    B_d = torch.from_numpy(np.ascontiguousarray(B.T, dtype=np.float32)).cuda().t()
+    s = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec)
+    max_iter = args.max_iter or cfg["max_iter"]
+    t0 = time.perf_counter()
+    _, _, res = s.solve(B_d, cfg["tol"], max_iter)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(json.dumps({"workload": workload_name(cfg), "max_iter": max_iter, "seconds": dt,
+                      "setup_ms": s.info()["setup_ms"], "gpu_launches": s.info()["gpu_launches"],
+                      "converged": int(np.sum(res["status"] == l1.CONVERGED)),
+                      "mean_iters": float(np.mean(res["iters"])), "max_iters": int(np.max(res["iters"]))}),
+          flush=True)
+    s.close()
+    return 0
 
 
 def unavailable_reference(args):
