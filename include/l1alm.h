@@ -123,6 +123,14 @@ typedef struct {
                           * (the tensor-core products track the FP64 iteration more
                           * closely than the CUDA-core FP32 ones, so by default they
                           * run to the last column) */
+    int32_t tune;        /* L1_ENGINE_TC: 0 -> l1_setup times the tile strategies of
+                          * the tensor-core sweeps (fused or deferred epilogue,
+                          * split-K slices) at batch widths up to 4096 for each sweep
+                          * shape and keeps the fastest (l1_tuning); -1 -> a fixed
+                          * rule from the tile and multiprocessor counts.  The slice
+                          * count sets the order in which K slices are added, so two
+                          * handles whose timings chose differently can differ in the
+                          * last bits. */
 } l1_options;
 
 /* Per-instance results (host memory). */
@@ -321,6 +329,22 @@ L1_API int l1_lipschitz_static(const float* A, int64_t m, int64_t n, int64_t lda
  */
 L1_API int l1_solve_plain(l1_handle h, const float* b, double tol, int32_t max_iter, float* x,
                           l1_result* res);
+
+/*
+ * l1_tuning -- the tile strategies l1_setup's autotuner chose for the batched
+ * tensor-core sweeps (L1_ENGINE_TC, tune = 0).  No counterpart in the paper:
+ * it concerns how the products of Algorithm 2's batched iteration are tiled.
+ * For each sweep shape and timed tile count it tried the tile epilogue fused
+ * into the sweep, deferred to a second kernel that reads the tile's FP32 sums,
+ * and split-K with every slice count that keeps one CTA per multiprocessor,
+ * and kept the fastest (the simplest within 2 %).  Writes up to cap entries
+ * of 6 int32 each to out (host): the sweep's output rows M, its depth K, the
+ * output tile count (128 x 128 tiles), the number of K slices, 1 if the
+ * epilogue is deferred, and the chosen launch's measured time in microseconds
+ * (rounded); returns the number of entries written (0: no tuning was done),
+ * or L1_ERR_INVALID_ARG for a null handle, or for out == NULL with cap > 0.
+ */
+L1_API int l1_tuning(l1_handle h, int32_t* out, int32_t cap);
 
 /* Set the stream later calls enqueue on. */
 L1_API int l1_set_stream(l1_handle h, void* stream);

@@ -30,7 +30,7 @@ CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
 # every symbol include/l1alm.h declares
 EXPORTS = ("l1_options_init", "l1_setup", "l1_setup_group", "l1_group_load", "l1_solve_batch",
            "l1_backward", "l1_set_stream", "l1_get_info", "l1_destroy", "l1_status_string",
-           "l1_last_error", "l1_lipschitz_static", "l1_solve_plain")
+           "l1_last_error", "l1_lipschitz_static", "l1_solve_plain", "l1_tuning")
 
 
 class Options(C.Structure):
@@ -42,7 +42,7 @@ class Options(C.Structure):
                 ("class_offsets", C.POINTER(C.c_int32)), ("stream", C.c_void_p),
                 ("unroll_K", C.c_int32), ("unroll_J", C.c_int32), ("ckpt_every", C.c_int32),
                 ("profile", C.c_int32), ("tc_pieces", C.c_int32), ("refine", C.c_int32),
-                ("tc_pieces_y", C.c_int32), ("tc_min_cols", C.c_int32)]
+                ("tc_pieces_y", C.c_int32), ("tc_min_cols", C.c_int32), ("tune", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -112,6 +112,8 @@ def load() -> C.CDLL:
     L.l1_lipschitz_static.restype = C.c_int
     L.l1_solve_plain.argtypes = [vp, vp, dbl, i32, vp, C.POINTER(Result)]
     L.l1_solve_plain.restype = C.c_int
+    L.l1_tuning.argtypes = [vp, C.POINTER(i32), i32]
+    L.l1_tuning.restype = C.c_int
     _lib = L
     return L
 
@@ -164,7 +166,7 @@ class Solver:
                  class_offsets=None, precision: int = A_FP32, engine: int = ENGINE_AUTO,
                  profile: bool = False, tc_pieces: int = 0, tc_pieces_y: int = 0, tc_min_cols: int = 0,
                  unroll_K: int = 0, unroll_J: int = 0, ckpt_every: int = 0, refine: bool = True,
-                 stream=None):
+                 tune: bool = True, stream=None):
         L = load()
         o = Options()
         L.l1_options_init(C.byref(o))
@@ -181,6 +183,7 @@ class Solver:
         o.tc_pieces, o.tc_pieces_y, o.tc_min_cols = tc_pieces, tc_pieces_y, tc_min_cols
         o.unroll_K = unroll_K
         o.refine = 0 if refine else -1
+        o.tune = 0 if tune else -1
         if unroll_J:
             o.unroll_J = unroll_J
         if ckpt_every:
@@ -256,6 +259,15 @@ class Solver:
                                 _ptr(x_init), _ld(x_init) if x_init is not None else 0,
                                 _ptr(y_init), _ld(y_init) if y_init is not None else 0), "l1_solve_batch")
         return x, y, results_to_dict(res)
+
+    def tuning(self) -> list:
+        """l1_tuning: the autotuner's tile strategies, one dict per (sweep
+        shape, tile count)."""
+        cap = 256
+        buf = (C.c_int32 * (6 * cap))()
+        k = load().l1_tuning(self._h, buf, cap)
+        _check(k if k < 0 else 0, "l1_tuning")
+        return [dict(zip(("M", "K", "tiles", "ksplit", "deferred", "us"), buf[6 * e:6 * e + 6])) for e in range(k)]
 
     def solve_plain(self, b, tol: float, max_iter: int, x=None):
         """l1_solve_plain: DALM for one right-hand side b (m) with plain,

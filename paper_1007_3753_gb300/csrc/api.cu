@@ -1,4 +1,5 @@
 // The C ABI of include/l1alm.h: argument checks, handle lifetime, setup.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -211,6 +212,10 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
             if (h->use_tc) {
                 rc = tc16::make_factor_pieces(h);
                 if (rc) break;
+                if (o.tune >= 0) {
+                    rc = tc16::tune_splits(h);
+                    if (rc) break;
+                }
             }
         }
         cudaEventRecord(ev1, h->stream);
@@ -349,6 +354,15 @@ int l1_get_info(l1_handle hh, l1_info* info) {
         info->sweep_flop[k] = h->sweep_flop[k];
     }
     return L1_OK;
+}
+
+int l1_tuning(l1_handle hh, int32_t* out, int32_t cap) {
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h || cap < 0 || (cap > 0 && !out)) return L1_ERR_INVALID_ARG;
+    const int k = (int)std::min<size_t>(h->tc_splits.size(), (size_t)cap);
+    for (int e = 0; e < k; ++e)
+        for (int f = 0; f < 6; ++f) out[6 * e + f] = h->tc_splits[e][f];
+    return k;
 }
 
 int l1_destroy(l1_handle hh) {

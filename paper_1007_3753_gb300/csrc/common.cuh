@@ -137,7 +137,13 @@ struct Handle {
     __nv_bfloat16* A_rm_h[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16* A_cm_h[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16* F_h[3] = {nullptr, nullptr, nullptr};
-    float* tc_wk = nullptr;  // split-K slices of the narrow tensor-core sweeps (SMs x 128 x 128 floats)
+    // FP32 sums of split-K slices or of deferred-epilogue tiles of the
+    // tensor-core sweeps (slices x tiles x 128 x 128 floats)
+    float* tc_wk = nullptr;
+    size_t tc_wk_elems = 0;
+    // autotuned choices of the tensor-core sweeps:
+    // (M, K, tiles, K slices, deferred epilogue, microseconds)
+    std::vector<std::array<int32_t, 6>> tc_splits;
     int* tc_err = nullptr;  // device: first bounded-wait failure of a tcgen05 sweep
     // encoded TMA tensor maps, keyed by the operand pointers and shapes
     struct MapCacheEntry {

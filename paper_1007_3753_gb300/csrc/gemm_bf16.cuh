@@ -23,9 +23,12 @@
 //               slots and hands each finished 128-K chunk to the epilogue
 //   warps 2..9  epilogue: warp w reads TMEM lane quarter w % 4 (32 output
 //               rows) and one half of the columns; FP32 sums of the chunks,
-//               then the functor per element, deterministic per-column
-//               reductions (one partial per row block and column) and the
-//               aligned pieces of the returned values
+//               then either (fused) the functor per element, deterministic
+//               per-column reductions (one partial per row block and column)
+//               and the aligned pieces of the returned values, or (deferred,
+//               and every slice of a split-K launch) the FP32 sums to a
+//               scratch for finish_kernel, which runs the same epilogue with
+//               one CTA per 128 rows x 8 columns
 // Tiles whose columns are all inactive write zero partials and return.
 // Every mbarrier wait is bounded; a wait that runs out records an error code
 // in *err, the CTA leaves its loops, waits (bounded) for its own copies and
@@ -252,7 +255,7 @@ template <class E, int NPA, int NPX>
 __global__ void __launch_bounds__(kThreads, 1)
 sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, int K, E epi, PieceOut po,
              double* __restrict__ part, const int32_t* __restrict__ active, int* __restrict__ err, int ksplit,
-             float* __restrict__ wk) {
+             int defer, float* __restrict__ wk) {
     constexpr int BN = 128;
     constexpr int NR = E::NRED > 0 ? E::NRED : 1;
     constexpr int kMmaPerBlock = kKB / kMmaK;  // 4
@@ -286,7 +289,8 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
     // wave)
     const int tiles_m = (M + kBM - 1) / kBM, tiles_n = (N + BN - 1) / BN;
     // split K (ksplit > 1): CTA z of a tile takes the chunks [c0, c1) and
-    // leaves its FP32 sums in wk for finish_kernel
+    // leaves its FP32 sums in wk for finish_kernel; defer (ksplit == 1): the
+    // whole K range, the sums to wk, the epilogue to finish_kernel
     const int ntiles = tiles_m * tiles_n;
     const int z = blockIdx.x / ntiles, tid = blockIdx.x - z * ntiles;
     const int per_group = kGroupM * tiles_n;
@@ -300,7 +304,7 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
     const int cps = (nchunks + ksplit - 1) / ksplit;
     const int c0 = min(nchunks, z * cps), c1 = min(nchunks, c0 + cps);
     const int kb0 = c0 * kKBPerChunk, kb1 = min(kblocks, c1 * kKBPerChunk);
-    const bool split = ksplit > 1;
+    const bool split = ksplit > 1 || defer != 0;
     const int nterms = tl.n;
     bool has_lo = false;
 #pragma unroll
@@ -508,57 +512,99 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
 }
 
 
-// The second half of a split-K sweep: one CTA of kEpiWarps warps per 128 x 128
-// output tile adds the ksplit slices of wk in slice order (FP32) and runs the
-// same tile epilogue.  Dynamic shared memory: finish_smem<NR>() bytes.
-template <int NR>
-constexpr int finish_smem() { return 128 * kBM * 4 + 4 * 128 * NR * 8 + 128 * 4; }
+// The second half of a split-K or deferred sweep: one CTA of kBM threads (one per row)
+// per (row block, kFinCols columns) adds the ksplit slices of wk in slice
+// order (FP32) and runs the tile epilogue on its columns: the functor, the
+// per-column reduction terms (FP32 warp sums over 32 rows, the four row
+// quarters added in order in FP64, as in the sweep's own epilogue) and the
+// aligned BF16 pieces on the grid of the column's largest magnitude over the
+// row block.  Narrow batches get one CTA per few columns instead of one per
+// 128-column tile.
+constexpr int kFinCols = 8;
 
 template <class E>
-__global__ void __launch_bounds__(32 * kEpiWarps, 1)
+__global__ void __launch_bounds__(kBM)
 finish_kernel(int M, int N, int ksplit, const float* __restrict__ wk, E epi, PieceOut po,
               double* __restrict__ part, const int32_t* __restrict__ active) {
-    constexpr int BN = 128;
     constexpr int NR = E::NRED > 0 ? E::NRED : 1;
-    constexpr int CPT = BN / 2;
-    extern __shared__ __align__(16) uint8_t fsm[];
-    float* tile_s = reinterpret_cast<float*>(fsm);
-    double* red_s = reinterpret_cast<double*>(tile_s + BN * kBM);
-    float* max_s = reinterpret_cast<float*>(red_s + 4 * BN * NR);
+    __shared__ double red_s[4][kFinCols][NR];
+    __shared__ float max_s[4][kFinCols];
     __shared__ int any_active;
     const int tiles_m = (M + kBM - 1) / kBM;
-    const int tile_m = blockIdx.x % tiles_m, tile_n = blockIdx.x / tiles_m;
-    const int m0 = tile_m * kBM, n0 = tile_n * BN;
-    if (threadIdx.x == 0) any_active = active == nullptr ? 1 : 0;
+    const int tile_m = blockIdx.x % tiles_m, j0 = (blockIdx.x / tiles_m) * kFinCols;
+    const int t = threadIdx.x, q = t >> 5, lane = t & 31;
+    const int i = tile_m * kBM + t;
+    if (t == 0) any_active = 0;
     __syncthreads();
-    if (active != nullptr)
-        for (int c = threadIdx.x; c < BN; c += blockDim.x)
-            if (n0 + c < N && active[n0 + c]) any_active = 1;
+    if (t < kFinCols && j0 + t < N && (active == nullptr || active[j0 + t])) any_active = 1;
     __syncthreads();
     if (!any_active) {
         if constexpr (E::NRED > 0) {
-            for (int c = threadIdx.x; c < BN; c += blockDim.x)
-                if (n0 + c < N)
-                    for (int r = 0; r < NR; ++r) part[((int64_t)tile_m * N + n0 + c) * kPartStride + r] = 0.0;
+            if (t < kFinCols * NR) {
+                const int c = t / NR, r = t % NR;
+                if (j0 + c < N) part[((int64_t)tile_m * N + j0 + c) * kPartStride + r] = 0.0;
+            }
         }
         return;
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = warp & 3, cb = (warp >> 2) * CPT;
-    const int i = m0 + q * 32 + lane;
     const int64_t Mp = (int64_t)tiles_m * kBM;
-    float* my = tile_s + q * 32 + lane;
-#pragma unroll 4
-    for (int c = 0; c < CPT; ++c) {
-        const int j = n0 + cb + c;
-        float v = 0.0f;
-        if (j < N)
-            for (int z = 0; z < ksplit; ++z) v += wk[((int64_t)z * N + j) * Mp + i];
-        my[(cb + c) * kBM] = v;
+    float v[kFinCols];
+    typename E::State st[kFinCols];
+#pragma unroll
+    for (int u = 0; u < kFinCols; ++u) {
+        const int j = j0 + u;
+        v[u] = 0.0f;
+        if (j < N) {
+            for (int z = 0; z < ksplit; ++z) v[u] += wk[((int64_t)z * N + j) * Mp + i];
+            if (i < M) st[u] = epi.load(i, j);
+        }
     }
-    tile_epilogue<E, BN>(epi, po, true, i, M, N, n0, q, cb, lane, threadIdx.x, tile_s, red_s, max_s);
+#pragma unroll
+    for (int u = 0; u < kFinCols; ++u) {
+        const int j = j0 + u;
+        float rv[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) rv[r] = 0.0f;
+        float ret = 0.0f;
+        if (i < M && j < N) ret = epi.apply(i, j, v[u], st[u], rv);
+        v[u] = ret;
+        if constexpr (E::NRED > 0) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float sv = warp_sum_f(rv[r]);
+                if (lane == 0) red_s[q][u][r] = (double)sv;
+            }
+        }
+        if (po.np > 0) {
+            float mx = fabsf(ret);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) max_s[q][u] = mx;
+        }
+    }
     __syncthreads();
-    if constexpr (E::NRED > 0) write_partials<BN, NR>(red_s, part, tile_m, n0, N);
+    if (po.np > 0 && i < M) {
+#pragma unroll
+        for (int u = 0; u < kFinCols; ++u) {
+            const int j = j0 + u;
+            if (j >= N) break;
+            const float mx = fmaxf(fmaxf(max_s[0][u], max_s[1][u]), fmaxf(max_s[2][u], max_s[3][u]));
+            float p0, p1, p2;
+            split_aligned(v[u], mx, p0, p1, p2);
+            const int64_t o = (int64_t)j * po.ld + i;
+            po.p[0][o] = __float2bfloat16_rn(p0);
+            if (po.np > 1) po.p[1][o] = __float2bfloat16_rn(p1);
+            if (po.np > 2) po.p[2][o] = __float2bfloat16_rn(p2);
+        }
+    }
+    if constexpr (E::NRED > 0) {
+        if (t < kFinCols * NR) {
+            const int c = t / NR, r = t % NR;
+            if (j0 + c < N)
+                part[((int64_t)tile_m * N + j0 + c) * kPartStride + r] =
+                    red_s[0][c][r] + red_s[1][c][r] + red_s[2][c][r] + red_s[3][c][r];
+        }
+    }
 }
 
 }  // namespace tc16

@@ -8,21 +8,24 @@
 // is one contiguous, 16-byte aligned region of the arena.  Each CTA owns a
 // contiguous range of the active units of a step and
 //   1. streams its tiles from HBM into two shared buffers with 1-D TMA bulk
-//      copies (cp.async.bulk + mbarrier), the next tile in flight while the
-//      current one is processed,
-//   2. on entering an instance stages its residual r = b - A z (from the
-//      previous step's accumulator) in shared memory,
-//   3. forms g_J = A_J^T r (one warp per column, 16-byte shared loads) and
-//      updates x_J = soft(z_J + g_J/L, lambda/L), z_J = x_J + mu (x_J - x_J_old),
-//   4. adds A_J z_J to a shared-memory copy of the instance's next
-//      accumulator, which goes to global memory (one atomic per row) only
-//      when the CTA leaves the instance,
-// so every element of every active dictionary is read from HBM once per step.
-// After the pass a bounded grid barrier, a per-instance finalisation (stopping
-// rule of §VI-C, FISTA momentum), another barrier, and a rebuild of the
-// active-instance work list (converged instances drop out: compaction).
-// The same kernel runs the batched power iteration for L = ||A_i||_2^2 and
-// the final pass that forms A x for the objective.
+//      copies (cp.async.bulk + mbarrier), two units in flight,
+//   2. on entering an instance loads the rows of its residual r = b - A z
+//      (from the previous step's accumulator) that it owns into registers,
+//   3. reads each tile from shared memory ONCE into registers (a thread owns
+//      16-byte words: 8 BF16 or 4 FP32 rows of up to 8 columns), forms its
+//      partial dots of g_J = A_J^T r, and releases the buffer for the next
+//      copy; one warp per column sums the partials and updates
+//      x_J = soft(z_J + g_J/L, lambda/L), z_J = x_J + mu (x_J - x_J_old),
+//   4. adds A_J z_J from the same registers to its rows' accumulator, which
+//      goes to global memory (one atomic per row) only when the CTA leaves
+//      the instance,
+// so every element of every active dictionary is read from HBM once per step
+// and from shared memory once.  After the pass a bounded grid barrier, a
+// per-instance finalisation (stopping rule of §VI-C, FISTA momentum), another
+// barrier, and a rebuild of the active-instance work list (converged
+// instances drop out: compaction).  The same kernel runs the batched power
+// iteration for L = ||A_i||_2^2 and the final pass that forms A x for the
+// objective.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -37,8 +40,11 @@ enum GroupMode : int { GM_FISTA = 0, GM_POWER_INIT = 1, GM_POWER = 2, GM_FINAL =
 
 constexpr int kGThreads = 512;
 constexpr int kGWarps = kGThreads / 32;
-constexpr int kGMaxM = 8192;               // rows of r staged in shared memory
+constexpr int kGMaxM = 8192;               // rows of an instance
+constexpr int kGShared = 2048;             // rows of an instance whose rows several threads own (acc_s)
+constexpr int kGBufs = 3;                  // tile buffers (units in flight)
 constexpr int kGTileBytes = 64 * 1024;     // A tile in shared memory
+constexpr int kGPartials = 4096;           // dot partials of one unit (part_s)
 constexpr uint32_t kGBarrierSpin = 1u << 26;
 
 struct GroupState {
@@ -204,11 +210,202 @@ __device__ __forceinline__ void issue_tile(const GArgs& g, const UnitGeom& q, ui
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
-// Row r of an instance lives at plane r % E, position r / E of the shared
-// vectors r_s and acc_s (E = 8 elements per 16-byte group for BF16, 4 for
-// FP32, RG = ld / E groups): a lane that owns row group v touches word
-// k * RG + v of plane k, so a warp's accesses are consecutive words.
-__device__ __forceinline__ int soa_index(int r, int E, int RG) { return (r % E) * RG + r / E; }
+
+// ------------------------------------------------------ per-instance thread map
+// A column of a unit is RG = ld / E 16-byte words (E = 8 rows for BF16, 4 for
+// FP32).  A thread holds up to kGSlots words of a unit in registers: with
+// RP = 1 (RG <= 512) the words of row group t % RG in columns
+// 8 (t / RG) .. 8 (t / RG) + 7; with RP = 2 or 4 (taller instances, whose
+// units have at most 8 / RP columns) the words of row groups t + 512 k
+// (k < RP) in every column of the unit.  The thread keeps its rows' residual
+// r and its share of the next accumulator A z in registers for as long as the
+// CTA stays in the instance, so each tile is read from shared memory once.
+constexpr int kGSlots = 8;
+
+struct InstMap {
+    int i, m, n, ld, RG, RP;
+    int PR;              // dot partials per column (row groups, or threads)
+    int p;               // this thread's partial index
+    int rg0, col0;       // first row group and column
+    int valid;           // the thread owns words of this instance
+    int shared_rows;     // several threads own the same rows (acc_s gathers them)
+    int64_t bo, xo;
+    float Li, mu, cs;
+};
+
+__device__ __forceinline__ void map_instance(const GArgs& g, int i, InstMap& im) {
+    const int t = threadIdx.x;
+    im.i = i;
+    im.m = g.m[i];
+    im.n = g.n[i];
+    im.ld = g.ld[i];
+    im.RG = im.ld / (g.bf16 ? 8 : 4);
+    im.RP = im.RG <= kGThreads ? 1 : (im.RG <= 2 * kGThreads ? 2 : 4);
+    if (im.RP == 1) {
+        const int S = (min(g.ucols[i], im.n) + 7) / 8;
+        im.rg0 = t % im.RG;
+        im.col0 = 8 * (t / im.RG);
+        im.valid = t < im.RG * S;
+        im.PR = im.RG;
+        im.p = im.rg0;
+        // rows shared by several slices are gathered in acc_s; the host's
+        // unit sizing gives S > 1 only to instances of at most kGShared rows
+        // (the guard keeps taller ones on direct global atomics)
+        im.shared_rows = S > 1 && im.ld <= kGShared;
+    } else {
+        im.rg0 = t;
+        im.col0 = 0;
+        im.valid = 1;
+        im.PR = kGThreads;
+        im.p = t;
+        im.shared_rows = 0;
+    }
+    im.bo = g.boff[i];
+    im.xo = g.xoff[i];
+    im.Li = g.mode == GM_FISTA ? 1.0f / g.L[i] : 0.0f;
+    im.mu = g.mode == GM_FISTA ? g.mu[i] : 0.0f;
+    im.cs = g.mode == GM_POWER ? g.cscale[i] : 0.0f;
+}
+
+// Enter an instance: this thread's rows of the residual (FISTA: b - A z from
+// the previous step's accumulator; power: A v) and a zero accumulator.
+template <bool BF, int RP>
+__device__ __forceinline__ void enter_regs(const GArgs& g, const InstMap& im, const float* racc_cur, float* r,
+                                           float* acc) {
+    constexpr int E = BF ? 8 : 4;
+#pragma unroll
+    for (int k = 0; k < RP; ++k) {
+        const int rg = im.rg0 + kGThreads * k;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int row = rg * E + e;
+            float v = 0.0f;
+            if (im.valid && rg < im.RG && row < im.m) {
+                if (g.mode == GM_FISTA) v = g.b[im.bo + row] - racc_cur[im.bo + row];
+                else if (g.mode == GM_POWER) v = racc_cur[im.bo + row];
+            }
+            r[k * E + e] = v;
+            acc[k * E + e] = 0.0f;
+        }
+    }
+}
+
+// Load this thread's words of a staged unit into registers and, in the modes
+// that need A^T r, write its partial dot per column to part_s.
+template <bool BF, int RP>
+__device__ __forceinline__ void load_unit(const InstMap& im, int nc, const uint8_t* tile, bool dots,
+                                          const float* r, uint4* a, float* part_s) {
+    constexpr int E = BF ? 8 : 4;
+    constexpr int CPS = kGSlots / RP;
+    const size_t colb = (size_t)im.ld * (BF ? 2 : 4);
+#pragma unroll
+    for (int k = 0; k < RP; ++k) {
+        const int rg = im.rg0 + kGThreads * k;
+#pragma unroll
+        for (int c = 0; c < CPS; ++c) {
+            const int col = im.col0 + c;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (im.valid && rg < im.RG && col < nc)
+                v = *reinterpret_cast<const uint4*>(tile + (size_t)col * colb + (size_t)rg * 16);
+            a[k * CPS + c] = v;
+        }
+    }
+    if (!dots || !im.valid) return;
+#pragma unroll
+    for (int c = 0; c < CPS; ++c) {
+        float d = 0.0f;
+#pragma unroll
+        for (int k = 0; k < RP; ++k) {
+            const uint4 w = a[k * CPS + c];
+            const float* rk = r + k * E;
+            if (BF) {
+                d = fmaf(bf_lo(w.x), rk[0], d);
+                d = fmaf(bf_hi(w.x), rk[1], d);
+                d = fmaf(bf_lo(w.y), rk[2], d);
+                d = fmaf(bf_hi(w.y), rk[3], d);
+                d = fmaf(bf_lo(w.z), rk[4], d);
+                d = fmaf(bf_hi(w.z), rk[5], d);
+                d = fmaf(bf_lo(w.w), rk[6], d);
+                d = fmaf(bf_hi(w.w), rk[7], d);
+            } else {
+                d = fmaf(__uint_as_float(w.x), rk[0], d);
+                d = fmaf(__uint_as_float(w.y), rk[1], d);
+                d = fmaf(__uint_as_float(w.z), rk[2], d);
+                d = fmaf(__uint_as_float(w.w), rk[3], d);
+            }
+        }
+        const int col = im.col0 + c;
+        if (col < nc) part_s[col * im.PR + im.p] = d;
+    }
+}
+
+// acc(rows) += sum_c A(rows, c) z_c over the thread's words of the unit.
+template <bool BF, int RP>
+__device__ __forceinline__ void accumulate_unit(const InstMap& im, int nc, const uint4* a, const float* zj_s,
+                                                float* acc) {
+    constexpr int E = BF ? 8 : 4;
+    constexpr int CPS = kGSlots / RP;
+    if (!im.valid) return;
+#pragma unroll
+    for (int c = 0; c < CPS; ++c) {
+        const int col = im.col0 + c;
+        const float z = col < nc ? zj_s[col] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < RP; ++k) {
+            const uint4 w = a[k * CPS + c];
+            float* ak = acc + k * E;
+            if (BF) {
+                ak[0] = fmaf(bf_lo(w.x), z, ak[0]);
+                ak[1] = fmaf(bf_hi(w.x), z, ak[1]);
+                ak[2] = fmaf(bf_lo(w.y), z, ak[2]);
+                ak[3] = fmaf(bf_hi(w.y), z, ak[3]);
+                ak[4] = fmaf(bf_lo(w.z), z, ak[4]);
+                ak[5] = fmaf(bf_hi(w.z), z, ak[5]);
+                ak[6] = fmaf(bf_lo(w.w), z, ak[6]);
+                ak[7] = fmaf(bf_hi(w.w), z, ak[7]);
+            } else {
+                ak[0] = fmaf(__uint_as_float(w.x), z, ak[0]);
+                ak[1] = fmaf(__uint_as_float(w.y), z, ak[1]);
+                ak[2] = fmaf(__uint_as_float(w.z), z, ak[2]);
+                ak[3] = fmaf(__uint_as_float(w.w), z, ak[3]);
+            }
+        }
+    }
+}
+
+// Leave an instance: this thread's share of A z goes to the global
+// accumulator, or first to acc_s where several threads own the same rows.
+template <bool BF, int RP>
+__device__ __forceinline__ void flush_regs(const InstMap& im, const float* acc, float* racc_next, float* acc_s) {
+    constexpr int E = BF ? 8 : 4;
+    if (!im.valid) return;
+#pragma unroll
+    for (int k = 0; k < RP; ++k) {
+        const int rg = im.rg0 + kGThreads * k;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int row = rg * E + e;
+            if (rg < im.RG && row < im.m) {
+                if (im.shared_rows) atomicAdd(&acc_s[row], acc[k * E + e]);
+                else atomicAdd(&racc_next[im.bo + row], acc[k * E + e]);
+            }
+        }
+    }
+}
+
+// The register-held parts are instantiated per (element type, RP); an
+// instance's map picks one (BF16 units are at most 8192 rows, so RP <= 2).
+#define GROUP_DISPATCH(FN, ...)                                       \
+    do {                                                              \
+        if (g.bf16) {                                                 \
+            if (im.RP == 1) FN<true, 1>(__VA_ARGS__);                 \
+            else FN<true, 2>(__VA_ARGS__);                            \
+        } else {                                                      \
+            if (im.RP == 1) FN<false, 1>(__VA_ARGS__);                \
+            else if (im.RP == 2) FN<false, 2>(__VA_ARGS__);           \
+            else FN<false, 4>(__VA_ARGS__);                           \
+        }                                                             \
+    } while (0)
 
 // Per-unit column state, loaded before the tile arrives: x_c, z_c for the
 // thread's column c = threadIdx.x < nc.
@@ -226,147 +423,85 @@ __device__ __forceinline__ ColState load_cols(const GArgs& g, const UnitGeom& q)
     return cs;
 }
 
-// Columns of one staged tile: g_J = A_J^T r (when the tile has fewer columns
-// than warps, G warps share a column and leave partial dots in dot_s), then
-// threads c < nc apply the per-mode update, write z_c to zj_s and accumulate
-// their columns' reduction terms in d2 / w2.  Ends with a block barrier.
-__device__ __forceinline__ void tile_columns(const GArgs& g, const UnitGeom& q, const uint8_t* tile,
-                                             const float* r_s, float* dot_s, float* zj_s, const ColState& cst,
-                                             float Li, float mu, double& d2, double& w2) {
+// The columns of a unit, one warp per column: g_c = sum of the column's dot
+// partials (A_J^T r), then the per-mode update of x_c, z_c by lane 0, which
+// writes z_c to zj_s and adds the column's reduction terms to d2 / w2.
+__device__ __forceinline__ void unit_columns(const GArgs& g, const UnitGeom& q, const InstMap& im,
+                                             const float* part_s, const ColState* cst_s, float* zj_s, double& d2,
+                                             double& w2) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = q.i, ld = q.ld, nc = q.nc;
     const bool dots = g.mode == GM_FISTA || g.mode == GM_POWER;
-    const int G = nc >= kGWarps ? 1 : kGWarps / nc;  // warps per column
-    if (dots) {
-        const int c_first = G == 1 ? warp : warp / G, c_step = G == 1 ? kGWarps : nc;
-        const int gi = G == 1 ? 0 : warp % G;
-        if (warp < nc * G) {
-            for (int c = c_first; c < nc; c += c_step) {
-                float dot = 0.0f;
-                if (g.bf16) {
-                    const int RG = ld / 8;
-                    const uint4* col = reinterpret_cast<const uint4*>(tile + (size_t)c * ld * 2);
-                    for (int v = gi * 32 + lane; v < RG; v += 32 * G) {
-                        const uint4 a = col[v];
-                        dot = fmaf(bf_lo(a.x), r_s[v], dot);
-                        dot = fmaf(bf_hi(a.x), r_s[RG + v], dot);
-                        dot = fmaf(bf_lo(a.y), r_s[2 * RG + v], dot);
-                        dot = fmaf(bf_hi(a.y), r_s[3 * RG + v], dot);
-                        dot = fmaf(bf_lo(a.z), r_s[4 * RG + v], dot);
-                        dot = fmaf(bf_hi(a.z), r_s[5 * RG + v], dot);
-                        dot = fmaf(bf_lo(a.w), r_s[6 * RG + v], dot);
-                        dot = fmaf(bf_hi(a.w), r_s[7 * RG + v], dot);
-                    }
-                } else {
-                    const int RG = ld / 4;
-                    const float4* col = reinterpret_cast<const float4*>(tile + (size_t)c * ld * 4);
-                    for (int v = gi * 32 + lane; v < RG; v += 32 * G) {
-                        const float4 a = col[v];
-                        dot = fmaf(a.x, r_s[v], dot);
-                        dot = fmaf(a.y, r_s[RG + v], dot);
-                        dot = fmaf(a.z, r_s[2 * RG + v], dot);
-                        dot = fmaf(a.w, r_s[3 * RG + v], dot);
-                    }
-                }
-                dot = warp_sum_f(dot);
-                if (lane == 0) dot_s[c * G + gi] = dot;
-            }
-        }
-        __syncthreads();
-    }
-    const int c = threadIdx.x;
-    if (c < nc) {
+    for (int c = warp; c < q.nc; c += kGWarps) {
         float dot = 0.0f;
-        if (dots)
-            for (int k = 0; k < G; ++k) dot += dot_s[c * G + k];
-        const int64_t j = g.xoff[i] + q.col0 + c;
-        float zn;
-        if (g.mode == GM_FISTA) {
-            // Eq. 18: x = soft(z + A^T(b - A z)/L, lambda/L), z' = x + mu (x - x_old)
-            const float xn = soft_g(fmaf(dot, Li, cst.z), g.lambda * Li);
-            zn = fmaf(mu, xn - cst.x, xn);
-            g.x[j] = xn;
-            g.z[j] = zn;
-            const float dx = xn - cst.x;
-            d2 += (double)dx * dx;
-            w2 += (double)cst.x * cst.x;
-        } else if (g.mode == GM_POWER) {
-            zn = dot * g.cscale[i];  // v' = A^T A v scaled to about unit norm
-            g.x[j] = zn;
-            d2 += (double)zn * zn;
-        } else if (g.mode == GM_POWER_INIT) {
-            zn = rsqrtf((float)q.n);
-            g.x[j] = zn;
-            d2 += (double)zn * zn;
-        } else {  // GM_FINAL: A x
-            zn = cst.x;
-            w2 += fabs((double)zn);
+        if (dots) {
+            const float* pc = part_s + c * im.PR;
+            for (int p = lane; p < im.PR; p += 32) dot += pc[p];
+            dot = warp_sum_f(dot);
         }
-        zj_s[c] = zn;
+        if (lane == 0) {
+            const int64_t j = im.xo + q.col0 + c;
+            const ColState cs = cst_s[c];
+            float zn;
+            if (g.mode == GM_FISTA) {
+                // Eq. 18: x = soft(z + A^T(b - A z)/L, lambda/L), z' = x + mu (x - x_old)
+                const float xn = soft_g(fmaf(dot, im.Li, cs.z), g.lambda * im.Li);
+                zn = fmaf(im.mu, xn - cs.x, xn);
+                g.x[j] = xn;
+                g.z[j] = zn;
+                const float dx = xn - cs.x;
+                d2 += (double)dx * dx;
+                w2 += (double)cs.x * cs.x;
+            } else if (g.mode == GM_POWER) {
+                zn = dot * im.cs;  // v' = A^T A v scaled to about unit norm
+                g.x[j] = zn;
+                d2 += (double)zn * zn;
+            } else if (g.mode == GM_POWER_INIT) {
+                zn = rsqrtf((float)im.n);
+                g.x[j] = zn;
+                d2 += (double)zn * zn;
+            } else {  // GM_FINAL: A x
+                zn = cs.x;
+                w2 += fabs((double)zn);
+            }
+            zj_s[c] = zn;
+        }
     }
-    __syncthreads();
 }
 
-// acc_s[r] += sum_c A(r, c) z_c over the staged tile.  Threads take groups of
-// 8 (BF16) or 4 (FP32) consecutive rows; when an instance has fewer row
-// groups than threads, several threads share a row group over disjoint column
-// slices and combine with shared-memory atomics.
-__device__ __forceinline__ void tile_accumulate(const GArgs& g, const UnitGeom& q, const uint8_t* tile,
-                                                const float* zj_s, float* acc_s) {
-    const int ld = q.ld;
-    if (g.bf16) {
-        const int RG = ld / 8;
-        const int span = RG >= kGThreads ? kGThreads : RG;
-        const int CS = RG >= kGThreads ? 1 : kGThreads / RG;
-        const int cs = threadIdx.x / span;
-        if (cs >= CS) return;
-        for (int rg = threadIdx.x % span; rg < RG; rg += span) {
-            float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int c = cs; c < q.nc; c += CS) {
-                const uint4 a = reinterpret_cast<const uint4*>(tile + (size_t)c * ld * 2)[rg];
-                const float z = zj_s[c];
-                s[0] = fmaf(bf_lo(a.x), z, s[0]);
-                s[1] = fmaf(bf_hi(a.x), z, s[1]);
-                s[2] = fmaf(bf_lo(a.y), z, s[2]);
-                s[3] = fmaf(bf_hi(a.y), z, s[3]);
-                s[4] = fmaf(bf_lo(a.z), z, s[4]);
-                s[5] = fmaf(bf_hi(a.z), z, s[5]);
-                s[6] = fmaf(bf_lo(a.w), z, s[6]);
-                s[7] = fmaf(bf_hi(a.w), z, s[7]);
-            }
-            if (CS == 1) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) acc_s[k * RG + rg] += s[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) atomicAdd(&acc_s[k * RG + rg], s[k]);
-            }
+// Leave instance i: gather acc_s into the global accumulator (when rows are
+// shared) and add the CTA's reduction terms to the instance's sums.  Ends
+// with a block barrier.
+__device__ __forceinline__ void flush_instance(const GArgs& g, const InstMap& im, float* racc_next,
+                                               const float* acc_s, double* red_s, double& d2, double& w2) {
+    if (im.shared_rows) {
+        __syncthreads();
+        for (int r = threadIdx.x; r < im.m; r += blockDim.x) atomicAdd(&racc_next[im.bo + r], acc_s[r]);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double wd2 = warp_sum(d2), ww2 = warp_sum(w2);
+    if (lane == 0) {
+        red_s[warp] = wd2;
+        red_s[kGWarps + warp] = ww2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int w = 0; w < kGWarps; ++w) {
+            s1 += red_s[w];
+            s2 += red_s[kGWarps + w];
         }
-    } else {
-        const int RG = ld / 4;
-        const int span = RG >= kGThreads ? kGThreads : RG;
-        const int CS = RG >= kGThreads ? 1 : kGThreads / RG;
-        const int cs = threadIdx.x / span;
-        if (cs >= CS) return;
-        for (int rg = threadIdx.x % span; rg < RG; rg += span) {
-            float s[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int c = cs; c < q.nc; c += CS) {
-                const float4 a = reinterpret_cast<const float4*>(tile + (size_t)c * ld * 4)[rg];
-                const float z = zj_s[c];
-                s[0] = fmaf(a.x, z, s[0]);
-                s[1] = fmaf(a.y, z, s[1]);
-                s[2] = fmaf(a.z, z, s[2]);
-                s[3] = fmaf(a.w, z, s[3]);
-            }
-            if (CS == 1) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc_s[k * RG + rg] += s[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) atomicAdd(&acc_s[k * RG + rg], s[k]);
-            }
+        if (g.mode == GM_FISTA) {
+            atomicAdd(&g.d2[im.i], s1);
+            atomicAdd(&g.w2[im.i], s2);
+        } else if (g.mode == GM_FINAL) {
+            atomicAdd(&g.w2[im.i], s2);
+        } else {
+            atomicAdd(&g.vv[im.i], s1);
         }
     }
+    d2 = 0.0;
+    w2 = 0.0;
+    __syncthreads();
 }
 
 // rebuild the active-instance list and unit prefix (block 0 only)
@@ -412,78 +547,24 @@ __device__ void group_rebuild(const GArgs& g, int64_t* scan_s) {
     }
 }
 
-// Enter instance i: stage its residual (FISTA: b - A z; power: A v) and
-// clear the shared accumulator of its next A z (padding rows zero).
-__device__ __forceinline__ void stage_instance(const GArgs& g, int i, const float* racc_cur, float* r_s,
-                                               float* acc_s) {
-    const int m = g.m[i], ld = g.ld[i];
-    const int64_t bo = g.boff[i];
-    const bool dots = g.mode == GM_FISTA || g.mode == GM_POWER;
-    const int E = g.bf16 ? 8 : 4, RG = ld / E;
-    for (int r = threadIdx.x; r < ld; r += blockDim.x) {
-        float v = 0.0f;
-        if (dots && r < m) {
-            const float acc = racc_cur[bo + r];
-            v = g.mode == GM_FISTA ? g.b[bo + r] - acc : acc;
-        }
-        const int o = soa_index(r, E, RG);
-        r_s[o] = v;
-        acc_s[o] = 0.0f;
-    }
-    __syncthreads();
-}
 
-// Leave instance i: add the CTA's share of A z to the global accumulator and
-// its reduction terms to the instance's sums.
-__device__ __forceinline__ void flush_instance(const GArgs& g, int i, float* racc_next, const float* acc_s,
-                                               double* red_s, double& d2, double& w2) {
-    const int m = g.m[i], E = g.bf16 ? 8 : 4, RG = g.ld[i] / E;
-    const int64_t bo = g.boff[i];
-    for (int r = threadIdx.x; r < m; r += blockDim.x) atomicAdd(&racc_next[bo + r], acc_s[soa_index(r, E, RG)]);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double wd2 = warp_sum(d2), ww2 = warp_sum(w2);
-    if (lane == 0) {
-        red_s[warp] = wd2;
-        red_s[kGWarps + warp] = ww2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int w = 0; w < kGWarps; ++w) {
-            s1 += red_s[w];
-            s2 += red_s[kGWarps + w];
-        }
-        if (g.mode == GM_FISTA) {
-            atomicAdd(&g.d2[i], s1);
-            atomicAdd(&g.w2[i], s2);
-        } else if (g.mode == GM_FINAL) {
-            atomicAdd(&g.w2[i], s2);
-        } else {
-            atomicAdd(&g.vv[i], s1);
-        }
-    }
-    d2 = 0.0;
-    w2 = 0.0;
-    __syncthreads();
-}
 
-__global__ void __launch_bounds__(kGThreads) group_kernel(GArgs g) {
+__global__ void __launch_bounds__(kGThreads, 1) group_kernel(GArgs g) {
     extern __shared__ __align__(128) uint8_t gsm[];
-    float* r_s = reinterpret_cast<float*>(gsm);                               // kGMaxM floats
-    float* acc_s = r_s + kGMaxM;                                              // kGMaxM floats
-    uint8_t* tiles[2] = {gsm + 2 * kGMaxM * sizeof(float),                    // 2 x kGTileBytes
-                         gsm + 2 * kGMaxM * sizeof(float) + kGTileBytes};
-    float* zj_s = reinterpret_cast<float*>(tiles[1] + kGTileBytes);           // 256 floats
-    float* dot_s = zj_s + 256;                                                // 256 floats
-    double* red_s = reinterpret_cast<double*>(dot_s + 256);                   // 2 * kGWarps
+    uint8_t* tiles[kGBufs];                                                   // kGBufs x kGTileBytes
+    for (int k = 0; k < kGBufs; ++k) tiles[k] = gsm + k * kGTileBytes;
+    float* acc_s = reinterpret_cast<float*>(gsm + kGBufs * kGTileBytes);      // kGShared floats
+    float* part_s = acc_s + kGShared;                                         // kGPartials floats
+    float* zj_s = part_s + kGPartials;                                        // 256 floats
+    ColState* cst_s = reinterpret_cast<ColState*>(zj_s + 256);                // 256
+    double* red_s = reinterpret_cast<double*>(cst_s + 256);                   // 2 * kGWarps
     int64_t* scan_s = reinterpret_cast<int64_t*>(red_s + 2 * kGWarps);        // kGThreads
-    uint64_t* bars = reinterpret_cast<uint64_t*>(scan_s + kGThreads);         // 2
-    __shared__ UnitGeom geo_s[2];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(scan_s + kGThreads);         // kGBufs
+    __shared__ UnitGeom geo_s[kGBufs];
     __shared__ int abort_s;
     if (threadIdx.x == 0) {
         abort_s = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(g_smem(&bars[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(g_smem(&bars[1])));
+        for (int k = 0; k < kGBufs; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(g_smem(&bars[k])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -491,81 +572,94 @@ __global__ void __launch_bounds__(kGThreads) group_kernel(GArgs g) {
     const int nwarps_grid = gridDim.x * kGWarps;
     const int gwarp = blockIdx.x * kGWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase[kGBufs] = {0u, 0u, 0u};
+    // this thread's rows of the current instance: residual, accumulator
+    float r[16], acc[16];
+    uint4 a[kGSlots];
 
     for (int step = 0; step < g.max_steps; ++step) {
         const int cur = step & 1;
         const int nact = *(volatile int32_t*)g.nact;
         if (nact == 0) break;
         const int64_t total = g.upref[nact];
+        const bool dots = g.mode == GM_FISTA || g.mode == GM_POWER;
         // ---- pass over this CTA's contiguous range of active units
         {
             const float* racc_cur = cur ? g.racc1 : g.racc0;
             float* racc_next = cur ? g.racc0 : g.racc1;
             const int64_t per = (total + gridDim.x - 1) / gridDim.x;
             const int64_t u0 = min(total, (int64_t)blockIdx.x * per), u1 = min(total, u0 + per);
-            // thread 0 keeps two units in flight: the geometry of the units in
-            // buffers 0 and 1 lives in geo_s; the copy of unit u + 2 is issued
-            // as soon as unit u's buffer is free
-            bool pending[2] = {false, false};
+            // thread 0 keeps kGBufs units in flight: the geometry of the unit
+            // in buffer k lives in geo_s[k]; the copy of unit u + kGBufs is
+            // issued as soon as every thread has taken unit u's words into
+            // registers
+            bool pending[kGBufs] = {false, false, false};
             if (threadIdx.x == 0 && u0 < u1) {
                 geo_s[0] = geom_first(g, u0, nact);
                 issue_tile(g, geo_s[0], tiles[0], &bars[0]);
-                if (u0 + 1 < u1) {
-                    geo_s[1] = geom_next(g, geo_s[0]);
-                    issue_tile(g, geo_s[1], tiles[1], &bars[1]);
+                for (int k = 1; k < kGBufs && u0 + k < u1; ++k) {
+                    geo_s[k] = geom_next(g, geo_s[k - 1]);
+                    issue_tile(g, geo_s[k], tiles[k], &bars[k]);
                 }
             }
-            if (u0 < u1) pending[0] = true;
-            if (u0 + 1 < u1) pending[1] = true;
+            for (int k = 0; k < kGBufs; ++k) pending[k] = u0 + k < u1;
             __syncthreads();
-            int cur_i = -1;
-            float Li = 0.0f, mu = 0.0f;
+            InstMap im;
+            im.i = -1;
             double d2 = 0.0, w2 = 0.0;
             bool failed = false;
             for (int64_t u = u0; u < u1; ++u) {
-                const int b = (int)((u - u0) & 1);
+                const int b = (int)((u - u0) % kGBufs);
                 const UnitGeom q = geo_s[b];
                 const ColState cst = load_cols(g, q);  // in flight while the tile lands
-                if (q.i != cur_i) {
-                    if (cur_i >= 0) flush_instance(g, cur_i, racc_next, acc_s, red_s, d2, w2);
-                    stage_instance(g, q.i, racc_cur, r_s, acc_s);
-                    cur_i = q.i;
-                    if (g.mode == GM_FISTA) {
-                        Li = 1.0f / g.L[cur_i];
-                        mu = g.mu[cur_i];
+                if (q.i != im.i) {
+                    if (im.i >= 0) {
+                        GROUP_DISPATCH(flush_regs, im, acc, racc_next, acc_s);
+                        flush_instance(g, im, racc_next, acc_s, red_s, d2, w2);
                     }
+                    map_instance(g, q.i, im);
+                    if (im.shared_rows)
+                        for (int row = threadIdx.x; row < im.ld; row += blockDim.x) acc_s[row] = 0.0f;
+                    GROUP_DISPATCH(enter_regs, g, im, racc_cur, r, acc);
                 }
-                // every thread polls; the block agrees on the outcome
                 const bool ok = g_mbar_wait(&bars[b], phase[b]);
+                if (ok) GROUP_DISPATCH(load_unit, im, q.nc, tiles[b], dots, r, a, part_s);
+                if ((int)threadIdx.x < q.nc) cst_s[threadIdx.x] = cst;
+                // the block agrees on the copy's outcome; every thread has
+                // its words of the unit, so the buffer may be refilled
                 if (__syncthreads_or(!ok)) {
                     failed = true;
                     break;
                 }
                 phase[b] ^= 1u;
                 pending[b] = false;
-                tile_columns(g, q, tiles[b], r_s, dot_s, zj_s, cst, Li, mu, d2, w2);
-                tile_accumulate(g, q, tiles[b], zj_s, acc_s);
-                __syncthreads();
-                if (u + 2 < u1) {
+                if (u + kGBufs < u1) {
                     if (threadIdx.x == 0) {
-                        const UnitGeom q2 = geom_next(g, geo_s[b ^ 1]);
+                        // unit u + kGBufs follows unit u + kGBufs - 1, which
+                        // sits in the buffer before this one
+                        const UnitGeom q2 = geom_next(g, geo_s[(b + kGBufs - 1) % kGBufs]);
                         geo_s[b] = q2;
                         issue_tile(g, q2, tiles[b], &bars[b]);
                     }
                     pending[b] = true;
                 }
+                unit_columns(g, q, im, part_s, cst_s, zj_s, d2, w2);
+                __syncthreads();
+                GROUP_DISPATCH(accumulate_unit, im, q.nc, a, zj_s, acc);
             }
             if (failed) {
                 // a copy did not complete in time: record it, give the copies
                 // in flight a last bounded wait, and leave
                 if (threadIdx.x == 0) atomicCAS(g.err, 0, 2);
-                for (int k = 0; k < 2; ++k)
+                for (int k = 0; k < kGBufs; ++k)
                     if (pending[k]) g_mbar_wait(&bars[k], phase[k]);
                 *abort = 1;
                 return;
             }
-            if (cur_i >= 0) flush_instance(g, cur_i, racc_next, acc_s, red_s, d2, w2);
+            if (im.i >= 0) {
+                GROUP_DISPATCH(flush_regs, im, acc, racc_next, acc_s);
+                flush_instance(g, im, racc_next, acc_s, red_s, d2, w2);
+            }
         }
         if (!grid_sync(g, abort)) return;
         // ---- per-instance finalisation: one warp per active instance
@@ -632,6 +726,7 @@ __global__ void __launch_bounds__(kGThreads) group_kernel(GArgs g) {
         if (!grid_sync(g, abort)) return;
     }
 }
+
 
 // ------------------------------------------------------------------- host
 __global__ void quantize_store_kernel(const float* src, int m, int n, int ld, void* dst, int64_t off, int bf16) {
@@ -782,8 +877,13 @@ int group_setup(Handle* h, const float* const* A, const int64_t* m, const int64_
         if (m[i] <= 0 || n[i] <= 0 || m[i] > kGMaxM || n[i] > (1 << 24)) return L1_ERR_INVALID_ARG;
         const int mi = (int)m[i], ni = (int)n[i];
         const int ld = (int)round_up(mi, 8);
-        int uc = kGTileBytes / (esize * ld);
-        uc = std::max(1, std::min(uc, 256));
+        // columns per unit: a full unit is exactly kGThreads register words
+        // (a multiple of 8 columns), or 8 / RP columns for taller instances
+        const int cap = kGTileBytes / (esize * ld);
+        const int rg = ld * esize / 16;
+        int uc;
+        if (rg <= kGThreads) uc = std::min(256, 8 * (cap / 8));
+        else uc = rg <= 2 * kGThreads ? 4 : 2;
         G->hm[i] = mi; G->hn[i] = ni; G->hld[i] = ld; G->hucols[i] = uc;
         G->haoff[i] = ao; G->hboff[i] = bo; G->hxoff[i] = xo;
         G->hnunits[i] = (ni + uc - 1) / uc;
@@ -822,8 +922,8 @@ int group_setup(Handle* h, const float* const* A, const int64_t* m, const int64_
     L1_CUDA_TRY(cudaMemcpy(G->xoff, G->hxoff.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice));
     L1_CUDA_TRY(cudaMemcpy(G->nunits, G->hnunits.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice));
     // cooperative grid: every block resident
-    G->smem = 2 * kGMaxM * (int)sizeof(float) + 2 * kGTileBytes + 2 * 256 * (int)sizeof(float) +
-              2 * kGWarps * 8 + kGThreads * 8 + 2 * 8;
+    G->smem = kGBufs * kGTileBytes + (kGShared + kGPartials + 256) * (int)sizeof(float) +
+              256 * (int)sizeof(ColState) + 2 * kGWarps * 8 + kGThreads * 8 + kGBufs * 8;
     L1_CUDA_TRY(cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G->smem));
     int per_sm = 0, sms = 0;
     L1_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, group_kernel, kGThreads, G->smem));

@@ -303,6 +303,19 @@ static int ensure_workspace(Handle* h, int N) {
             h->splitk_floats = need;
         }
     }
+    if (h->use_tc && h->tc_wk) {
+        // the tensor-core sweeps' FP32 tile sums (split-K slices, deferred
+        // epilogues): every output tile of the widest sweep at this width
+        const size_t tm = (size_t)(std::max(m, n) + 127) / 128, tn = (size_t)(N + 127) / 128;
+        const size_t need = std::max((size_t)(h->sms > 0 ? h->sms : 152), tm * tn) * 128 * 128;
+        if (need > h->tc_wk_elems) {
+            dev_free(h, h->tc_wk);
+            h->tc_wk = nullptr;
+            h->tc_wk_elems = 0;
+            L1_TRY(dev_alloc_t(h, &h->tc_wk, need));
+            h->tc_wk_elems = need;
+        }
+    }
     L1_TRY(dev_alloc_t(h, &w.newpos, (size_t)N));
     L1_TRY(dev_alloc_t(h, &w.count, 1));
     if (cudaMallocHost(&w.h_count, 2 * sizeof(int32_t)) != cudaSuccess) return L1_ERR_OOM;
@@ -775,8 +788,25 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     // ---- classification (CAB with classes)
     const int C = (int)h->class_offsets.size() - 1;
     if (cab && C > 0) {
-        classify_resid_kernel<<<dim3(C, N), 128, 0, s>>>(h->A_rm, ldn, m, w.class_off, w.hB, w.hWe, w.hWx, ldm,
-                                                          ldn, N, w.resid2, w.classl1);
+        int csz_max = 0;
+        for (int c = 0; c < C; ++c) csz_max = std::max(csz_max, h->class_offsets[c + 1] - h->class_offsets[c]);
+        constexpr int kClassSmem = 160 * 1024;
+        if ((size_t)csz_max * 32 * sizeof(float) <= kClassSmem) {
+            const int sm = csz_max * 32 * (int)sizeof(float);
+            L1_CUDA_TRY(cudaFuncSetAttribute(classify_tile_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kClassSmem));
+            classify_tile_kernel<32><<<dim3(C, (N + 31) / 32), 256, sm, s>>>(
+                h->A_cm, ldm, m, w.class_off, w.hB, w.hWe, w.hWx, ldn, N, w.resid2, w.classl1);
+        } else if ((size_t)csz_max * 4 * sizeof(float) <= kClassSmem) {
+            const int sm = csz_max * 4 * (int)sizeof(float);
+            L1_CUDA_TRY(cudaFuncSetAttribute(classify_tile_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kClassSmem));
+            classify_tile_kernel<4><<<dim3(C, (N + 3) / 4), 256, sm, s>>>(
+                h->A_cm, ldm, m, w.class_off, w.hB, w.hWe, w.hWx, ldn, N, w.resid2, w.classl1);
+        } else {
+            classify_resid_kernel<<<dim3(C, N), 128, 0, s>>>(h->A_rm, ldn, m, w.class_off, w.hB, w.hWe, w.hWx,
+                                                              ldm, ldn, N, w.resid2, w.classl1);
+        }
         L1_LAUNCH_CHECK(h);
         classify_argmin_kernel<<<(N + 127) / 128, 128, 0, s>>>(w.resid2, w.classl1, C, N, hr.label, hr.sci_label);
         L1_LAUNCH_CHECK(h);

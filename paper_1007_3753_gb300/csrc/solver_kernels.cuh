@@ -671,8 +671,74 @@ __global__ void final_metrics_kernel(int N, const float* smax_arr, double* fin, 
 
 // ----------------------------------------------------------- classification
 // Per-class residual ||b - e - A delta_c(x)||_2 (§II-A) and the l1 mass
-// ||delta_c(x)||_1 of the SCI rule (Eq. 40); one block per (class, column).
-// A is read row-major so a class's columns in one row are contiguous.
+// ||delta_c(x)||_1 of the SCI rule (Eq. 40).
+//
+// classify_tile_kernel<JT>: one block per (class, JT test vectors); the
+// class's coefficients of those vectors sit in shared memory (class size x
+// JT floats), and each thread walks rows i = t, t + blockDim, ...: it reads
+// the class's entries of row i from the column-major A (consecutive threads,
+// consecutive rows: coalesced), forms the JT products in FP32, and adds the
+// squared residuals b_ij - e_ij - (A delta_c(x_j))_i of its rows in FP32;
+// the threads' sums are added over each warp in FP32 and over the warps in
+// FP64, in a fixed order.  Blocks of one column tile run back to back, so the
+// tile's b and e are read from HBM once for all classes.
+template <int JT>
+__global__ void __launch_bounds__(256) classify_tile_kernel(const float* A_cm, int64_t ldm, int m,
+                                                            const int32_t* offsets, const float* B,
+                                                            const float* E, const float* Wx, int64_t ldn,
+                                                            int N, double* resid2, double* l1mass) {
+    extern __shared__ float xs[];  // [class size][JT]
+    __shared__ float wsum[8][JT];
+    const int cls = blockIdx.x, j0 = blockIdx.y * JT;
+    const int c0 = offsets[cls], csz = offsets[cls + 1] - c0;
+    for (int idx = threadIdx.x; idx < csz * JT; idx += blockDim.x) {
+        const int jj = idx / csz, k = idx % csz;
+        xs[k * JT + jj] = j0 + jj < N ? Wx[(int64_t)(j0 + jj) * ldn + c0 + k] : 0.0f;
+    }
+    __syncthreads();
+    float q[JT];
+#pragma unroll
+    for (int jj = 0; jj < JT; ++jj) q[jj] = 0.0f;
+    const float* Ac = A_cm + (int64_t)c0 * ldm;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        float sacc[JT];
+#pragma unroll
+        for (int jj = 0; jj < JT; ++jj) sacc[jj] = 0.0f;
+        for (int k = 0; k < csz; ++k) {
+            const float a = Ac[(int64_t)k * ldm + i];
+            const float* xk = xs + k * JT;
+#pragma unroll
+            for (int jj = 0; jj < JT; ++jj) sacc[jj] = fmaf(a, xk[jj], sacc[jj]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < JT; ++jj) {
+            if (j0 + jj < N) {
+                const int64_t o = (int64_t)(j0 + jj) * ldm + i;
+                const float v = B[o] - (E ? E[o] : 0.0f) - sacc[jj];
+                q[jj] = fmaf(v, v, q[jj]);
+            }
+        }
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int jj = 0; jj < JT; ++jj) {
+        const float sv = warp_sum_f(q[jj]);
+        if (lane == 0) wsum[w][jj] = sv;
+    }
+    __syncthreads();
+    if (threadIdx.x < JT && j0 + (int)threadIdx.x < N) {
+        const int jj = threadIdx.x;
+        double r2 = 0.0, l1v = 0.0;
+        for (int ww = 0; ww < 8; ++ww) r2 += (double)wsum[ww][jj];
+        for (int k = 0; k < csz; ++k) l1v += fabs((double)xs[k * JT + jj]);
+        resid2[(int64_t)cls * N + j0 + jj] = r2;
+        l1mass[(int64_t)cls * N + j0 + jj] = l1v;
+    }
+}
+
+// Classes too large for classify_tile_kernel's shared memory: one block per
+// (class, column); A is read row-major so a class's columns in one row are
+// contiguous.
 __global__ void classify_resid_kernel(const float* A_rm, int64_t lda_rm, int m,
                                       const int32_t* offsets, const float* B, const float* E,
                                       const float* Wx, int64_t ldm, int64_t ldn, int N,

@@ -64,21 +64,47 @@ inline int get_maps(Handle* h, int M, int N, int K, const Operands& op, int bn, 
     return L1_OK;
 }
 
-// K slices of a sweep with fewer output tiles than SMs (a narrow batch, or a
-// small dictionary): enough to give every SM one CTA, each slice whole
-// 128-element chunks; the slices' sums are added in slice order by
-// finish_kernel (deterministic for a given batch width).  Their scratch holds
-// ksplit x tiles x 128 x 128 floats <= SMs x 128 x 128.
-inline int ksplit(const Handle* h, int tiles, int K) {
-    const int sms = h->sms > 0 ? h->sms : 152;
+// How a sweep's output tiles are produced: K slices (ks > 1: split-K, the
+// slices' FP32 sums added in slice order by finish_kernel, deterministic for a
+// given batch width) and whether the tile epilogue runs in the sweep (fused)
+// or in finish_kernel from the tile's FP32 sums (deferred; always with
+// ks > 1).  The scratch holds ks x tiles x 128 x 128 floats.
+struct Split {
+    int ks, defer;
+};
+
+inline Split normalise(const Handle* h, int ks, int defer, int K, int tiles) {
     const int chunks = (K + kChunk - 1) / kChunk;
-    // (measured: two slices of the 64 tiles of a 1024 x 1024 batch lose to
-    // one, the finish pass costing more than the second wave of CTAs saves)
-    if (!h->tc_wk || 4 * tiles > sms || chunks < 4) return 1;
-    int ks = std::min(std::min(sms / tiles, chunks), 16);
+    ks = std::max(1, std::min(std::min(ks, chunks), 16));
     const int cps = (chunks + ks - 1) / ks;
-    return (chunks + cps - 1) / cps;  // no empty slice
+    ks = (chunks + cps - 1) / cps;  // no empty slice
+    Split r{ks, (ks > 1 || defer) ? 1 : 0};
+    if (r.defer && (size_t)r.ks * tiles * kBM * 128 > h->tc_wk_elems) r = Split{1, 0};
+    return r;
 }
+
+// The autotuner's choice for (M, K, tiles) (tune_splits): the entry of that
+// tile count, else of the nearest smaller one (its slice count capped at one
+// CTA per SM); without one, enough slices to give every SM a CTA when a
+// quarter of them has a tile, else fused.
+inline Split split_choice(const Handle* h, int M, int K, int tiles) {
+    const int sms = h->sms > 0 ? h->sms : 152;
+    if (!h->tc_wk) return Split{1, 0};
+    const std::array<int32_t, 6>* near = nullptr;
+    for (const auto& e : h->tc_splits)
+        if (e[0] == M && e[1] == K && e[2] <= tiles && (!near || e[2] > (*near)[2])) near = &e;
+    if (near) return normalise(h, std::min((*near)[3], std::max(1, sms / tiles)), (*near)[4], K, tiles);
+    const int chunks = (K + kChunk - 1) / kChunk;
+    if (4 * tiles > sms || chunks < 4) return Split{1, 0};
+    return normalise(h, std::min(sms / tiles, 16), 1, K, tiles);
+}
+
+// Time the tile strategies of each tensor-core sweep shape of the handle (A u,
+// the y-step, A^T y): fused, deferred and split-K with every useful slice
+// count, at tile counts from one column tile up to 4096 columns, on scratch
+// panels; record the fastest in h->tc_splits.  Skipped (fixed rule) when the
+// scratch cannot be allocated.
+int tune_splits(Handle* h);
 
 // One BF16 tensor-core sweep sum_t a_{ia(t)} x_{ix(t)} with epilogue epi
 // (gemm_bf16.cuh): operands split on the aligned grid of 128-element K
@@ -87,25 +113,23 @@ inline int ksplit(const Handle* h, int tiles, int K) {
 // row blocks (partials per column) or a negative error code.
 template <class E, int NPA, int NPX>
 int launch_inst(Handle* h, const Maps& maps, const Terms& tl, int M, int N, int K, const E& epi,
-                const PieceOut& po, double* part, const int32_t* active) {
+                const PieceOut& po, double* part, const int32_t* active, Split force = Split{0, 0}) {
     using S = Cfg<128, NPA, NPX>;
-    constexpr int NR = E::NRED > 0 ? E::NRED : 1;
     static bool attr_set = false;
     if (!attr_set) {
         L1_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<E, NPA, NPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          S::kBytes));
-        L1_CUDA_TRY(cudaFuncSetAttribute(finish_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         finish_smem<NR>()));
         attr_set = true;
     }
     const int tiles_m = (M + kBM - 1) / kBM, tiles = tiles_m * ((N + 127) / 128);
-    const int ks = ksplit(h, tiles, K);
-    sweep_kernel<E, NPA, NPX><<<tiles * ks, kThreads, S::kBytes, h->stream>>>(maps, tl, M, N, K, epi, po, part,
-                                                                              active, h->tc_err, ks, h->tc_wk);
+    const Split sp = force.ks > 0 ? normalise(h, force.ks, force.defer, K, tiles) : split_choice(h, M, K, tiles);
+    const int ks = sp.ks;
+    sweep_kernel<E, NPA, NPX><<<tiles * ks, kThreads, S::kBytes, h->stream>>>(
+        maps, tl, M, N, K, epi, po, part, active, h->tc_err, ks, sp.defer, h->tc_wk);
     L1_LAUNCH_CHECK(h);
-    if (ks > 1) {
-        finish_kernel<E><<<tiles, 32 * kEpiWarps, finish_smem<NR>(), h->stream>>>(M, N, ks, h->tc_wk, epi, po, part,
-                                                                                 active);
+    if (sp.defer) {
+        const int fin = tiles_m * ((N + kFinCols - 1) / kFinCols);
+        finish_kernel<E><<<fin, kBM, 0, h->stream>>>(M, N, ks, h->tc_wk, epi, po, part, active);
         L1_LAUNCH_CHECK(h);
     }
     return tiles_m;

@@ -545,3 +545,37 @@ def test_4096_workload_against_stored_oracle_answers(l1):
     ex.check()
     s.close()
     s4.close()
+
+
+def test_split_autotuner_records_choices_and_keeps_parity(l1):
+    """l1_setup's autotuner times the tile strategies (fused or deferred
+    epilogue, split-K) of the three tensor-core sweep shapes (A u: m x n, the
+    y-step: m x m, A^T y: n x m) at widths up to 4096 and keeps the fastest;
+    tune=False keeps the fixed rule.  A narrow batch solved on either handle
+    matches the oracle after the same iterations."""
+    p = synthetic.cab_problem(1024, 40, 30, 6, corrupt=0.3, seed=11)
+    A, B = p["A"], p["B"]
+    m, n = A.shape
+    s = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, engine=l1.ENGINE_TC, tc_min_cols=1)
+    t = s.tuning()
+    print("split-K choices:", t)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert len(t) > 0
+    for e in t:
+        assert (e["M"], e["K"]) in {(m, n), (m, m), (n, m)}
+        assert 1 <= e["ksplit"] <= 16 and e["us"] >= 0 and e["deferred"] in (0, 1)
+        assert e["ksplit"] == 1 or (e["deferred"] == 1 and e["tiles"] * e["ksplit"] <= sms)
+    s0 = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, engine=l1.ENGINE_TC, tc_min_cols=1, tune=False)
+    assert s0.tuning() == []
+    iters = 120
+    xa, _, _ = s.solve(_dev(B), tol=0.0, max_iter=iters)
+    xb, _, _ = s0.solve(_dev(B), tol=0.0, max_iter=iters)
+    xa, xb = xa.cpu().numpy(), xb.cpu().numpy()
+    ex = Errs("narrow TC batch, tuned and fixed split-K, 120 iterations")
+    for j in range(B.shape[1]):
+        w, _, _ = oracle.dalm(A, B[:, j], cab=True, tol=0.0, max_iter=iters)
+        ex.add(xa[:, j], w)
+        ex.add(xb[:, j], w)
+    ex.check()
+    s.close()
+    s0.close()
