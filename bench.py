@@ -361,9 +361,9 @@ def bench_ours(args, rank, world):
     # that times every sweep with CUDA events (the roofline), the others on
     # the one without events
     s = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec,
-                  stream=stream.cuda_stream)
+                  tune=not args.no_tune, stream=stream.cuda_stream)
     sp = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec,
-                   profile=True, stream=stream.cuda_stream)
+                   tune=not args.no_tune, profile=True, stream=stream.cuda_stream)
     setup_ms = s.info()["setup_ms"]
     tc = l1.load() is not None and engine != l1.ENGINE_SIMT and args.precision != "fp8"
     tol, max_iter = cfg["tol"], cfg["max_iter"]
@@ -726,6 +726,103 @@ def bench_unrolled(args, rank, world):
 
 # basis pursuit (Eq. 1) of §VI-A: A 200 x 400 Gaussian with unit columns,
 # x0 20-sparse with +-1 entries, b = A x0, tol 1e-6; 20 seeded instances
+# the convex alignment step of §II-B (reading R16): tall B_k = [training
+# images of one subject, -Jacobian] stand-ins, m = 1200 pixels, p = 11
+# (7 images + 4 transformation parameters), unit Gaussian columns, a planted
+# w0 ~ N(0, 1) and 10 % of the pixels grossly corrupted (5 N(0, 1))
+ALIGN = dict(m=1200, p=11, count=4096, frac=0.1, tol=1e-6, max_outer=5000, seed=6000)
+
+
+def align_problems(count, m, p, frac, seed):
+    g = np.random.default_rng(seed)
+    B = g.standard_normal((count, p, m))
+    B /= np.linalg.norm(B, axis=2, keepdims=True)
+    w0 = g.standard_normal((count, p))
+    e0 = np.zeros((count, m))
+    for k in range(count):
+        idx = g.choice(m, int(frac * m), replace=False)
+        e0[k, idx] = 5.0 * g.standard_normal(idx.size)
+    b = np.einsum("kpm,kp->km", B, w0) + e0
+    return B.astype(np.float32), b.astype(np.float32)
+
+
+def bench_align(args, rank, world):
+    """--workload align: count independent alignment steps in one launch
+    (l1_align_batch, one CTA per problem); a sample of 4 problems checked
+    against the FP64 oracle at the same tolerance."""
+    import torch
+
+    import paper_1007_3753_gb300 as l1
+    from paper_1007_3753_gb300 import build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    l1.load()
+    a = ALIGN
+    B, b = align_problems(a["count"], a["m"], a["p"], a["frac"], a["seed"] + rank)
+    Bd, bd = torch.from_numpy(B).cuda(), torch.from_numpy(b).cuda()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        l1.align_batch(Bd, bd, a["tol"], a["max_outer"])
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    step_ms, conv = [], 0
+    for _ in range(args.steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        w, e, res = l1.align_batch(Bd, bd, a["tol"], a["max_outer"])
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        conv += int(np.sum(res["status"] == l1.CONVERGED))
+    clocks = sampler.stop() if sampler else None
+    total_ms = sum(step_ms)
+    w, e = w.cpu().numpy(), e.cpu().numpy()
+    # the cpu_baseline leg: the FP64 oracle on a sample of the problems, one
+    # host thread, timed; its answers also verify the GPU's
+    import oracle
+    per, ok = [], 0
+    sample = (0, 1, a["count"] // 2, a["count"] - 1)
+    t_or = 0.0
+    for k in sample:
+        Bk = np.asfortranarray(B[k].T.astype(np.float64))
+        bk = b[k].astype(np.float64)
+        t0 = time.perf_counter()
+        wo, eo, _, st = oracle.palm_align(Bk, bk, tol=a["tol"], max_outer=a["max_outer"])
+        t_or += time.perf_counter() - t0
+        kg = int(res["iters"][k])
+        if abs(kg - st["iters"]) <= 1 and kg != st["iters"]:
+            wo, eo, _, _ = oracle.palm_align(Bk, bk, tol=0.0, max_outer=kg)
+        xw = float(np.linalg.norm(w[k] - wo) / np.linalg.norm(wo))
+        xe = float(np.linalg.norm(e[k] - eo) / np.linalg.norm(eo))
+        good = abs(kg - st["iters"]) <= 1 and xw <= 1e-4 and xe <= 1e-4
+        ok += int(good)
+        per.append({"problem": k, "stop_gpu_minus_oracle": kg - st["iters"], "rel_err_w": xw, "rel_err_e": xe,
+                    "verified": good})
+    frac_ok = ok / len(per)
+    # bytes of one problem: B_k and b_k in, w and e out, once per launch
+    bytes_per = 4.0 * (a["m"] * a["p"] + 2 * a["m"] + a["p"])
+    line = {"metric": "alignment steps/sec (min ||e||_1 s.t. b = B w + e, at rel. err <= 1e-4 vs FP64 oracle)",
+            "value": frac_ok * conv / (total_ms / 1e3), "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 products, f64 w-step and reductions", "data": "synthetic",
+            "config": {"workload": f"align_m{a['m']}_p{a['p']}_count{a['count']}", "tol": a["tol"],
+                       "corrupt_fraction": a["frac"], "mean_iters": float(np.mean(res["iters"])),
+                       "max_iters": int(np.max(res["iters"])),
+                       "l2": "every problem is read from HBM once into shared memory"},
+            "oracle_agreement": {"of": len(per), "within_bar": ok, "per_instance": per},
+            "cpu_baseline": {"value": len(sample) / t_or, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"problems {list(sample)}, orc_palm_align one after another on one thread"},
+            "hbm_bytes_per_step": bytes_per * a["count"], "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 P1 = dict(m=200, n=400, k=20, count=20, tol=1e-6, max_iter=5000)
 
 
@@ -813,7 +910,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--engine", choices=["auto", "tc", "simt"], default="auto",
                     help="cab: the library's automatic choice (the tensor-core engine for DALM) or a forced one")
-    ap.add_argument("--workload", choices=["cab4096", "cab1024", "qp-group", "unrolled", "p1"], default="cab4096")
+    ap.add_argument("--workload", choices=["cab4096", "cab1024", "qp-group", "unrolled", "p1", "align"],
+                    default="cab4096")
     ap.add_argument("--count", type=int, default=None, help="qp-group: number of instances")
     ap.add_argument("--max-iter", type=int, default=None, help="qp-group, or cab with --solve-only: iteration cap")
     ap.add_argument("--solve-only", action="store_true",
@@ -822,6 +920,9 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32",
                     help="cab: stored precision of A (bf16 / fp8 add the FP32 refinement phase)")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="cab: skip the CPU oracle timing")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="cab: the fixed tile rule instead of the setup-time autotuner (for runs under a profiler, "
+                         "whose per-launch overhead distorts the tuner's timings)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -831,6 +932,8 @@ def main():
         return bench_unrolled(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
     if args.workload == "p1":
         return bench_p1(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
+    if args.workload == "align":
+        return bench_align(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
     if args.impl == "reference":
         return bench_reference(args, rank, world)
     if args.solve_only:
@@ -855,7 +958,8 @@ def solve_once(args):
     prec = {"fp32": l1.A_FP32, "bf16": l1.A_BF16, "fp8": l1.A_FP8E4M3}[args.precision]
     A_d = torch.from_numpy(np.ascontiguousarray(A.T, dtype=np.float32)).cuda().t()
     B_d = torch.from_numpy(np.ascontiguousarray(B.T, dtype=np.float32)).cuda().t()
-    s = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec)
+    s = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec,
+                  tune=not args.no_tune)
     max_iter = args.max_iter or cfg["max_iter"]
     t0 = time.perf_counter()
     _, _, res = s.solve(B_d, cfg["tol"], max_iter)

@@ -127,10 +127,21 @@ typedef struct {
                           * the tensor-core sweeps (fused or deferred epilogue,
                           * split-K slices) at batch widths up to 4096 for each sweep
                           * shape and keeps the fastest (l1_tuning); -1 -> a fixed
-                          * rule from the tile and multiprocessor counts.  The slice
+                          * rule from the tile and multiprocessor counts (deferred
+                          * epilogue; split-K when a quarter of the SMs would hold
+                          * every tile), e.g. under a profiler, whose per-launch
+                          * overhead distorts the tuner's timings.  The slice
                           * count sets the order in which K slices are added, so two
                           * handles whose timings chose differently can differ in the
                           * last bits. */
+    int32_t cg_steps;    /* DALM: 0 -> the exact y-step of Eq. 39 through the FP64 factor
+                          * of B B^T; 1 -> one conjugate-gradient step on that system
+                          * from the previous y per iteration instead (§V-B, reading
+                          * R15): no m x m factor is formed, so setup needs no O(m^2)
+                          * memory or Cholesky.  §V-B reports that this variant fails
+                          * on face images; on the cross-and-bouquet model it stalls
+                          * far from the constraint.  FP32 dictionary and the
+                          * tensor-core engine only (L1_ERR_UNSUPPORTED otherwise). */
 } l1_options;
 
 /* Per-instance results (host memory). */
@@ -345,6 +356,34 @@ L1_API int l1_solve_plain(l1_handle h, const float* b, double tol, int32_t max_i
  * or L1_ERR_INVALID_ARG for a null handle, or for out == NULL with cap > 0.
  */
 L1_API int l1_tuning(l1_handle h, int32_t* out, int32_t cap);
+
+/*
+ * l1_align_batch -- the convex step of the face-alignment loop (§II-B, the
+ * last problem displayed there): for k < count, min ||e||_1 s.t.
+ * b_k = B_k w + e with B_k tall (m x p, p <= 32, p < m; in the paper the
+ * training images of one subject beside the negated Jacobian of the
+ * transformation) and w not penalised.  Reading R16: Algorithm 1 with its
+ * x-step replaced by the exact least-squares minimiser over w (B_k^T B_k
+ * inverted once per problem in FP64), e-step and multiplier step as in
+ * Algorithm 1, xi = 2m/||b_k||_1 (or xi0 > 0) held fixed, from w = 0,
+ * e = b_k, theta = 0; each problem stops on the relative change of [w; e]
+ * (§VI-C) below tol, or after max_outer iterations.
+ *   B      device, problem k at B + k strideB, column-major with leading
+ *          dimension ldB >= m (strideB >= ldB p)
+ *   b      device, problem k at b + k strideb (strideb >= m)
+ *   w, e   device outputs: w of problem k at w + k p, e at e + k m
+ *   res    host, count results: status (L1_NONFINITE also for a B_k^T B_k
+ *          that is singular to working precision), iters, rel_change,
+ *          primal_obj = ||e||_1, param = xi; dual_obj, gap, resid NaN
+ * One CTA per problem holds B_k and the m-vectors in shared memory, so
+ * 4 (m p + 4 m) bytes + 17 KB must fit 200 KB.  The call allocates a small
+ * result buffer and synchronises the stream.  Needs no handle.
+ * Errors: L1_ERR_INVALID_ARG (sizes, strides, null pointers, a problem too
+ * large), L1_ERR_OOM, L1_ERR_CUDA.
+ */
+L1_API int l1_align_batch(const float* B, int64_t m, int64_t p, int64_t ldB, int64_t strideB, const float* b,
+                          int64_t strideb, int64_t count, double tol, int32_t max_outer, double xi0, void* stream,
+                          float* w, float* e, l1_result* res);
 
 /* Set the stream later calls enqueue on. */
 L1_API int l1_set_stream(l1_handle h, void* stream);

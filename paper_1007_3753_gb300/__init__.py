@@ -30,7 +30,7 @@ CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
 # every symbol include/l1alm.h declares
 EXPORTS = ("l1_options_init", "l1_setup", "l1_setup_group", "l1_group_load", "l1_solve_batch",
            "l1_backward", "l1_set_stream", "l1_get_info", "l1_destroy", "l1_status_string",
-           "l1_last_error", "l1_lipschitz_static", "l1_solve_plain", "l1_tuning")
+           "l1_last_error", "l1_lipschitz_static", "l1_solve_plain", "l1_tuning", "l1_align_batch")
 
 
 class Options(C.Structure):
@@ -42,7 +42,8 @@ class Options(C.Structure):
                 ("class_offsets", C.POINTER(C.c_int32)), ("stream", C.c_void_p),
                 ("unroll_K", C.c_int32), ("unroll_J", C.c_int32), ("ckpt_every", C.c_int32),
                 ("profile", C.c_int32), ("tc_pieces", C.c_int32), ("refine", C.c_int32),
-                ("tc_pieces_y", C.c_int32), ("tc_min_cols", C.c_int32), ("tune", C.c_int32)]
+                ("tc_pieces_y", C.c_int32), ("tc_min_cols", C.c_int32), ("tune", C.c_int32),
+                ("cg_steps", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -114,6 +115,9 @@ def load() -> C.CDLL:
     L.l1_solve_plain.restype = C.c_int
     L.l1_tuning.argtypes = [vp, C.POINTER(i32), i32]
     L.l1_tuning.restype = C.c_int
+    L.l1_align_batch.argtypes = [vp, i64, i64, i64, i64, vp, i64, i64, dbl, i32, dbl, vp, vp, vp,
+                                 C.POINTER(Result)]
+    L.l1_align_batch.restype = C.c_int
     _lib = L
     return L
 
@@ -166,7 +170,7 @@ class Solver:
                  class_offsets=None, precision: int = A_FP32, engine: int = ENGINE_AUTO,
                  profile: bool = False, tc_pieces: int = 0, tc_pieces_y: int = 0, tc_min_cols: int = 0,
                  unroll_K: int = 0, unroll_J: int = 0, ckpt_every: int = 0, refine: bool = True,
-                 tune: bool = True, stream=None):
+                 tune: bool = True, cg_steps: int = 0, stream=None):
         L = load()
         o = Options()
         L.l1_options_init(C.byref(o))
@@ -184,6 +188,7 @@ class Solver:
         o.unroll_K = unroll_K
         o.refine = 0 if refine else -1
         o.tune = 0 if tune else -1
+        o.cg_steps = cg_steps
         if unroll_J:
             o.unroll_J = unroll_J
         if ckpt_every:
@@ -432,6 +437,31 @@ def lipschitz_static(A, max_iter: int = 1000, rtol: float = 1e-6, stream=None,
     if return_status:
         return rho.value, status.value == CONVERGED, iters.value
     return rho.value
+
+
+def align_batch(B, b, tol: float = 1e-6, max_outer: int = 10000, xi0: float = 0.0, stream=None):
+    """l1_align_batch: the alignment step of §II-B for count problems,
+    min ||e||_1 s.t. b_k = B_k w + e, w unpenalised (reading R16).
+
+    ``B`` is a CUDA float32 tensor of shape (count, p, m) (problem k's
+    column j is B[k, j]), ``b`` of shape (count, m).  Returns (w, e, results)
+    with w of shape (count, p) and e of shape (count, m)."""
+    import torch
+    for name, t in (("B", B), ("b", b)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
+            raise TypeError(f"align_batch: {name} must be a float32 CUDA tensor")
+    if B.dim() != 3 or b.dim() != 2 or b.shape[0] != B.shape[0] or b.shape[1] != B.shape[2]:
+        raise ValueError("align_batch: B must be (count, p, m) and b (count, m)")
+    B = B.contiguous()
+    b = b.contiguous()
+    count, p, m = B.shape
+    w = torch.empty((count, p), dtype=torch.float32, device=B.device)
+    e = torch.empty((count, m), dtype=torch.float32, device=B.device)
+    res = (Result * count)()
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    _check(load().l1_align_batch(_ptr(B), m, p, m, m * p, _ptr(b), m, count, float(tol), int(max_outer),
+                                 float(xi0), st, _ptr(w), _ptr(e), res), "l1_align_batch")
+    return w, e, results_to_dict(res)
 
 
 def _colmajor(t):

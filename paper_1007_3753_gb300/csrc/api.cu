@@ -135,6 +135,11 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
         return L1_ERR_INVALID_ARG;
     if (o.tc_pieces == 1 || o.tc_pieces_y == 1) return L1_ERR_UNSUPPORTED;  // a one-piece panel cannot converge
     if (o.engine == L1_ENGINE_TC && (o.solver != L1_DALM || mode == L1_QP_LAMBDA)) return L1_ERR_UNSUPPORTED;
+    if (o.cg_steps < 0) return L1_ERR_INVALID_ARG;
+    // DALM with a CG y-step (R15): one step, FP32 dictionary, tensor-core sweeps
+    if (o.cg_steps > 0 && (o.cg_steps != 1 || o.solver != L1_DALM || mode == L1_QP_LAMBDA ||
+                           o.precision != L1_A_FP32 || o.engine == L1_ENGINE_SIMT || o.unroll_K > 0))
+        return L1_ERR_UNSUPPORTED;
     if (o.unroll_K < 0 || o.unroll_J < 0 || o.ckpt_every < 0) return L1_ERR_INVALID_ARG;
     if (o.unroll_K > 0) {
         // R11: unrolled PALM in P1 mode on the CUDA cores
@@ -202,7 +207,13 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
             h->lipschitz = 1.01 * rho;
             if (!(h->lipschitz > 0.0)) { rc = L1_ERR_INVALID_ARG; break; }  // A == 0
         }
-        if (o.solver == L1_DALM && mode != L1_QP_LAMBDA) {
+        if (o.solver == L1_DALM && mode != L1_QP_LAMBDA && o.cg_steps > 0) {
+            // the CG y-step needs no factor of B B^T
+            if (h->use_tc && o.tune >= 0) {
+                rc = tc16::tune_splits(h);
+                if (rc) break;
+            }
+        } else if (o.solver == L1_DALM && mode != L1_QP_LAMBDA) {
             rc = dev_alloc_t(h, &h->F, (size_t)h->ldm * m);
             if (rc) break;
             rc = dev_alloc_t(h, &h->F_lo, (size_t)h->ldm * m);

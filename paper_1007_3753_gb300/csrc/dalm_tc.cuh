@@ -129,8 +129,67 @@ struct EpiTcS {
     }
 };
 
+// ---------------------------------------- DALM with a conjugate-gradient y-step
+// One CG step on (B B^T) y = B z_{k+1} - (B w_k - b)/beta from y_k (§V-B's
+// inexact alternative to the factor; reading R15): its residual is
+// r_0 = B V + b/beta = d (the same d as above), p = d, and
+// y_{k+1} = y_k + alpha d with alpha = ||d||^2 / (d^T B B^T d)
+//                                    = ||d||^2 / ||B^T d||^2.
+
+// T1' (rows of A, acc = A V_x): d as in EpiTcD, also stored in FP32 (the
+// y-step adds alpha d); red: ||d||^2.
+struct EpiCgD {
+    static constexpr int NRED = 1;
+    struct State {
+        float b, ve;
+        int act;
+    };
+    float* D;
+    const float* Ve;
+    const float* B;
+    const float* binv;
+    const int32_t* active;
+    int64_t ldm;
+    int cab;
+    __device__ State load(int i, int j) const {
+        const int64_t o = (int64_t)j * ldm + i;
+        return State{B[o], cab ? Ve[o] : 0.0f, active[j]};
+    }
+    __device__ float apply(int i, int j, float acc, const State& st, float* red) const {
+        if (!st.act) return 0.0f;
+        const float d = fmaf(st.b, binv[j], acc) + st.ve;
+        D[(int64_t)j * ldm + i] = d;
+        red[0] += d * d;
+        return d;
+    }
+};
+
+// T2' (rows of A^T, acc = A^T d): red: ||A^T d||^2 (the identity block of
+// B^T d is d itself, whose square is T1's term).  Nothing is stored.
+struct EpiCgQ {
+    static constexpr int NRED = 1;
+    struct State {
+        int act;
+    };
+    const int32_t* active;
+    __device__ State load(int, int j) const { return State{active[j]}; }
+    __device__ float apply(int, int, float acc, const State& st, float* red) const {
+        if (st.act) red[0] += acc * acc;
+        return 0.0f;
+    }
+};
+
 int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcD& epi,
              const tc16::PieceOut& po, double* part, const int32_t* active);
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiCgD& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active);
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiCgQ& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active);
+// The y-epilogue (EpiTcY) applied to acc = alpha_j S(i, j) (S: m x N, leading
+// dimension lds) instead of a sweep's sums: the CG y-step.  Returns the
+// number of row blocks.
+int tc_scaled_y(Handle* h, int M, int N, const float* S, int64_t lds, const float* alpha, const EpiTcY& epi,
+                const tc16::PieceOut& po, double* part, const int32_t* active);
 int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcY& epi,
              const tc16::PieceOut& po, double* part, const int32_t* active);
 int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcS& epi,

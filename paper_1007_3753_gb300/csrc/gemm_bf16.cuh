@@ -57,7 +57,14 @@ using tc::tma_load_2d;
 using tc::tmem_ld32;
 
 constexpr int kBM = 128;       // output rows per tile = TMEM lanes
-constexpr int kKB = 64;        // BF16 elements per K block (one 128-byte swizzle row)
+#ifndef L1_TC_KB
+#define L1_TC_KB 64
+#endif
+// BF16 elements per K block = one swizzle row (64: 128-byte rows, two
+// 96 KB ring stages for three-piece operands; 32: 64-byte rows, four 48 KB
+// stages)
+constexpr int kKB = L1_TC_KB;
+static_assert(kKB == 64 || kKB == 32, "K block");
 constexpr int kMmaK = 16;      // K of one kind::f16 MMA
 constexpr int kMaxPieces = 3;
 constexpr int kMaxTerms = 9;
@@ -141,7 +148,7 @@ __device__ __forceinline__ void split_aligned(float v, float bmax, float& p0, fl
 
 template <int BN, int NPA, int NPX>
 struct Cfg {
-    static constexpr int kATile = kBM * kKB * 2;  // 16 KB
+    static constexpr int kATile = kBM * kKB * 2;  // 16 or 8 KB
     static constexpr int kXTile = BN * kKB * 2;
     static constexpr int kStage = NPA * kATile + NPX * kXTile;
     static constexpr int kStages = (200 * 1024 / kStage) > 6 ? 6 : (200 * 1024 / kStage);
@@ -258,7 +265,7 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
              int defer, float* __restrict__ wk) {
     constexpr int BN = 128;
     constexpr int NR = E::NRED > 0 ? E::NRED : 1;
-    constexpr int kMmaPerBlock = kKB / kMmaK;  // 4
+    constexpr int kMmaPerBlock = kKB / kMmaK;  // 4 or 2
     constexpr uint32_t kIdesc = instr_desc_bf16(kBM, BN);
     constexpr uint32_t kTmemCols = 512;        // hi[0], hi[1], lo[0], lo[1]
     constexpr int CPT = BN / 2;                // columns per epilogue thread
@@ -423,8 +430,8 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
                         bool& first = hi ? first_hi : first_lo;
 #pragma unroll
                         for (int k = 0; k < kMmaPerBlock; ++k) {
-                            const uint64_t ad = smem_desc(a_addr + k * kMmaK * 2);
-                            const uint64_t bd = smem_desc(x_addr + k * kMmaK * 2);
+                            const uint64_t ad = smem_desc<kKB * 2>(a_addr + k * kMmaK * 2);
+                            const uint64_t bd = smem_desc<kKB * 2>(x_addr + k * kMmaK * 2);
                             mma_bf16(d, ad, bd, kIdesc, first ? 0u : 1u);
                             first = false;
                         }
@@ -522,10 +529,12 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
 // 128-column tile.
 constexpr int kFinCols = 8;
 
+// The sums are wk[(z * N + j) * ldw + i] over the slices z < ksplit; with
+// colscale they are multiplied by colscale[j] before the epilogue.
 template <class E>
 __global__ void __launch_bounds__(kBM)
-finish_kernel(int M, int N, int ksplit, const float* __restrict__ wk, E epi, PieceOut po,
-              double* __restrict__ part, const int32_t* __restrict__ active) {
+finish_kernel(int M, int N, int ksplit, const float* __restrict__ wk, int64_t ldw, const float* __restrict__ colscale,
+              E epi, PieceOut po, double* __restrict__ part, const int32_t* __restrict__ active) {
     constexpr int NR = E::NRED > 0 ? E::NRED : 1;
     __shared__ double red_s[4][kFinCols][NR];
     __shared__ float max_s[4][kFinCols];
@@ -547,16 +556,16 @@ finish_kernel(int M, int N, int ksplit, const float* __restrict__ wk, E epi, Pie
         }
         return;
     }
-    const int64_t Mp = (int64_t)tiles_m * kBM;
     float v[kFinCols];
     typename E::State st[kFinCols];
 #pragma unroll
     for (int u = 0; u < kFinCols; ++u) {
         const int j = j0 + u;
         v[u] = 0.0f;
-        if (j < N) {
-            for (int z = 0; z < ksplit; ++z) v[u] += wk[((int64_t)z * N + j) * Mp + i];
-            if (i < M) st[u] = epi.load(i, j);
+        if (j < N && i < M) {
+            for (int z = 0; z < ksplit; ++z) v[u] += wk[((int64_t)z * N + j) * ldw + i];
+            if (colscale) v[u] *= colscale[j];
+            st[u] = epi.load(i, j);
         }
     }
 #pragma unroll

@@ -42,7 +42,7 @@ constexpr int kGThreads = 512;
 constexpr int kGWarps = kGThreads / 32;
 constexpr int kGMaxM = 8192;               // rows of an instance
 constexpr int kGShared = 2048;             // rows of an instance whose rows several threads own (acc_s)
-constexpr int kGBufs = 3;                  // tile buffers (units in flight)
+constexpr int kGBufs = 2;                  // tile buffers (units in flight; three measured slower)
 constexpr int kGTileBytes = 64 * 1024;     // A tile in shared memory
 constexpr int kGPartials = 4096;           // dot partials of one unit (part_s)
 constexpr uint32_t kGBarrierSpin = 1u << 26;
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(kGThreads, 1) group_kernel(GArgs g) {
     const int nwarps_grid = gridDim.x * kGWarps;
     const int gwarp = blockIdx.x * kGWarps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    uint32_t phase[kGBufs] = {0u, 0u, 0u};
+    uint32_t phase[kGBufs] = {};
     // this thread's rows of the current instance: residual, accumulator
     float r[16], acc[16];
     uint4 a[kGSlots];
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(kGThreads, 1) group_kernel(GArgs g) {
             // in buffer k lives in geo_s[k]; the copy of unit u + kGBufs is
             // issued as soon as every thread has taken unit u's words into
             // registers
-            bool pending[kGBufs] = {false, false, false};
+            bool pending[kGBufs] = {};
             if (threadIdx.x == 0 && u0 < u1) {
                 geo_s[0] = geom_first(g, u0, nact);
                 issue_tile(g, geo_s[0], tiles[0], &bars[0]);
@@ -608,10 +608,15 @@ __global__ void __launch_bounds__(kGThreads, 1) group_kernel(GArgs g) {
             im.i = -1;
             double d2 = 0.0, w2 = 0.0;
             bool failed = false;
+            // the column state of a unit is loaded one unit ahead (two
+            // dependent loads: the instance's offset, then x and z)
+            ColState cst_next{0.0f, 0.0f};
+            if (u0 < u1) cst_next = load_cols(g, geo_s[0]);
             for (int64_t u = u0; u < u1; ++u) {
                 const int b = (int)((u - u0) % kGBufs);
                 const UnitGeom q = geo_s[b];
-                const ColState cst = load_cols(g, q);  // in flight while the tile lands
+                const ColState cst = cst_next;
+                if (u + 1 < u1) cst_next = load_cols(g, geo_s[(b + 1) % kGBufs]);
                 if (q.i != im.i) {
                     if (im.i >= 0) {
                         GROUP_DISPATCH(flush_regs, im, acc, racc_next, acc_s);
@@ -634,7 +639,11 @@ __global__ void __launch_bounds__(kGThreads, 1) group_kernel(GArgs g) {
                 phase[b] ^= 1u;
                 pending[b] = false;
                 if (u + kGBufs < u1) {
-                    if (threadIdx.x == 0) {
+                    // issued from the last warp, which has a column of the
+                    // unit to finish only when the unit has more than
+                    // kGWarps - 1 columns (the geometry of a new instance
+                    // costs global loads)
+                    if (threadIdx.x == kGThreads - 32) {
                         // unit u + kGBufs follows unit u + kGBufs - 1, which
                         // sits in the buffer before this one
                         const UnitGeom q2 = geom_next(g, geo_s[(b + kGBufs - 1) % kGBufs]);

@@ -545,7 +545,9 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     int phase = 1;
     int32_t* iters1 = w.hcoli + 5 * w.cap_N;
     // tensor-core engine (batched DALM): BF16 pieces of A and the panels
-    const int tc_min = o.tc_min_cols > 0 ? o.tc_min_cols : 1;
+    // DALM with a CG y-step: tensor cores only, to the last column
+    const bool cg = o.cg_steps > 0;
+    const int tc_min = cg ? 1 : (o.tc_min_cols > 0 ? o.tc_min_cols : 1);
     const int tcp = o.tc_pieces > 0 ? std::min(o.tc_pieces, 3) : 3;      // A sweeps
     const int tcy = o.tc_pieces_y > 0 ? std::min(o.tc_pieces_y, 3) : 3;  // y-step
     bool tc_mode = h->use_tc && solver == L1_DALM && N_cur >= tc_min;
@@ -562,7 +564,51 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
         const double na = N_cur;
         auto run_chunk = [&](cudaStream_t s) -> int {
         for (int r = 0; r < check_every; ++r) {
-            if (solver == L1_DALM && tc_mode) {
+            if (solver == L1_DALM && tc_mode && cg) {
+                // Algorithm 2 with one conjugate-gradient y-step (§V-B,
+                // reading R15) on the tensor cores: d = B V + b/beta and
+                // ||d||^2; ||A^T d||^2; alpha = ||d||^2 / ||B^T d||^2;
+                // y += alpha d with the CAB e-part (EpiTcY on alpha d); A^T y
+                // with the x-part (EpiTcS)
+                const tc16::Terms ta = terms_square(tcp);
+                tc16::Operands o1{{h->A_rm_h[0], h->A_rm_h[1], h->A_rm_h[2]}, tcp,
+                                  {w.Vh[0], w.Vh[1], w.Vh[2]}, tcp, ldn, ldn};
+                tc16::PieceOut po1{{w.Dh[0], w.Dh[1], w.Dh[2]}, tcp, ldm};
+                prof.start(0, 2.0 * m * n * na);
+                const int np_d = tc_sweep(h, m, N_cur, n, o1, ta,
+                                          EpiCgD{w.R, P->Ue, P->B, c.binv, c.active, ldm, cab ? 1 : 0}, po1, part_m,
+                                          c.active);
+                prof.stop();
+                if (np_d < 0) return np_d;
+                tc16::Operands o2{{h->A_cm_h[0], h->A_cm_h[1], h->A_cm_h[2]}, tcp,
+                                  {w.Dh[0], w.Dh[1], w.Dh[2]}, tcp, ldm, ldm};
+                tc16::PieceOut po0{{nullptr, nullptr, nullptr}, 0, ldn};
+                prof.start(1, 2.0 * m * n * na);
+                const int np_q = tc_sweep(h, n, N_cur, m, o2, ta, EpiCgQ{c.active}, po0, part_n, c.active);
+                prof.stop();
+                if (np_q < 0) return np_q;
+                float* alpha = P->colf + 5 * w.cap_N;
+                cg_alpha_kernel<<<N_cur, 128, 0, s>>>(c, part_m, np_d, part_n, np_q, cab ? 1 : 0, alpha);
+                L1_LAUNCH_CHECK(h);
+                tc16::PieceOut po2{{w.Yh[0], w.Yh[1], w.Yh[2]}, tcp, ldm};
+                const int np_e = tc_scaled_y(
+                    h, m, N_cur, w.R, ldm, alpha,
+                    EpiTcY{P->Y, P->We, P->Cc, P->Ue, c.beta, c.binv, c.active, ldm, cab ? 1 : 0}, po2, part_m,
+                    c.active);
+                if (np_e < 0) return np_e;
+                tc16::Operands o3{{h->A_cm_h[0], h->A_cm_h[1], h->A_cm_h[2]}, tcp,
+                                  {w.Yh[0], w.Yh[1], w.Yh[2]}, tcp, ldm, ldm};
+                tc16::PieceOut po3{{w.Vh[0], w.Vh[1], w.Vh[2]}, tcp, ldn};
+                prof.start(2, 2.0 * m * n * na);
+                const int np_x = tc_sweep(h, n, N_cur, m, o3, ta,
+                                          EpiTcS{P->Wx, P->X, P->Ux, c.beta, c.binv, c.active, ldn}, po3, part_n,
+                                          c.active);
+                prof.stop();
+                if (np_x < 0) return np_x;
+                ctrl_dalm_kernel<<<(N_cur + kCtrlCols - 1) / kCtrlCols, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e,
+                                                                                     part_n, np_x, tol, max_iter);
+                L1_LAUNCH_CHECK(h);
+            } else if (solver == L1_DALM && tc_mode) {
                 // Algorithm 2 on the BF16 tensor cores, the y-step as a
                 // correction (EpiTcD / EpiTcY / EpiTcS): pa pieces of A (one,
                 // the BF16 A itself, in the first phase of a BF16 solve), tcp
@@ -595,7 +641,8 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                                               c.active);
                 prof.stop();
                 if (np_x < 0) return np_x;
-                ctrl_dalm_kernel<<<N_cur, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e, part_n, np_x, tol, max_iter);
+                ctrl_dalm_kernel<<<(N_cur + kCtrlCols - 1) / kCtrlCols, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e,
+                                                                                     part_n, np_x, tol, max_iter);
                 L1_LAUNCH_CHECK(h);
             } else if (solver == L1_DALM) {
                 // Algorithm 2: three sweeps per iteration on the CUDA cores
@@ -618,7 +665,8 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                 else np_x = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, P->Y, ldm, e3, part_n, c.active);
                 prof.stop();
                 if (np_x < 0) return np_x;
-                ctrl_dalm_kernel<<<N_cur, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e, part_n, np_x, tol, max_iter);
+                ctrl_dalm_kernel<<<(N_cur + kCtrlCols - 1) / kCtrlCols, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e,
+                                                                                     part_n, np_x, tol, max_iter);
                 L1_LAUNCH_CHECK(h);
             } else {
                 // Algorithm 1 / Eq. 18: two sweeps per inner FISTA step

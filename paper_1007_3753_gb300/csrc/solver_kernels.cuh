@@ -322,18 +322,32 @@ __device__ __forceinline__ double sum_parts(const double* part, int np, int N, i
     return block_sum_128(v, sh);
 }
 
+// DALM controller: one warp per column (kCtrlCols columns per 128-thread
+// block) adds the row-block partials of ||dw||^2 and ||w||^2 (lane p takes
+// row blocks p, p + 32, ...; then a fixed warp tree) and applies the
+// relative-change rule of §VI-C.
+constexpr int kCtrlCols = 4;
+
 __global__ void ctrl_dalm_kernel(Cols c, const double* part_e, int np_e, const double* part_x,
                                  int np_x, double tol, int max_iter) {
-    __shared__ double sh[4];
-    const int j = blockIdx.x;
-    if (!c.active[j]) return;
-    double d2 = sum_parts(part_x, np_x, c.N, j, 0, sh);
-    double w2 = sum_parts(part_x, np_x, c.N, j, 1, sh);
-    if (part_e) {
-        d2 += sum_parts(part_e, np_e, c.N, j, 0, sh);
-        w2 += sum_parts(part_e, np_e, c.N, j, 1, sh);
+    const int j = blockIdx.x * kCtrlCols + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= c.N || !c.active[j]) return;
+    double d2 = 0.0, w2 = 0.0;
+    for (int p = lane; p < np_x; p += 32) {
+        const double* q = part_x + ((int64_t)p * c.N + j) * kPartStride;
+        d2 += q[0];
+        w2 += q[1];
     }
-    if (threadIdx.x != 0) return;
+    if (part_e) {
+        for (int p = lane; p < np_e; p += 32) {
+            const double* q = part_e + ((int64_t)p * c.N + j) * kPartStride;
+            d2 += q[0];
+            w2 += q[1];
+        }
+    }
+    d2 = warp_sum(d2);
+    w2 = warp_sum(w2);
+    if (lane != 0) return;
     const int it = c.iters[j] + 1;
     c.iters[j] = it;
     c.inner[j] = it;
@@ -348,6 +362,25 @@ __global__ void ctrl_dalm_kernel(Cols c, const double* part_e, int np_e, const d
     } else if (it >= max_iter) {
         c.status[j] = L1_MAX_ITER;
         c.active[j] = 0;
+    }
+}
+
+// DALM with a CG y-step (reading R15): alpha_j = ||d||^2 / ||B^T d||^2 from
+// the row-block partials of ||d||^2 (part_d) and ||A^T d||^2 (part_q); for
+// CAB B^T d = [A^T d; d].  Inactive columns get 0.
+__global__ void cg_alpha_kernel(Cols c, const double* part_d, int np_d, const double* part_q, int np_q, int cab,
+                                float* alpha) {
+    __shared__ double sh[4];
+    const int j = blockIdx.x;
+    if (!c.active[j]) {
+        if (threadIdx.x == 0) alpha[j] = 0.0f;
+        return;
+    }
+    const double dd = sum_parts(part_d, np_d, c.N, j, 0, sh);
+    const double qq = sum_parts(part_q, np_q, c.N, j, 0, sh);
+    if (threadIdx.x == 0) {
+        const double den = qq + (cab ? dd : 0.0);
+        alpha[j] = den > 0.0 ? (float)(dd / den) : 0.0f;
     }
 }
 

@@ -24,22 +24,26 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 int make_map_bf16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch_bytes,
-                  uint32_t box_rows) {
+                  uint32_t box_inner, uint32_t box_rows) {
     auto fn = encode_fn();
     if (!fn) {
         set_last_error("cuTensorMapEncodeTiled unavailable");
         return L1_ERR_CUDA;
     }
     // TMA rules: 16-byte aligned base and pitch; the box's inner extent is
-    // 128 bytes (64 BF16) and every x coordinate used is a multiple of 64
-    if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch_bytes & 15) || box_rows == 0 || box_rows > 256)
+    // the swizzle width (128 or 64 bytes) and every x coordinate used is a
+    // multiple of box_inner (a multiple of 16 bytes)
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch_bytes & 15) || box_rows == 0 || box_rows > 256 ||
+        (box_inner != 64 && box_inner != 32))
         return L1_ERR_INVALID_ARG;
     const cuuint64_t dims[2] = {inner, rows};
     const cuuint64_t strides[1] = {pitch_bytes};
-    const cuuint32_t box[2] = {64, box_rows};
+    const cuuint32_t box[2] = {box_inner, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    box_inner == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_last_error("cuTensorMapEncodeTiled (bf16) failed: " + std::to_string((int)r));

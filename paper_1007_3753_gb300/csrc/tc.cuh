@@ -9,10 +9,12 @@ namespace l1 {
 namespace tc {
 
 // Tiled 2-D tensor map over `rows` rows of `inner` BF16 elements, row pitch
-// pitch_bytes; box = 64 elements (128 bytes) x box_rows, 128-byte swizzle.
-// Returns L1_OK, L1_ERR_INVALID_ARG (misaligned base or pitch) or L1_ERR_CUDA.
+// pitch_bytes; box = box_inner elements (64: 128 bytes, 128-byte swizzle; 32:
+// 64 bytes, 64-byte swizzle) x box_rows.
+// Returns L1_OK, L1_ERR_INVALID_ARG (misaligned base or pitch, another box
+// width) or L1_ERR_CUDA.
 int make_map_bf16(CUtensorMap* map, const void* base, uint64_t inner, uint64_t rows, uint64_t pitch_bytes,
-                  uint32_t box_rows);
+                  uint32_t box_inner, uint32_t box_rows);
 
 }  // namespace tc
 }  // namespace l1

@@ -135,6 +135,7 @@ int tune_splits(Handle* h) {
         int64_t lda;
     };
     const Shape shapes[3] = {{m, n, h->A_rm_h, h->ldn}, {m, m, h->F_h, h->ldm}, {n, m, h->A_cm_h, h->ldm}};
+    const int nshapes = h->F_h[0] ? 3 : 2;  // no factor pieces: A u and A^T y only
     // column-tile counts timed (batch widths up to 4096); a width between two
     // of them takes the smaller one's choice
     static const int kTileCols[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
@@ -178,7 +179,9 @@ int tune_splits(Handle* h) {
             ++h->launches;
         }
         const Terms tl = terms_3x3();
-        for (const Shape& sh : shapes) {
+        for (int si = 0; si < 3; ++si) {
+            if (nshapes == 2 && si == 1) continue;
+            const Shape& sh = shapes[si];
             const int tm = (sh.M + kBM - 1) / kBM;
             const int chunks = (sh.K + kChunk - 1) / kChunk;
             for (int tn : kTileCols) {

@@ -52,9 +52,9 @@ inline int get_maps(Handle* h, int M, int N, int K, const Operands& op, int bn, 
     }
     std::memset(out, 0, sizeof(*out));
     for (int p = 0; p < op.npa; ++p)
-        L1_TRY(tc::make_map_bf16(&out->a[p], op.a[p], (uint64_t)K, (uint64_t)M, (uint64_t)op.lda * 2, kBM));
+        L1_TRY(tc::make_map_bf16(&out->a[p], op.a[p], (uint64_t)K, (uint64_t)M, (uint64_t)op.lda * 2, kKB, kBM));
     for (int p = 0; p < op.npx; ++p)
-        L1_TRY(tc::make_map_bf16(&out->x[p], op.x[p], (uint64_t)K, (uint64_t)N, (uint64_t)op.ldx * 2, bn));
+        L1_TRY(tc::make_map_bf16(&out->x[p], op.x[p], (uint64_t)K, (uint64_t)N, (uint64_t)op.ldx * 2, kKB, bn));
     Handle::MapCacheEntry e;
     e.key = key;
     for (int p = 0; p < op.npa; ++p) e.maps.push_back(out->a[p]);
@@ -85,8 +85,10 @@ inline Split normalise(const Handle* h, int ks, int defer, int K, int tiles) {
 
 // The autotuner's choice for (M, K, tiles) (tune_splits): the entry of that
 // tile count, else of the nearest smaller one (its slice count capped at one
-// CTA per SM); without one, enough slices to give every SM a CTA when a
-// quarter of them has a tile, else fused.
+// CTA per SM).  Without one (tuning off, or a shape it did not time): the
+// epilogue deferred, and enough K slices to give every SM a CTA when a
+// quarter of them has a tile -- what the tuner chose for the 4096 x 4000 and
+// 1024 x 1200 cross-and-bouquet shapes at every width it timed.
 inline Split split_choice(const Handle* h, int M, int K, int tiles) {
     const int sms = h->sms > 0 ? h->sms : 152;
     if (!h->tc_wk) return Split{1, 0};
@@ -95,7 +97,7 @@ inline Split split_choice(const Handle* h, int M, int K, int tiles) {
         if (e[0] == M && e[1] == K && e[2] <= tiles && (!near || e[2] > (*near)[2])) near = &e;
     if (near) return normalise(h, std::min((*near)[3], std::max(1, sms / tiles)), (*near)[4], K, tiles);
     const int chunks = (K + kChunk - 1) / kChunk;
-    if (4 * tiles > sms || chunks < 4) return Split{1, 0};
+    if (4 * tiles > sms || chunks < 4) return normalise(h, 1, 1, K, tiles);
     return normalise(h, std::min(sms / tiles, 16), 1, K, tiles);
 }
 
@@ -129,9 +131,23 @@ int launch_inst(Handle* h, const Maps& maps, const Terms& tl, int M, int N, int 
     L1_LAUNCH_CHECK(h);
     if (sp.defer) {
         const int fin = tiles_m * ((N + kFinCols - 1) / kFinCols);
-        finish_kernel<E><<<fin, kBM, 0, h->stream>>>(M, N, ks, h->tc_wk, epi, po, part, active);
+        finish_kernel<E><<<fin, kBM, 0, h->stream>>>(M, N, ks, h->tc_wk, (int64_t)tiles_m * kBM, nullptr, epi, po,
+                                                     part, active);
         L1_LAUNCH_CHECK(h);
     }
+    return tiles_m;
+}
+
+// finish_kernel on sums that are not a sweep's: S(i, j) = sum over z <
+// ksplit of src[(z * N + j) * lds + i], times colscale[j] when given.
+// Returns the number of row blocks.
+template <class E>
+int finish(Handle* h, int M, int N, int ksplit, const float* src, int64_t lds, const float* colscale, const E& epi,
+           const PieceOut& po, double* part, const int32_t* active) {
+    const int tiles_m = (M + kBM - 1) / kBM;
+    const int fin = tiles_m * ((N + kFinCols - 1) / kFinCols);
+    finish_kernel<E><<<fin, kBM, 0, h->stream>>>(M, N, ksplit, src, lds, colscale, epi, po, part, active);
+    L1_LAUNCH_CHECK(h);
     return tiles_m;
 }
 

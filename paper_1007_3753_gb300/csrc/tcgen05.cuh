@@ -66,13 +66,17 @@ __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
 // tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle,
 // 8-row core groups 1024 bytes apart (SBO), start address advanced along K
 // inside the swizzle row for successive MMAs.
+// K-major shared-memory matrix descriptor (tcgen05): rows of swz bytes (128
+// or 64), 8-row core groups swz * 8 bytes apart, the matching swizzle mode.
+template <int swz>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    static_assert(swz == 128 || swz == 64, "swizzle width");
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
     d |= (uint64_t)1 << 16;                         // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+    d |= (uint64_t)((swz * 8) >> 4) << 32;          // stride byte offset
     d |= (uint64_t)1 << 46;                         // descriptor version
-    d |= (uint64_t)2 << 61;                         // SWIZZLE_128B
+    d |= (uint64_t)(swz == 128 ? 2 : 4) << 61;      // SWIZZLE_128B / SWIZZLE_64B
     return d;
 }
 

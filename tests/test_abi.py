@@ -120,6 +120,12 @@ def test_refused_combinations_before_any_cuda_call(lib):
     assert setup(l1.CAB, solver=l1.PALM, unroll_K=5) == U       # unrolled PALM is P1
     assert setup(l1.P1, solver=l1.DALM, unroll_K=5) == U
     assert setup(l1.P1, solver=l1.PALM, unroll_K=-1) == I
+    # DALM with a CG y-step (R15): one step, FP32, tensor cores
+    assert setup(l1.CAB, cg_steps=-1) == I
+    assert setup(l1.CAB, cg_steps=2) == U
+    assert setup(l1.CAB, solver=l1.PALM, cg_steps=1) == U
+    assert setup(l1.CAB, engine=l1.ENGINE_SIMT, cg_steps=1) == U
+    assert setup(l1.CAB, precision=l1.A_BF16, cg_steps=1) == U
     assert setup(l1.P1, solver=7) == I
     assert setup(l1.P1, precision=9) == I
     assert setup(l1.P1, engine=9) == I
