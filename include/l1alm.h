@@ -204,8 +204,10 @@ L1_API int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t m
  * L1_A_BF16 (round to nearest even; FP32 arithmetic).  L = ||A_i||_2^2 of
  * each instance comes from a batched power iteration (x 1.01).  A == NULL
  * allocates the group and leaves the dictionaries to l1_group_load.
+ * Sizes: 1 <= m[i] <= 4096 (an instance's rows stay in the registers of one
+ * CTA), 1 <= n[i] <= 2^24.
  * Errors: L1_ERR_INVALID_ARG (mode other than QP_LAMBDA, lambda <= 0, count
- * or a size <= 0), L1_ERR_OOM, L1_ERR_CUDA, L1_ERR_UNSUPPORTED.
+ * or a size out of range), L1_ERR_OOM, L1_ERR_CUDA, L1_ERR_UNSUPPORTED.
  */
 L1_API int l1_setup_group(const float* const* A, const int64_t* m, const int64_t* n, int64_t count,
                           int32_t mode, const l1_options* opt, l1_handle* out);

@@ -131,9 +131,26 @@ struct PieceOut {
 
 // Aligned split of v on the grid of a block whose largest magnitude is bmax
 // (see above); returns the pieces as floats.
+// 2^e as a float from its IEEE bits (normal range, -126 <= e <= 127)
+__device__ __forceinline__ float pow2_bits(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
 __device__ __forceinline__ void split_aligned(float v, float bmax, float& p0, float& p1, float& p2) {
     if (!(bmax > 0.0f)) {
         p0 = p1 = p2 = 0.0f;
+        return;
+    }
+    const int eb = (int)((__float_as_uint(bmax) >> 23) & 0xffu);
+    if (eb >= 25 && eb <= 254) {
+        // bmax in [2^(eb-127), 2^(eb-126)): bmax < 2^E with E = eb - 126.
+        // Every grid step 2^(E - 8(p+1)) and its reciprocal are normal
+        // floats here, so dividing by the step and multiplying by the
+        // reciprocal give the same (exact) value
+        const int E = eb - 126;
+        p0 = rintf(v * pow2_bits(8 - E)) * pow2_bits(E - 8);
+        const float r1 = v - p0;
+        p1 = rintf(r1 * pow2_bits(16 - E)) * pow2_bits(E - 16);
+        const float r2 = r1 - p1;
+        p2 = rintf(r2 * pow2_bits(24 - E)) * pow2_bits(E - 24);
         return;
     }
     int E;

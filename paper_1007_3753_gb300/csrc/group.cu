@@ -4,7 +4,7 @@
 //
 // Work.  The dictionaries are stored column-major (FP32 or BF16) in one
 // allocation.  A work unit is (instance, tile of consecutive columns) sized so
-// the tile (padding rows included) fits a 64 KB shared-memory buffer; a tile
+// the tile (padding rows included) fits a 32 KB shared-memory buffer; a tile
 // is one contiguous, 16-byte aligned region of the arena.  Each CTA owns a
 // contiguous range of the active units of a step and
 //   1. streams its tiles from HBM into two shared buffers with 1-D TMA bulk
@@ -20,10 +20,12 @@
 //      goes to global memory (one atomic per row) only when the CTA leaves
 //      the instance,
 // so every element of every active dictionary is read from HBM once per step
-// and from shared memory once.  After the pass a bounded grid barrier, a
-// per-instance finalisation (stopping rule of §VI-C, FISTA momentum), another
-// barrier, and a rebuild of the active-instance work list (converged
-// instances drop out: compaction).  The same kernel runs the batched power
+// and from shared memory once.  CTAs are 256 threads with 81 KB of shared
+// memory, two per SM, so that one CTA's barriers overlap the other's work.
+// After the pass a bounded grid barrier, a per-instance finalisation
+// (stopping rule of §VI-C, FISTA momentum), another barrier, and a rebuild
+// of the active-instance work list (converged instances drop out:
+// compaction).  The same kernel runs the batched power
 // iteration for L = ||A_i||_2^2 and the final pass that forms A x for the
 // objective.
 #include <algorithm>
@@ -38,13 +40,13 @@ namespace l1 {
 
 enum GroupMode : int { GM_FISTA = 0, GM_POWER_INIT = 1, GM_POWER = 2, GM_FINAL = 3 };
 
-constexpr int kGThreads = 512;
+constexpr int kGThreads = 256;                // two CTAs per SM
 constexpr int kGWarps = kGThreads / 32;
-constexpr int kGMaxM = 8192;               // rows of an instance
-constexpr int kGShared = 2048;             // rows of an instance whose rows several threads own (acc_s)
+constexpr int kGMaxM = 4096;               // rows of an instance (RP <= 2 for BF16, 4 for FP32)
+constexpr int kGShared = 1024;             // rows of an instance whose rows several threads own (acc_s)
 constexpr int kGBufs = 2;                  // tile buffers (units in flight; three measured slower)
-constexpr int kGTileBytes = 64 * 1024;     // A tile in shared memory
-constexpr int kGPartials = 4096;           // dot partials of one unit (part_s)
+constexpr int kGTileBytes = 32 * 1024;     // A tile in shared memory
+constexpr int kGPartials = 2048;           // dot partials of one unit (part_s)
 constexpr uint32_t kGBarrierSpin = 1u << 26;
 
 struct GroupState {
@@ -214,9 +216,9 @@ __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 
 // ------------------------------------------------------ per-instance thread map
 // A column of a unit is RG = ld / E 16-byte words (E = 8 rows for BF16, 4 for
 // FP32).  A thread holds up to kGSlots words of a unit in registers: with
-// RP = 1 (RG <= 512) the words of row group t % RG in columns
+// RP = 1 (RG <= 256) the words of row group t % RG in columns
 // 8 (t / RG) .. 8 (t / RG) + 7; with RP = 2 or 4 (taller instances, whose
-// units have at most 8 / RP columns) the words of row groups t + 512 k
+// units have at most 8 / RP columns) the words of row groups t + 256 k
 // (k < RP) in every column of the unit.  The thread keeps its rows' residual
 // r and its share of the next accumulator A z in registers for as long as the
 // CTA stays in the instance, so each tile is read from shared memory once.
@@ -394,7 +396,8 @@ __device__ __forceinline__ void flush_regs(const InstMap& im, const float* acc, 
 }
 
 // The register-held parts are instantiated per (element type, RP); an
-// instance's map picks one (BF16 units are at most 8192 rows, so RP <= 2).
+// instance's map picks one (instances are at most 4096 rows: RP <= 2 for BF16,
+// RP <= 4 for FP32).
 #define GROUP_DISPATCH(FN, ...)                                       \
     do {                                                              \
         if (g.bf16) {                                                 \
@@ -549,7 +552,7 @@ __device__ void group_rebuild(const GArgs& g, int64_t* scan_s) {
 
 
 
-__global__ void __launch_bounds__(kGThreads, 1) group_kernel(GArgs g) {
+__global__ void __launch_bounds__(kGThreads, 2) group_kernel(GArgs g) {
     extern __shared__ __align__(128) uint8_t gsm[];
     uint8_t* tiles[kGBufs];                                                   // kGBufs x kGTileBytes
     for (int k = 0; k < kGBufs; ++k) tiles[k] = gsm + k * kGTileBytes;
