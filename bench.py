@@ -536,8 +536,8 @@ def bench_ours(args, rank, world):
             "config": config_dict(cfg, {"parallelism": f"replicas{world}" if world > 1 else "single",
                                         "engine": "tc" if tc else "simt", "precision": args.precision,
                                         "setup_ms": setup_ms, "mean_iters": statistics.mean(iters),
-                                        "tiles_autotuned": [[e["M"], e["K"], e["tiles"], e["ksplit"], e["deferred"]]
-                                                            for e in s.tuning()],
+                                        "tiles_autotuned": [[e["M"], e["K"], e["tiles"], e["ksplit"], e["deferred"],
+                                                             e["bn"]] for e in s.tuning()],
                                         "converged_solves_per_s": conv / (total_ms / 1e3),
                                         "label_accuracy_vs_planted": labels_ok / (args.steps * N)}),
             "e2e": {"value": frac_ok * N * world * args.steps / e2e_s, "unit": "solves/s",

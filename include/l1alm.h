@@ -344,18 +344,20 @@ L1_API int l1_solve_plain(l1_handle h, const float* b, double tol, int32_t max_i
                           l1_result* res);
 
 /*
- * l1_tuning -- the tile strategies l1_setup's autotuner chose for the batched
- * tensor-core sweeps (L1_ENGINE_TC, tune = 0).  No counterpart in the paper:
- * it concerns how the products of Algorithm 2's batched iteration are tiled.
- * For each sweep shape and timed tile count it tried the tile epilogue fused
- * into the sweep, deferred to a second kernel that reads the tile's FP32 sums,
- * and split-K with every slice count that keeps one CTA per multiprocessor,
+ * l1_tuning -- the tile shapes and strategies l1_setup's autotuner chose for
+ * the batched tensor-core sweeps (L1_ENGINE_TC, tune = 0).  No counterpart in
+ * the paper: it concerns how the products of Algorithm 2's batched iteration
+ * are tiled.  For each sweep shape and timed batch width it tried 128-wide
+ * output tiles with the epilogue fused into the sweep or deferred to a second
+ * kernel that reads the tile's FP32 sums, split-K with every slice count that
+ * keeps one CTA per multiprocessor, and 64-wide tiles (deferred, split-K),
  * and kept the fastest (the simplest within 2 %).  Writes up to cap entries
- * of 6 int32 each to out (host): the sweep's output rows M, its depth K, the
- * output tile count (128 x 128 tiles), the number of K slices, 1 if the
- * epilogue is deferred, and the chosen launch's measured time in microseconds
- * (rounded); returns the number of entries written (0: no tuning was done),
- * or L1_ERR_INVALID_ARG for a null handle, or for out == NULL with cap > 0.
+ * of 7 int32 each to out (host): the sweep's output rows M, its depth K, the
+ * batch width as a count of 128 x 128 output tiles, the number of K slices, 1
+ * if the epilogue is deferred, the tile width (128 or 64), and the chosen
+ * launch's measured time in microseconds (rounded); returns the number of
+ * entries written (0: no tuning was done), or L1_ERR_INVALID_ARG for a null
+ * handle, or for out == NULL with cap > 0.
  */
 L1_API int l1_tuning(l1_handle h, int32_t* out, int32_t cap);
 

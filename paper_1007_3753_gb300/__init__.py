@@ -269,10 +269,11 @@ class Solver:
         """l1_tuning: the autotuner's tile strategies, one dict per (sweep
         shape, tile count)."""
         cap = 256
-        buf = (C.c_int32 * (6 * cap))()
+        buf = (C.c_int32 * (7 * cap))()
         k = load().l1_tuning(self._h, buf, cap)
         _check(k if k < 0 else 0, "l1_tuning")
-        return [dict(zip(("M", "K", "tiles", "ksplit", "deferred", "us"), buf[6 * e:6 * e + 6])) for e in range(k)]
+        return [dict(zip(("M", "K", "tiles", "ksplit", "deferred", "bn", "us"), buf[7 * e:7 * e + 7]))
+                for e in range(k)]
 
     def solve_plain(self, b, tol: float, max_iter: int, x=None):
         """l1_solve_plain: DALM for one right-hand side b (m) with plain,

@@ -372,7 +372,7 @@ int l1_tuning(l1_handle hh, int32_t* out, int32_t cap) {
     if (!h || cap < 0 || (cap > 0 && !out)) return L1_ERR_INVALID_ARG;
     const int k = (int)std::min<size_t>(h->tc_splits.size(), (size_t)cap);
     for (int e = 0; e < k; ++e)
-        for (int f = 0; f < 6; ++f) out[6 * e + f] = h->tc_splits[e][f];
+        for (int f = 0; f < 7; ++f) out[7 * e + f] = h->tc_splits[e][f];
     return k;
 }
 

@@ -141,9 +141,9 @@ struct Handle {
     // tensor-core sweeps (slices x tiles x 128 x 128 floats)
     float* tc_wk = nullptr;
     size_t tc_wk_elems = 0;
-    // autotuned choices of the tensor-core sweeps:
-    // (M, K, tiles, K slices, deferred epilogue, microseconds)
-    std::vector<std::array<int32_t, 6>> tc_splits;
+    // autotuned choices of the tensor-core sweeps: (M, K, 128-wide tiles,
+    // K slices, deferred epilogue, tile width, microseconds)
+    std::vector<std::array<int32_t, 7>> tc_splits;
     int* tc_err = nullptr;  // device: first bounded-wait failure of a tcgen05 sweep
     // encoded TMA tensor maps, keyed by the operand pointers and shapes
     struct MapCacheEntry {

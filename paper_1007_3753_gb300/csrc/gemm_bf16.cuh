@@ -168,7 +168,7 @@ struct Cfg {
     static constexpr int kATile = kBM * kKB * 2;  // 16 or 8 KB
     static constexpr int kXTile = BN * kKB * 2;
     static constexpr int kStage = NPA * kATile + NPX * kXTile;
-    static constexpr int kStages = (200 * 1024 / kStage) > 6 ? 6 : (200 * 1024 / kStage);
+    static constexpr int kStages = (216 * 1024 / kStage) > 6 ? 6 : (216 * 1024 / kStage);
     static_assert(kStages >= 2, "two ring stages must fit");
     static constexpr int kBytes = kStages * kStage + 256 + 1024 /* alignment slack */;
 };
@@ -275,16 +275,16 @@ __device__ __forceinline__ void write_partials(const double* red_s, double* part
     }
 }
 
-template <class E, int NPA, int NPX>
+template <class E, int NPA, int NPX, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
 sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, int K, E epi, PieceOut po,
              double* __restrict__ part, const int32_t* __restrict__ active, int* __restrict__ err, int ksplit,
              int defer, float* __restrict__ wk) {
-    constexpr int BN = 128;
+    static_assert(BN == 128 || BN == 64, "tile width");
     constexpr int NR = E::NRED > 0 ? E::NRED : 1;
     constexpr int kMmaPerBlock = kKB / kMmaK;  // 4 or 2
     constexpr uint32_t kIdesc = instr_desc_bf16(kBM, BN);
-    constexpr uint32_t kTmemCols = 512;        // hi[0], hi[1], lo[0], lo[1]
+    constexpr uint32_t kTmemCols = 4 * BN;     // hi[0], hi[1], lo[0], lo[1]
     constexpr int CPT = BN / 2;                // columns per epilogue thread
     using S = Cfg<BN, NPA, NPX>;
     constexpr int kStages = S::kStages;
@@ -513,7 +513,9 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
                     if (j < N) wk[((int64_t)z * N + j) * Mp + i] = sum[c];
                 }
             }
-        } else {
+        } else if constexpr (BN == 128) {
+            // (fused epilogue: 128-wide tiles only; the host defers the
+            // epilogue of 64-wide ones)
             // the tile's values go to shared memory (the ring is idle: every
             // MMA, and so every copy it waited for, has completed)
             float* my = tile_s + q * 32 + lane;
@@ -526,7 +528,7 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if constexpr (E::NRED > 0) {
+    if constexpr (E::NRED > 0 && BN == 128) {
         if (!flags[1] && !split) write_partials<BN, NR>(red_s, part, tile_m, n0, N);
     }
     if (warp == 1) {
@@ -536,63 +538,58 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
 }
 
 
-// The second half of a split-K or deferred sweep: one CTA of kBM threads (one per row)
-// per (row block, kFinCols columns) adds the ksplit slices of wk in slice
-// order (FP32) and runs the tile epilogue on its columns: the functor, the
-// per-column reduction terms (FP32 warp sums over 32 rows, the four row
-// quarters added in order in FP64, as in the sweep's own epilogue) and the
-// aligned BF16 pieces on the grid of the column's largest magnitude over the
-// row block.  Narrow batches get one CTA per few columns instead of one per
-// 128-column tile.
-constexpr int kFinCols = 8;
+// The second half of a split-K or deferred sweep: one CTA of kBM threads
+// per (column, kFinRB consecutive 128-row blocks) adds the ksplit slices of
+// wk in slice order (FP32) and runs the tile epilogue there: the functor, the
+// per-column reduction terms of each row block (FP32 warp sums over 32 rows,
+// the four row quarters added in order in FP64, as in the sweep's own
+// epilogue) and the aligned BF16 pieces on the grid of the largest magnitude
+// of each 128-row block.  A CTA reads each array of its column in runs of up
+// to kFinRB x 512 contiguous bytes; rbs (1 .. kFinRB) row blocks per CTA.
+constexpr int kFinRB = 8;
 
 // The sums are wk[(z * N + j) * ldw + i] over the slices z < ksplit; with
 // colscale they are multiplied by colscale[j] before the epilogue.
 template <class E>
 __global__ void __launch_bounds__(kBM)
 finish_kernel(int M, int N, int ksplit, const float* __restrict__ wk, int64_t ldw, const float* __restrict__ colscale,
-              E epi, PieceOut po, double* __restrict__ part, const int32_t* __restrict__ active) {
+              E epi, PieceOut po, double* __restrict__ part, const int32_t* __restrict__ active, int rbs) {
     constexpr int NR = E::NRED > 0 ? E::NRED : 1;
-    __shared__ double red_s[4][kFinCols][NR];
-    __shared__ float max_s[4][kFinCols];
-    __shared__ int any_active;
+    __shared__ double red_s[4][kFinRB][NR];
+    __shared__ float max_s[4][kFinRB];
     const int tiles_m = (M + kBM - 1) / kBM;
-    const int tile_m = blockIdx.x % tiles_m, j0 = (blockIdx.x / tiles_m) * kFinCols;
+    const int groups = (tiles_m + rbs - 1) / rbs;
+    const int j = blockIdx.x / groups, rb0 = (blockIdx.x % groups) * rbs;
     const int t = threadIdx.x, q = t >> 5, lane = t & 31;
-    const int i = tile_m * kBM + t;
-    if (t == 0) any_active = 0;
-    __syncthreads();
-    if (t < kFinCols && j0 + t < N && (active == nullptr || active[j0 + t])) any_active = 1;
-    __syncthreads();
-    if (!any_active) {
+    const int nrb = min(rbs, tiles_m - rb0);
+    if (active != nullptr && !active[j]) {
         if constexpr (E::NRED > 0) {
-            if (t < kFinCols * NR) {
-                const int c = t / NR, r = t % NR;
-                if (j0 + c < N) part[((int64_t)tile_m * N + j0 + c) * kPartStride + r] = 0.0;
-            }
+            if (t < nrb * NR) part[((int64_t)(rb0 + t / NR) * N + j) * kPartStride + t % NR] = 0.0;
         }
         return;
     }
-    float v[kFinCols];
-    typename E::State st[kFinCols];
+    float v[kFinRB];
+    typename E::State st[kFinRB];
+    const float cs = colscale ? colscale[j] : 1.0f;
 #pragma unroll
-    for (int u = 0; u < kFinCols; ++u) {
-        const int j = j0 + u;
+    for (int u = 0; u < kFinRB; ++u) {
+        const int i = (rb0 + u) * kBM + t;
         v[u] = 0.0f;
-        if (j < N && i < M) {
+        if (u < nrb && i < M) {
             for (int z = 0; z < ksplit; ++z) v[u] += wk[((int64_t)z * N + j) * ldw + i];
-            if (colscale) v[u] *= colscale[j];
+            if (colscale) v[u] *= cs;
             st[u] = epi.load(i, j);
         }
     }
 #pragma unroll
-    for (int u = 0; u < kFinCols; ++u) {
-        const int j = j0 + u;
+    for (int u = 0; u < kFinRB; ++u) {
+        if (u >= nrb) break;
+        const int i = (rb0 + u) * kBM + t;
         float rv[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) rv[r] = 0.0f;
         float ret = 0.0f;
-        if (i < M && j < N) ret = epi.apply(i, j, v[u], st[u], rv);
+        if (i < M) ret = epi.apply(i, j, v[u], st[u], rv);
         v[u] = ret;
         if constexpr (E::NRED > 0) {
 #pragma unroll
@@ -609,11 +606,12 @@ finish_kernel(int M, int N, int ksplit, const float* __restrict__ wk, int64_t ld
         }
     }
     __syncthreads();
-    if (po.np > 0 && i < M) {
+    if (po.np > 0) {
 #pragma unroll
-        for (int u = 0; u < kFinCols; ++u) {
-            const int j = j0 + u;
-            if (j >= N) break;
+        for (int u = 0; u < kFinRB; ++u) {
+            if (u >= nrb) break;
+            const int i = (rb0 + u) * kBM + t;
+            if (i >= M) break;
             const float mx = fmaxf(fmaxf(max_s[0][u], max_s[1][u]), fmaxf(max_s[2][u], max_s[3][u]));
             float p0, p1, p2;
             split_aligned(v[u], mx, p0, p1, p2);
@@ -624,11 +622,10 @@ finish_kernel(int M, int N, int ksplit, const float* __restrict__ wk, int64_t ld
         }
     }
     if constexpr (E::NRED > 0) {
-        if (t < kFinCols * NR) {
-            const int c = t / NR, r = t % NR;
-            if (j0 + c < N)
-                part[((int64_t)tile_m * N + j0 + c) * kPartStride + r] =
-                    red_s[0][c][r] + red_s[1][c][r] + red_s[2][c][r] + red_s[3][c][r];
+        if (t < nrb * NR) {
+            const int u = t / NR, r = t % NR;
+            part[((int64_t)(rb0 + u) * N + j) * kPartStride + r] =
+                red_s[0][u][r] + red_s[1][u][r] + red_s[2][u][r] + red_s[3][u][r];
         }
     }
 }

@@ -44,7 +44,7 @@ constexpr int kGThreads = 256;                // two CTAs per SM
 constexpr int kGWarps = kGThreads / 32;
 constexpr int kGMaxM = 4096;               // rows of an instance (RP <= 2 for BF16, 4 for FP32)
 constexpr int kGShared = 1024;             // rows of an instance whose rows several threads own (acc_s)
-constexpr int kGBufs = 2;                  // tile buffers (units in flight; three measured slower)
+constexpr int kGBufs = 2;                  // tile buffers per CTA (three measured slower, at one and at two CTAs per SM)
 constexpr int kGTileBytes = 32 * 1024;     // A tile in shared memory
 constexpr int kGPartials = 2048;           // dot partials of one unit (part_s)
 constexpr uint32_t kGBarrierSpin = 1u << 26;
@@ -561,8 +561,9 @@ __global__ void __launch_bounds__(kGThreads, 2) group_kernel(GArgs g) {
     float* zj_s = part_s + kGPartials;                                        // 256 floats
     ColState* cst_s = reinterpret_cast<ColState*>(zj_s + 256);                // 256
     double* red_s = reinterpret_cast<double*>(cst_s + 256);                   // 2 * kGWarps
-    int64_t* scan_s = reinterpret_cast<int64_t*>(red_s + 2 * kGWarps);        // kGThreads
-    uint64_t* bars = reinterpret_cast<uint64_t*>(scan_s + kGThreads);         // kGBufs
+    // the rebuild's scan runs between passes, when part_s is idle
+    int64_t* scan_s = reinterpret_cast<int64_t*>(part_s);                     // kGThreads
+    uint64_t* bars = reinterpret_cast<uint64_t*>(red_s + 2 * kGWarps);        // kGBufs
     __shared__ UnitGeom geo_s[kGBufs];
     __shared__ int abort_s;
     if (threadIdx.x == 0) {
@@ -934,8 +935,9 @@ int group_setup(Handle* h, const float* const* A, const int64_t* m, const int64_
     L1_CUDA_TRY(cudaMemcpy(G->xoff, G->hxoff.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice));
     L1_CUDA_TRY(cudaMemcpy(G->nunits, G->hnunits.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice));
     // cooperative grid: every block resident
+    static_assert(kGPartials * sizeof(float) >= kGThreads * sizeof(int64_t), "scan scratch inside part_s");
     G->smem = kGBufs * kGTileBytes + (kGShared + kGPartials + 256) * (int)sizeof(float) +
-              256 * (int)sizeof(ColState) + 2 * kGWarps * 8 + kGThreads * 8 + kGBufs * 8;
+              256 * (int)sizeof(ColState) + 2 * kGWarps * 8 + kGBufs * 8;
     L1_CUDA_TRY(cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G->smem));
     int per_sm = 0, sms = 0;
     L1_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, group_kernel, kGThreads, G->smem));

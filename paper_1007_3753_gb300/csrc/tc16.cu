@@ -188,25 +188,30 @@ int tune_splits(Handle* h) {
                 if (rc != L1_OK) break;
                 const int tiles = tm * tn, N = tn * 128;
                 Operands op{{sh.a[0], sh.a[1], sh.a[2]}, 3, {X[0], X[1], X[2]}, 3, sh.lda, Kp};
-                Maps maps;
-                rc = get_maps(h, sh.M, N, sh.K, op, 128, &maps);
-                if (rc) break;
                 const EpiTune epi{S, Mp};
                 const PieceOut po{{P[0], P[1], P[2]}, 3, Mp};
-                // candidates: fused, deferred, and each distinct slice count
-                // that keeps at most one CTA per SM
-                std::vector<Split> cands = {Split{1, 0}, Split{1, 1}};
-                for (int ks = 2; ks <= std::min(16, chunks) && ks * tiles <= sms; ++ks) {
-                    const Split c = normalise(h, ks, 1, sh.K, tiles);
-                    if (c.ks > 1 && c.ks != cands.back().ks) cands.push_back(c);
+                // candidates: 128-wide tiles fused, deferred, and split-K with
+                // each distinct slice count that keeps at most one CTA per SM;
+                // 64-wide tiles deferred and split the same way
+                std::vector<Split> cands = {Split{1, 0, 128}, Split{1, 1, 128}};
+                for (int bn : {128, 64}) {
+                    const int tb = tm * ((N + bn - 1) / bn);
+                    if (bn == 64) cands.push_back(Split{1, 1, 64});
+                    int last = 1;
+                    for (int ks = 2; ks <= std::min(16, chunks) && ks * tb <= sms; ++ks) {
+                        const Split c = normalise(h, Split{ks, 1, bn}, sh.M, N, sh.K);
+                        if (c.ks > 1 && c.bn == bn && c.ks != last) {
+                            cands.push_back(c);
+                            last = c.ks;
+                        }
+                    }
                 }
                 std::vector<float> times;
                 for (const Split& c : cands) {
                     constexpr int kReps = 3;
                     for (int r = 0; r <= kReps && rc == L1_OK; ++r) {
                         if (r == 1) cudaEventRecord(e0, s);
-                        const int q = launch_inst<EpiTune, 3, 3>(h, maps, tl, sh.M, N, sh.K, epi, po, nullptr,
-                                                                 nullptr, c);
+                        const int q = launch<EpiTune>(h, sh.M, N, sh.K, op, tl, epi, po, nullptr, nullptr, c);
                         if (q < 0) rc = q;
                     }
                     if (rc) break;
@@ -220,13 +225,13 @@ int tune_splits(Handle* h) {
                     times.push_back(1e3f * ms / kReps);
                 }
                 if (rc) break;
-                // the first candidate (fused, then deferred, then fewer
-                // slices) within 2 % of the fastest
+                // the first candidate (128-wide fused, deferred, fewer
+                // slices, then 64-wide) within 2 % of the fastest
                 float fastest = 1e30f;
                 for (float t : times) fastest = std::min(fastest, t);
                 size_t best = 0;
                 while (times[best] > 1.02f * fastest) ++best;
-                h->tc_splits.push_back({sh.M, sh.K, tiles, cands[best].ks, cands[best].defer,
+                h->tc_splits.push_back({sh.M, sh.K, tiles, cands[best].ks, cands[best].defer, cands[best].bn,
                                         (int32_t)std::lround(times[best])});
             }
             if (rc) break;

@@ -64,41 +64,56 @@ inline int get_maps(Handle* h, int M, int N, int K, const Operands& op, int bn, 
     return L1_OK;
 }
 
-// How a sweep's output tiles are produced: K slices (ks > 1: split-K, the
-// slices' FP32 sums added in slice order by finish_kernel, deterministic for a
-// given batch width) and whether the tile epilogue runs in the sweep (fused)
-// or in finish_kernel from the tile's FP32 sums (deferred; always with
-// ks > 1).  The scratch holds ks x tiles x 128 x 128 floats.
+// Row blocks per finish-kernel CTA: long contiguous runs of a column when
+// the batch is wide, one block per CTA (more CTAs) when it is narrow.
+inline int fin_row_blocks(int tiles_m, int N) {
+    const int sms = 152;
+    return (int64_t)N * tiles_m >= 8LL * sms * kFinRB ? kFinRB : 1;
+}
+
+// How a sweep's output tiles are produced: their width bn (128, or 64 for
+// narrow batches: half the MMA work per CTA, three ring stages), K slices
+// (ks > 1: split-K, the slices' FP32 sums added in slice order by
+// finish_kernel, deterministic for a given batch width) and whether the tile
+// epilogue runs in the sweep (fused; 128-wide tiles only) or in
+// finish_kernel from the tile's FP32 sums (deferred; always with ks > 1 or
+// bn = 64).  The scratch holds ks x tiles x 128 x bn floats.
 struct Split {
-    int ks, defer;
+    int ks, defer, bn;
 };
 
-inline Split normalise(const Handle* h, int ks, int defer, int K, int tiles) {
+inline Split normalise(const Handle* h, Split want, int M, int N, int K) {
     const int chunks = (K + kChunk - 1) / kChunk;
-    ks = std::max(1, std::min(std::min(ks, chunks), 16));
+    const int bn = want.bn == 64 ? 64 : 128;
+    int ks = std::max(1, std::min(std::min(want.ks, chunks), 16));
     const int cps = (chunks + ks - 1) / ks;
     ks = (chunks + cps - 1) / cps;  // no empty slice
-    Split r{ks, (ks > 1 || defer) ? 1 : 0};
-    if (r.defer && (size_t)r.ks * tiles * kBM * 128 > h->tc_wk_elems) r = Split{1, 0};
+    Split r{ks, (ks > 1 || want.defer || bn == 64) ? 1 : 0, bn};
+    const size_t tiles = (size_t)((M + kBM - 1) / kBM) * ((N + bn - 1) / bn);
+    if (r.defer && (size_t)r.ks * tiles * kBM * bn > h->tc_wk_elems) r = Split{1, 0, 128};
     return r;
 }
 
-// The autotuner's choice for (M, K, tiles) (tune_splits): the entry of that
-// tile count, else of the nearest smaller one (its slice count capped at one
-// CTA per SM).  Without one (tuning off, or a shape it did not time): the
-// epilogue deferred, and enough K slices to give every SM a CTA when a
-// quarter of them has a tile -- what the tuner chose for the 4096 x 4000 and
-// 1024 x 1200 cross-and-bouquet shapes at every width it timed.
-inline Split split_choice(const Handle* h, int M, int K, int tiles) {
+// The autotuner's choice for (M, K) at the batch's count of 128-wide tiles
+// (tune_splits): the entry of that count, else of the nearest smaller one
+// (its slice count capped at one CTA per SM).  Without one (tuning off, or a
+// shape it did not time): 128-wide tiles, the epilogue deferred, and enough
+// K slices to give every SM a CTA when a quarter of them has a tile.
+inline Split split_choice(const Handle* h, int M, int N, int K) {
     const int sms = h->sms > 0 ? h->sms : 152;
-    if (!h->tc_wk) return Split{1, 0};
-    const std::array<int32_t, 6>* near = nullptr;
+    if (!h->tc_wk) return Split{1, 0, 128};
+    const int tm = (M + kBM - 1) / kBM, tiles = tm * ((N + 127) / 128);
+    const std::array<int32_t, 7>* near = nullptr;
     for (const auto& e : h->tc_splits)
         if (e[0] == M && e[1] == K && e[2] <= tiles && (!near || e[2] > (*near)[2])) near = &e;
-    if (near) return normalise(h, std::min((*near)[3], std::max(1, sms / tiles)), (*near)[4], K, tiles);
+    if (near) {
+        const int bn = (*near)[5];
+        const int tb = tm * ((N + bn - 1) / bn);
+        return normalise(h, Split{std::min((*near)[3], std::max(1, sms / tb)), (*near)[4], bn}, M, N, K);
+    }
     const int chunks = (K + kChunk - 1) / kChunk;
-    if (4 * tiles > sms || chunks < 4) return normalise(h, 1, 1, K, tiles);
-    return normalise(h, std::min(sms / tiles, 16), 1, K, tiles);
+    if (4 * tiles > sms || chunks < 4) return normalise(h, Split{1, 1, 128}, M, N, K);
+    return normalise(h, Split{std::min(sms / tiles, 16), 1, 128}, M, N, K);
 }
 
 // Time the tile strategies of each tensor-core sweep shape of the handle (A u,
@@ -109,30 +124,30 @@ inline Split split_choice(const Handle* h, int M, int K, int tiles) {
 int tune_splits(Handle* h);
 
 // One BF16 tensor-core sweep sum_t a_{ia(t)} x_{ix(t)} with epilogue epi
-// (gemm_bf16.cuh): operands split on the aligned grid of 128-element K
-// blocks, exactly one leading term (0, 0); the functor returns the value
-// that goes to the piece sink po (po.np = 0: none).  Returns the number of
-// row blocks (partials per column) or a negative error code.
-template <class E, int NPA, int NPX>
+// (gemm_bf16.cuh), tiles and slices as sp says (resolved by launch):
+// operands split on the aligned grid of 128-element K blocks, exactly one
+// leading term (0, 0); the functor returns the value that goes to the piece
+// sink po (po.np = 0: none).  Returns the number of row blocks (partials per
+// column) or a negative error code.
+template <class E, int NPA, int NPX, int BN>
 int launch_inst(Handle* h, const Maps& maps, const Terms& tl, int M, int N, int K, const E& epi,
-                const PieceOut& po, double* part, const int32_t* active, Split force = Split{0, 0}) {
-    using S = Cfg<128, NPA, NPX>;
+                const PieceOut& po, double* part, const int32_t* active, Split sp) {
+    using S = Cfg<BN, NPA, NPX>;
     static bool attr_set = false;
     if (!attr_set) {
-        L1_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<E, NPA, NPX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         S::kBytes));
+        L1_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<E, NPA, NPX, BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes));
         attr_set = true;
     }
-    const int tiles_m = (M + kBM - 1) / kBM, tiles = tiles_m * ((N + 127) / 128);
-    const Split sp = force.ks > 0 ? normalise(h, force.ks, force.defer, K, tiles) : split_choice(h, M, K, tiles);
+    const int tiles_m = (M + kBM - 1) / kBM, tiles = tiles_m * ((N + BN - 1) / BN);
     const int ks = sp.ks;
-    sweep_kernel<E, NPA, NPX><<<tiles * ks, kThreads, S::kBytes, h->stream>>>(
+    sweep_kernel<E, NPA, NPX, BN><<<tiles * ks, kThreads, S::kBytes, h->stream>>>(
         maps, tl, M, N, K, epi, po, part, active, h->tc_err, ks, sp.defer, h->tc_wk);
     L1_LAUNCH_CHECK(h);
     if (sp.defer) {
-        const int fin = tiles_m * ((N + kFinCols - 1) / kFinCols);
-        finish_kernel<E><<<fin, kBM, 0, h->stream>>>(M, N, ks, h->tc_wk, (int64_t)tiles_m * kBM, nullptr, epi, po,
-                                                     part, active);
+        const int rbs = fin_row_blocks(tiles_m, N);
+        finish_kernel<E><<<N * ((tiles_m + rbs - 1) / rbs), kBM, 0, h->stream>>>(
+            M, N, ks, h->tc_wk, (int64_t)tiles_m * kBM, nullptr, epi, po, part, active, rbs);
         L1_LAUNCH_CHECK(h);
     }
     return tiles_m;
@@ -145,17 +160,19 @@ template <class E>
 int finish(Handle* h, int M, int N, int ksplit, const float* src, int64_t lds, const float* colscale, const E& epi,
            const PieceOut& po, double* part, const int32_t* active) {
     const int tiles_m = (M + kBM - 1) / kBM;
-    const int fin = tiles_m * ((N + kFinCols - 1) / kFinCols);
-    finish_kernel<E><<<fin, kBM, 0, h->stream>>>(M, N, ksplit, src, lds, colscale, epi, po, part, active);
+    const int rbs = fin_row_blocks(tiles_m, N);
+    finish_kernel<E><<<N * ((tiles_m + rbs - 1) / rbs), kBM, 0, h->stream>>>(M, N, ksplit, src, lds, colscale, epi,
+                                                                           po, part, active, rbs);
     L1_LAUNCH_CHECK(h);
     return tiles_m;
 }
 
 // Piece counts (npa, npx) a launch may use: square splits of two or three
-// pieces, and one-piece A with a two- or three-piece panel.
+// pieces, and one-piece A with a two- or three-piece panel; 64-wide tiles
+// for the three-piece square split.  force.ks > 0 overrides the tile choice.
 template <class E>
 int launch(Handle* h, int M, int N, int K, const Operands& op, const Terms& tl, const E& epi, const PieceOut& po,
-           double* part, const int32_t* active) {
+           double* part, const int32_t* active, Split force = Split{0, 0, 128}) {
     if (tl.n < 1 || tl.n > kMaxTerms) return L1_ERR_INVALID_ARG;
     int nhi = 0;
     for (int t = 0; t < tl.n; ++t) {
@@ -165,13 +182,18 @@ int launch(Handle* h, int M, int N, int K, const Operands& op, const Terms& tl, 
     if (nhi != 1) return L1_ERR_INVALID_ARG;  // exactly one leading term a_0 x_0
     if ((op.lda & 7) || (op.ldx & 7) || po.np < 0 || po.np > kMaxPieces || (po.np > 0 && (po.ld < M)))
         return L1_ERR_INVALID_ARG;
+    const int cfg = op.npa * 10 + op.npx;
+    Split sp = force.ks > 0 ? normalise(h, force, M, N, K) : split_choice(h, M, N, K);
+    if (sp.bn == 64 && cfg != 33) sp = normalise(h, Split{sp.ks, 1, 128}, M, N, K);
     Maps maps;
-    L1_TRY(get_maps(h, M, N, K, op, 128, &maps));
-    switch (op.npa * 10 + op.npx) {
-        case 12: return launch_inst<E, 1, 2>(h, maps, tl, M, N, K, epi, po, part, active);
-        case 13: return launch_inst<E, 1, 3>(h, maps, tl, M, N, K, epi, po, part, active);
-        case 22: return launch_inst<E, 2, 2>(h, maps, tl, M, N, K, epi, po, part, active);
-        case 33: return launch_inst<E, 3, 3>(h, maps, tl, M, N, K, epi, po, part, active);
+    L1_TRY(get_maps(h, M, N, K, op, sp.bn, &maps));
+    switch (cfg) {
+        case 12: return launch_inst<E, 1, 2, 128>(h, maps, tl, M, N, K, epi, po, part, active, sp);
+        case 13: return launch_inst<E, 1, 3, 128>(h, maps, tl, M, N, K, epi, po, part, active, sp);
+        case 22: return launch_inst<E, 2, 2, 128>(h, maps, tl, M, N, K, epi, po, part, active, sp);
+        case 33:
+            if (sp.bn == 64) return launch_inst<E, 3, 3, 64>(h, maps, tl, M, N, K, epi, po, part, active, sp);
+            return launch_inst<E, 3, 3, 128>(h, maps, tl, M, N, K, epi, po, part, active, sp);
         default: return L1_ERR_UNSUPPORTED;
     }
 }
