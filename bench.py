@@ -65,9 +65,12 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates of the part
 # (all 1024 columns active, cold cache) of each CUDA-core sweep of this
 # build, and the algorithmic bytes of that launch
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-width launch of
-# the tensor-core sweeps of this build (filled from profiles/), keyed by
-# workload and sweep
-TC_TRAFFIC = {}
+# the tensor-core sweeps of this build (the sweep and its finish kernel, the
+# deferred epilogue, as CUDA events bracket both), keyed by workload and
+# sweep; profiles/dalm_tc_sweeps_cab_m4096_n4000_N4096_ncu_full.md
+TC_TRAFFIC = {("cab_dalm_m4096_n4000_N4096", "A_V"): 910.0e6,
+              ("cab_dalm_m4096_n4000_N4096", "Finv_d"): 1230.3e6,
+              ("cab_dalm_m4096_n4000_N4096", "At_y"): 1076.6e6}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -476,8 +479,9 @@ def bench_ours(args, rank, world):
         roofline = {"bound": "tensor",
                     "kernel": f"sweep {names[k]} (tc16::sweep_kernel, tcgen05 kind::f16, 3 x 3 BF16 pieces)",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": tr,
-                    "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-width launch" if tr else None,
+                    "traffic": None,
+                    "traffic_note": ("the ncu capture is of a full-width launch: roofline_full_width.traffic"
+                                     if tr else None),
                     "peak_note": ("of measured bf16_tflops_sustained; achieved counts the algorithmic FP32 "
                                   "products 2*M*K*(active columns)"),
                     "executed_tflops": achieved * terms, "executed_frac": achieved * terms / peak,
@@ -502,10 +506,14 @@ def bench_ours(args, rank, world):
     fms = fw1["sweep_ms"][k] - fw0["sweep_ms"][k]
     ffl = fw1["sweep_flop"][k] - fw0["sweep_flop"][k]
     fach = ffl / (fms / 1e3) / 1e12 if fms > 0 else 0.0
+    trf = TC_TRAFFIC.get((workload_name(cfg), names[k])) if tc else None
     roofline_full = {"bound": roofline["bound"], "kernel": roofline["kernel"], "achieved": fach,
                      "peak": roofline["peak"], "unit": "TFLOP/s", "frac": fach / roofline["peak"],
                      "executed_frac": fach * terms / roofline["peak"],
                      "avg_launch_us": 1e3 * fms / 32.0,
+                     "traffic": trf,
+                     "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-width launch "
+                                      "(sweep + finish kernel, cold cache), bytes" if trf else None),
                      "note": f"32 iterations, all {N} columns active, same handle and events"}
 
     # ---- the plain per-instance FP32 GPU solver (l1_solve_plain: one right-
