@@ -174,7 +174,7 @@ struct Cfg {
 };
 
 constexpr int kEpiWarps = 8;                  // two per TMEM lane quarter
-constexpr int kGroupM = 16;                   // row tiles per group of the tile order
+constexpr int kGroupM = 16;                   // row tiles per group of the tile order (4 .. 32: same time)
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 // The epilogue of one 128 x BN tile whose values are in tile_s (column-
@@ -546,7 +546,11 @@ sweep_kernel(const __grid_constant__ Maps maps, const Terms tl, int M, int N, in
 // epilogue) and the aligned BF16 pieces on the grid of the largest magnitude
 // of each 128-row block.  A CTA reads each array of its column in runs of up
 // to kFinRB x 512 contiguous bytes; rbs (1 .. kFinRB) row blocks per CTA.
-constexpr int kFinRB = 8;
+#ifndef L1_FIN_RB
+#define L1_FIN_RB 2  // measured on the 4096 x 4000 solve: 1 5.13 s, 2 4.94 s, 4 5.02 s, 8 5.24 s
+#endif
+constexpr int kFinRB = L1_FIN_RB;
+static_assert(kFinRB >= 1 && kFinRB <= 8, "row blocks per finish CTA");
 
 // The sums are wk[(z * N + j) * ldw + i] over the slices z < ksplit; with
 // colscale they are multiplied by colscale[j] before the epilogue.

@@ -92,21 +92,29 @@ int make_factor_pieces(Handle* h) {
 // --------------------------------------------------------------- autotuner
 namespace {
 
-// Epilogue of the timing launches: reads and writes one float per output
-// element (the real epilogues move one to four) and emits BF16 pieces.
+// Epilogue of the timing launches: the traffic of the heaviest real one (the
+// y-step's, EpiTcY for CAB): three floats read and four written per output
+// element, besides the BF16 pieces.
 struct EpiTune {
     static constexpr int NRED = 0;
     struct State {
-        float s;
+        float a, b, c;
         int act;
     };
-    float* S;
-    int64_t ld;
-    __device__ State load(int i, int j) const { return State{S[(int64_t)j * ld + i], 1}; }
+    float* S;  // four planes of ld x N
+    int64_t ld, plane;
+    __device__ State load(int i, int j) const {
+        const int64_t o = (int64_t)j * ld + i;
+        return State{S[o], S[plane + o], S[2 * plane + o], 1};
+    }
     __device__ float apply(int i, int j, float acc, const State& st, float*) const {
-        const float v = fmaf(st.s, 0.5f, acc);
-        S[(int64_t)j * ld + i] = v;
-        return v;
+        const int64_t o = (int64_t)j * ld + i;
+        const float y = fmaf(st.a, 0.5f, acc);
+        S[o] = y;
+        S[plane + o] = fmaf(st.b, 0.5f, y);
+        S[2 * plane + o] = fmaf(st.c, 0.5f, y);
+        S[3 * plane + o] = y - st.c;
+        return y;
     }
 };
 
@@ -143,7 +151,7 @@ int tune_splits(Handle* h) {
     if (!h->tc_wk) return L1_OK;
     const int Nt = kMaxTilesN * 128;
     const int64_t Kp = round_up(std::max(m, n), 8), Mp = round_up(std::max(m, n), 128);
-    const size_t xbytes = (size_t)kMaxPieces * Kp * Nt * 2, sbytes = (size_t)Mp * Nt * 4,
+    const size_t xbytes = (size_t)kMaxPieces * Kp * Nt * 2, sbytes = (size_t)4 * Mp * Nt * 4,
                  pbytes = (size_t)kMaxPieces * Mp * Nt * 2, wbytes = (size_t)Mp * Nt * 4;
     uint8_t* scratch = nullptr;
     if (xbytes + sbytes + pbytes + wbytes > ((size_t)3 << 30) ||
@@ -188,7 +196,7 @@ int tune_splits(Handle* h) {
                 if (rc != L1_OK) break;
                 const int tiles = tm * tn, N = tn * 128;
                 Operands op{{sh.a[0], sh.a[1], sh.a[2]}, 3, {X[0], X[1], X[2]}, 3, sh.lda, Kp};
-                const EpiTune epi{S, Mp};
+                const EpiTune epi{S, Mp, (int64_t)Mp * Nt};
                 const PieceOut po{{P[0], P[1], P[2]}, 3, Mp};
                 // candidates: 128-wide tiles fused, deferred, and split-K with
                 // each distinct slice count that keeps at most one CTA per SM;
