@@ -90,6 +90,9 @@ def lib() -> C.CDLL:
             L.orc_fista_qp.restype = C.c_int
             L.orc_fista_qp.argtypes = [dp, C.c_int, C.c_int, dp, C.c_double, C.c_double,
                                        C.c_double, C.c_int, dp, C.POINTER(Stats)]
+            L.orc_fista_cont.restype = C.c_int
+            L.orc_fista_cont.argtypes = [dp, C.c_int, C.c_int, dp, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_double, C.c_int, dp, C.POINTER(Stats)]
             L.orc_palm.restype = C.c_int
             L.orc_palm.argtypes = [dp, C.c_int, C.c_int, dp, C.POINTER(PalmOpts), dp, dp, dp,
                                    C.POINTER(Stats)]
@@ -144,6 +147,23 @@ def fista_qp(A, b, lam: float, L: float | None = None, tol: float = 1e-10,
     st = Stats()
     _check(lib().orc_fista_qp(_p(A), m, n, _p(b), lam, L, tol, max_iter, _p(x), C.byref(st)),
            "fista_qp")
+    return x, st.as_dict()
+
+
+def fista_cont(A, b, lam: float, lam0: float, rho: float = 0.95, L: float | None = None,
+               tol: float = 1e-10, max_iter: int = 100000):
+    """FISTA with fixed-point continuation (reading R17): Eq. 18 with lambda_k
+    decreasing geometrically (factor rho per iteration) from lam0 to lam.
+    Returns (x, stats)."""
+    A = _f64(A, True)
+    b = _f64(b)
+    m, n = A.shape
+    if L is None:
+        L = lipschitz(A)
+    x = np.zeros(n)
+    st = Stats()
+    _check(lib().orc_fista_cont(_p(A), m, n, _p(b), lam0, lam, rho, L, tol, max_iter, _p(x), C.byref(st)),
+           "fista_cont")
     return x, st.as_dict()
 
 

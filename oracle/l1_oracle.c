@@ -53,6 +53,11 @@
  *   R16 The alignment step of §II-B solved by PALM: Algorithm 1 with the
  *       x-step replaced by the exact least-squares minimiser over the
  *       unpenalised w, and xi fixed at 2m/||b||_1.
+ *   R17 FISTA with fixed-point continuation (the setup of the comparison in
+ *       §VI-A): iteration k of Eq. 18 uses lambda_k, lambda_1 = lambda_0 given,
+ *       lambda_{k+1} = max(rho lambda_k, lambda) with rho = 0.95; t and the
+ *       extrapolation carry over when lambda changes; the stopping rule (R6
+ *       on x) is applied only once lambda_k has reached lambda.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -171,11 +176,36 @@ double orc_lipschitz(const double* A, int m, int n, int max_iter, double rtol,
 
 /* ------------------------------------------------ FISTA for (QP_lambda) */
 
-/* Eq. 18 (§IV-A) on F(x) = 1/2 ||b - A x||^2 + lambda ||x||_1:
+/* One step of Eq. 18 (§IV-A) on F(x) = 1/2 ||b - A x||^2 + lambda ||x||_1:
  *   x_k     = soft(y_k - grad f(y_k)/L, lambda/L),  grad f(y) = A^T (A y - b)
  *   t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
  *   y_{k+1} = x_k + (t_k - 1)/t_{k+1} (x_k - x_{k-1}),
- * with y_1 = x_0 = 0, t_1 = 1.  Stops on R6 applied to x. */
+ * from y = y_k, xp = x_{k-1}, *tp = t_k; leaves x = x_k, y = y_{k+1},
+ * xp = x_k, *tp = t_{k+1}; returns the relative change of x (R6).  r and g
+ * are m- and n-vectors of scratch. */
+static double fista_step(const double* A, int m, int n, const double* b, double lambda, double L,
+                         double* y, double* xp, double* r, double* g, double* x, double* tp) {
+    const double t = *tp;
+    mat_vec(A, m, n, y, r);
+    for (int i = 0; i < m; ++i) r[i] = b[i] - r[i];      /* r = b - A y */
+    mat_tvec(A, m, n, r, g);                               /* g = -grad f(y) */
+    for (int j = 0; j < n; ++j) x[j] = soft(y[j] + g[j] / L, lambda / L);
+    const double t_new = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    const double mu = (t - 1.0) / t_new;
+    double d2 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double dj = x[j] - xp[j];
+        d2 += dj * dj;
+        y[j] = x[j] + mu * dj;
+    }
+    const double rel = rel_change(sqrt(d2), nrm2(xp, n));
+    memcpy(xp, x, sizeof(double) * n);
+    *tp = t_new;
+    return rel;
+}
+
+/* FISTA (Eq. 18) for (QP_lambda) with y_1 = x_0 = 0, t_1 = 1; stops on R6
+ * applied to x. */
 int orc_fista_qp(const double* A, int m, int n, const double* b, double lambda,
                  double L, double tol, int max_iter, double* x, orc_stats* st) {
     if (!A || !b || !x || m <= 0 || n <= 0 || !(L > 0.0) || lambda < 0.0) return ORC_ERR_ARG;
@@ -187,22 +217,39 @@ int orc_fista_qp(const double* A, int m, int n, const double* b, double lambda,
     double t = 1.0, rel = INFINITY;
     int k = 0, conv = 0;
     for (k = 1; k <= max_iter; ++k) {
-        mat_vec(A, m, n, y, r);
-        for (int i = 0; i < m; ++i) r[i] = b[i] - r[i];      /* r = b - A y */
-        mat_tvec(A, m, n, r, g);                               /* g = -grad f(y) */
-        for (int j = 0; j < n; ++j) x[j] = soft(y[j] + g[j] / L, lambda / L);
-        const double t_new = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-        const double mu = (t - 1.0) / t_new;
-        double d2 = 0.0;
-        for (int j = 0; j < n; ++j) {
-            const double dj = x[j] - xp[j];
-            d2 += dj * dj;
-            y[j] = x[j] + mu * dj;
-        }
-        rel = rel_change(sqrt(d2), nrm2(xp, n));
-        memcpy(xp, x, sizeof(double) * n);
-        t = t_new;
+        rel = fista_step(A, m, n, b, lambda, L, y, xp, r, g, x, &t);
         if (rel < tol) { conv = 1; break; }
+    }
+    if (st) {
+        st->iters = k > max_iter ? max_iter : k;
+        st->inner_total = st->iters;
+        st->converged = conv;
+        st->rel_change = rel;
+        st->param = lambda / L;
+    }
+    free(y); free(xp); free(r); free(g);
+    return ORC_OK;
+}
+
+/* FISTA with continuation (R17): the steps of Eq. 18 with the threshold
+ * lambda_k / L of a geometrically decreasing lambda_k, from lambda_0 down to
+ * lambda; the rule R6 is applied once lambda_k = lambda. */
+int orc_fista_cont(const double* A, int m, int n, const double* b, double lambda0, double lambda,
+                   double rho, double L, double tol, int max_iter, double* x, orc_stats* st) {
+    if (!A || !b || !x || m <= 0 || n <= 0 || !(L > 0.0) || lambda < 0.0 || lambda0 < lambda ||
+        !(rho > 0.0 && rho <= 1.0))
+        return ORC_ERR_ARG;
+    double* y = (double*)zalloc(n);
+    double* xp = (double*)zalloc(n);
+    double* r = (double*)zalloc(m);
+    double* g = (double*)zalloc(n);
+    if (!y || !xp || !r || !g) { free(y); free(xp); free(r); free(g); return ORC_ERR_NOMEM; }
+    double t = 1.0, rel = INFINITY, lam = lambda0;
+    int k = 0, conv = 0;
+    for (k = 1; k <= max_iter; ++k) {
+        rel = fista_step(A, m, n, b, lam, L, y, xp, r, g, x, &t);
+        if (lam <= lambda && rel < tol) { conv = 1; break; }
+        lam = rho * lam > lambda ? rho * lam : lambda;
     }
     if (st) {
         st->iters = k > max_iter ? max_iter : k;

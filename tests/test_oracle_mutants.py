@@ -51,16 +51,21 @@ MUTANTS = [
     ("fista_threshold_unscaled", "Eq. 18 threshold lambda/L",
      "x[j] = soft(y[j] + g[j] / L, lambda / L);", "x[j] = soft(y[j] + g[j] / L, lambda);"),
     ("fista_no_momentum", "Eq. 18 momentum (t_k - 1)/t_{k+1}",
-     "        const double mu = (t - 1.0) / t_new;\n        double d2",
-     "        const double mu = 0.0;\n        double d2"),
+     "    const double mu = (t - 1.0) / t_new;\n    double d2",
+     "    const double mu = 0.0;\n    double d2"),
     ("fista_momentum_index", "Eq. 18 momentum (t_k - 1)/t_{k+1}",
-     "        const double mu = (t - 1.0) / t_new;\n        double d2",
-     "        const double mu = t / t_new;\n        double d2"),
+     "    const double mu = (t - 1.0) / t_new;\n    double d2",
+     "    const double mu = t / t_new;\n    double d2"),
     ("fista_extrapolate_from_old", "Eq. 18 y_{k+1} = x_k + mu (x_k - x_{k-1})",
      "y[j] = x[j] + mu * dj;", "y[j] = xp[j] + mu * dj;"),
     ("fista_t_update", "Eq. 18 t_{k+1}",
-     "        const double t_new = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));\n        const double mu = (t - 1.0) / t_new;\n        double d2",
-     "        const double t_new = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t));\n        const double mu = (t - 1.0) / t_new;\n        double d2"),
+     "    const double t_new = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));\n    const double mu = (t - 1.0) / t_new;\n    double d2",
+     "    const double t_new = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t));\n    const double mu = (t - 1.0) / t_new;\n    double d2"),
+    # FISTA with continuation, reading R17
+    ("fista_cont_below_target", "R17 lambda_{k+1} = max(rho lambda_k, lambda)",
+     "lam = rho * lam > lambda ? rho * lam : lambda;", "lam = rho * lam;"),
+    ("fista_cont_stops_early", "R17 the rule applies once lambda_k = lambda",
+     "if (lam <= lambda && rel < tol) { conv = 1; break; }", "if (rel < 1e3 * tol) { conv = 1; break; }"),
     # PALM, Algorithm 1 / Eq. 33 / reading R10
     ("palm_e_multiplier_sign", "Algorithm 1 e-step",
      "e_new[i] = soft(b[i] - Ax[i] + theta[i] / xi, 1.0 / xi);",

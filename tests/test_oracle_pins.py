@@ -690,3 +690,54 @@ def test_unrolled_adjoint_identity():
         assert abs(Jv @ u - v @ JTu) <= 1e-8 * max(1.0, abs(v @ JTu))
         checked += 1
     assert checked >= 3
+
+
+def test_fista_continuation_reaches_the_lasso_solution():
+    """Reading R17 (FISTA with fixed-point continuation, the setup of the
+    §VI-A comparison).  With lambda_0 = lambda it is Eq. 18 step for step.
+    From lambda_0 = ||A^T b||_inf (where x = 0 is the minimiser) it ends at
+    the same (QP_lambda) minimiser, checked by enumeration of sign patterns on
+    tiny inputs and by the KKT conditions of Eq. 12 on the §VI-A instance,
+    in fewer iterations than plain FISTA there (§VI-A: continuation makes
+    FISTA more effective)."""
+    g = np.random.default_rng(17)
+    for trial in range(6):
+        m, n = 4, 6
+        A = g.standard_normal((m, n))
+        A = np.asfortranarray(A / np.linalg.norm(A, axis=0))
+        b = g.standard_normal(m)
+        lmax = np.max(np.abs(A.T @ b))
+        lam = 0.2 * lmax
+        best, xbest = np.inf, None
+        for k in range(0, m + 1):
+            for S in itertools.combinations(range(n), k):
+                S = list(S)
+                for sgn in itertools.product([-1.0, 1.0], repeat=k):
+                    x = np.zeros(n)
+                    if k:
+                        AS = A[:, S]
+                        xs = np.linalg.solve(AS.T @ AS, AS.T @ b - lam * np.array(sgn))
+                        if np.any(np.sign(xs) != np.array(sgn)):
+                            continue
+                        x[S] = xs
+                    F = 0.5 * np.sum((b - A @ x) ** 2) + lam * np.abs(x).sum()
+                    if F < best:
+                        best, xbest = F, x
+        x, st = oracle.fista_cont(A, b, lam, lam0=lmax, tol=1e-14, max_iter=200000)
+        assert np.linalg.norm(x - xbest) <= 1e-7 * max(1.0, np.linalg.norm(xbest)), trial
+        xq, _ = oracle.fista_qp(A, b, lam, tol=1e-10, max_iter=2000)
+        xc, _ = oracle.fista_cont(A, b, lam, lam0=lam, tol=1e-10, max_iter=2000)
+        assert np.array_equal(xq, xc)
+    pr = synthetic.p1_instance(200, 400, 20, seed=0)
+    A, b = pr["A"], pr["b"]
+    L = oracle.lipschitz(A)
+    lmax = np.max(np.abs(A.T @ b))
+    lam = 1e-3 * lmax
+    xq, sq = oracle.fista_qp(A, b, lam, L, tol=1e-8, max_iter=100000)
+    xc, sc = oracle.fista_cont(A, b, lam, lam0=lmax, L=L, tol=1e-8, max_iter=100000)
+    assert sc["converged"] and sc["iters"] < sq["iters"], (sc["iters"], sq["iters"])
+    c = A.T @ (b - A @ xc)  # Eq. 12 at the minimiser, to the accuracy the rule allows
+    S = np.abs(xc) > 0
+    assert np.max(np.abs(c)) <= lam * (1 + 1e-3)
+    assert np.max(np.abs(c[S] - lam * np.sign(xc[S]))) <= 1e-3 * lam
+    assert np.linalg.norm(xc - xq) <= 1e-6 * np.linalg.norm(xq)
