@@ -68,9 +68,9 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates of the part
 # the tensor-core sweeps of this build (the sweep and its finish kernel, the
 # deferred epilogue, as CUDA events bracket both), keyed by workload and
 # sweep; profiles/dalm_tc_sweeps_cab_m4096_n4000_N4096_ncu_full.md
-TC_TRAFFIC = {("cab_dalm_m4096_n4000_N4096", "A_V"): 910.0e6,
-              ("cab_dalm_m4096_n4000_N4096", "Finv_d"): 1230.3e6,
-              ("cab_dalm_m4096_n4000_N4096", "At_y"): 1076.6e6}
+TC_TRAFFIC = {("cab_dalm_m4096_n4000_N4096", "A_V"): 907.8e6,
+              ("cab_dalm_m4096_n4000_N4096", "Finv_d"): 1228.2e6,
+              ("cab_dalm_m4096_n4000_N4096", "At_y"): 1070.8e6}
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
