@@ -142,6 +142,13 @@ typedef struct {
                           * on face images; on the cross-and-bouquet model it stalls
                           * far from the constraint.  FP32 dictionary and the
                           * tensor-core engine only (L1_ERR_UNSUPPORTED otherwise). */
+    double lambda0;      /* QP_LAMBDA: > lambda -> FISTA with fixed-point continuation
+                          * (the FISTA setup of the §VI-A comparison, reading R17):
+                          * step k of Eq. 18 thresholds at lambda_k / L with
+                          * lambda_1 = lambda0, lambda_{k+1} = max(rho lambda_k,
+                          * lambda), and the stopping rule applies once lambda_k has
+                          * reached lambda; 0 -> plain FISTA at lambda */
+    double cont_rho;     /* continuation factor rho in (0, 1]; 0 -> 0.95 */
 } l1_options;
 
 /* Per-instance results (host memory). */

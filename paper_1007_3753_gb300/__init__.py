@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("unroll_K", C.c_int32), ("unroll_J", C.c_int32), ("ckpt_every", C.c_int32),
                 ("profile", C.c_int32), ("tc_pieces", C.c_int32), ("refine", C.c_int32),
                 ("tc_pieces_y", C.c_int32), ("tc_min_cols", C.c_int32), ("tune", C.c_int32),
-                ("cg_steps", C.c_int32)]
+                ("cg_steps", C.c_int32), ("lambda0", C.c_double), ("cont_rho", C.c_double)]
 
 
 class Result(C.Structure):
@@ -170,7 +170,8 @@ class Solver:
                  class_offsets=None, precision: int = A_FP32, engine: int = ENGINE_AUTO,
                  profile: bool = False, tc_pieces: int = 0, tc_pieces_y: int = 0, tc_min_cols: int = 0,
                  unroll_K: int = 0, unroll_J: int = 0, ckpt_every: int = 0, refine: bool = True,
-                 tune: bool = True, cg_steps: int = 0, stream=None):
+                 tune: bool = True, cg_steps: int = 0, lam0: float = 0.0, cont_rho: float = 0.0,
+                 stream=None):
         L = load()
         o = Options()
         L.l1_options_init(C.byref(o))
@@ -189,6 +190,7 @@ class Solver:
         o.refine = 0 if refine else -1
         o.tune = 0 if tune else -1
         o.cg_steps = cg_steps
+        o.lambda0, o.cont_rho = lam0, cont_rho
         if unroll_J:
             o.unroll_J = unroll_J
         if ckpt_every:

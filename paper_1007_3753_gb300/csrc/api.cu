@@ -136,6 +136,9 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
     if (o.tc_pieces == 1 || o.tc_pieces_y == 1) return L1_ERR_UNSUPPORTED;  // a one-piece panel cannot converge
     if (o.engine == L1_ENGINE_TC && (o.solver != L1_DALM || mode == L1_QP_LAMBDA)) return L1_ERR_UNSUPPORTED;
     if (o.cg_steps < 0) return L1_ERR_INVALID_ARG;
+    // FISTA with continuation (R17): batched (QP_lambda) only
+    if (o.lambda0 < 0.0 || o.cont_rho < 0.0 || o.cont_rho > 1.0) return L1_ERR_INVALID_ARG;
+    if (o.lambda0 > 0.0 && (mode != L1_QP_LAMBDA || o.unroll_K > 0)) return L1_ERR_UNSUPPORTED;
     // DALM with a CG y-step (R15): one step, FP32 dictionary, tensor-core sweeps
     if (o.cg_steps > 0 && (o.cg_steps != 1 || o.solver != L1_DALM || mode == L1_QP_LAMBDA ||
                            o.precision != L1_A_FP32 || o.engine == L1_ENGINE_SIMT || o.unroll_K > 0))
@@ -267,6 +270,7 @@ int l1_setup_group(const float* const* A, const int64_t* m, const int64_t* n, in
     else l1_options_init(&o);
     if (!(o.lambda > 0.0)) return L1_ERR_INVALID_ARG;
     if (o.precision != L1_A_FP32 && o.precision != L1_A_BF16) return L1_ERR_UNSUPPORTED;
+    if (o.lambda0 != 0.0) return L1_ERR_UNSUPPORTED;  // continuation: l1_setup batches only
     for (int64_t i = 0; i < count; ++i)
         if (m[i] <= 0 || n[i] <= 0) return L1_ERR_INVALID_ARG;
     Handle* h = new (std::nothrow) Handle();

@@ -17,7 +17,8 @@ namespace {
 static_assert(sizeof(l1_result) == 6 * 4 + 6 * 8, "l1_result layout");
 
 __global__ void init_cols_kernel(Cols c, const float* B, int64_t ldm, int m, int mode,
-                                 double beta_opt, double xi0_opt, double xi_max, double lambda) {
+                                 double beta_opt, double xi0_opt, double xi_max, double lambda,
+                                 double lambda0) {
     __shared__ double sh[4];
     const int j = blockIdx.x;
     double s = 0.0;
@@ -30,12 +31,13 @@ __global__ void init_cols_kernel(Cols c, const float* B, int64_t ldm, int m, int
     c.beta[j] = (float)beta;
     c.binv[j] = (float)(1.0 / beta);
     // PALM: xi_0 = 2m / ||b||_1 (§V-A); FISTA for QP uses xi = 1/lambda so that
-    // the threshold 1/(xi L) is lambda / L (Eq. 18)
+    // the threshold 1/(xi L) is lambda / L (Eq. 18); with continuation (R17)
+    // xi starts at 1/lambda_0 and grows to its cap 1/lambda
     double xi0;
-    if (mode == L1_QP_LAMBDA) xi0 = 1.0 / lambda;
+    if (mode == L1_QP_LAMBDA) xi0 = 1.0 / (lambda0 > lambda ? lambda0 : lambda);
     else xi0 = xi0_opt > 0.0 ? xi0_opt : (s > 0.0 ? 2.0 * m / s : 1.0);
     c.xi[j] = (float)xi0;
-    c.xicap[j] = (float)(xi0 * xi_max);
+    c.xicap[j] = mode == L1_QP_LAMBDA ? (float)(1.0 / lambda) : (float)(xi0 * xi_max);
     c.mu[j] = 0.0f;
     c.t[j] = 1.0;
     c.active[j] = 1;
@@ -522,7 +524,8 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
         L1_CUDA_TRY(cudaMemcpy2DAsync(P->Y, ldm * sizeof(float), y_init, ldyi * sizeof(float), m * sizeof(float), N,
                                       cudaMemcpyDefault, s));
     Cols c = make_cols(h, 0, N);
-    init_cols_kernel<<<N, 128, 0, s>>>(c, P->B, ldm, m, mode, o.beta, o.xi0, xi_max, o.lambda);
+    init_cols_kernel<<<N, 128, 0, s>>>(c, P->B, ldm, m, mode, o.beta, o.xi0, xi_max, o.lambda,
+                                       o.lambda0);
     L1_LAUNCH_CHECK(h);
 
     const int check_every = o.check_every > 0 ? o.check_every : 16;
@@ -532,6 +535,9 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     PalmParams pp;
     pp.mode = mode;
     pp.growth = (mode == L1_CAB || mode == L1_QP_LAMBDA) ? 1.0f : (float)(o.xi_growth > 0.0 ? o.xi_growth : 1.2);
+    // FISTA with continuation (R17): lambda_{k+1} = max(rho lambda_k, lambda)
+    if (mode == L1_QP_LAMBDA && o.lambda0 > o.lambda)
+        pp.growth = (float)(1.0 / (o.cont_rho > 0.0 ? o.cont_rho : 0.95));
     pp.Linv = h->lipschitz > 0.0 ? (float)(1.0 / h->lipschitz) : 0.0f;
     const int inner_max = o.inner_max > 0 ? o.inner_max : 50;
     const double inner_tol = o.inner_tol > 0.0 ? o.inner_tol : 0.1 * tol;
@@ -797,7 +803,8 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
             L1_CUDA_TRY(cudaMemcpyAsync(P->Ue, w.hUe, pm, cudaMemcpyDeviceToDevice, s));
             L1_CUDA_TRY(cudaMemcpyAsync(P->Y, w.hY, pm, cudaMemcpyDeviceToDevice, s));
             c = make_cols(h, 0, N);
-            init_cols_kernel<<<N, 128, 0, s>>>(c, P->B, ldm, m, mode, o.beta, o.xi0, xi_max, o.lambda);
+            init_cols_kernel<<<N, 128, 0, s>>>(c, P->B, ldm, m, mode, o.beta, o.xi0, xi_max, o.lambda,
+                                       o.lambda0);
             L1_LAUNCH_CHECK(h);
             refine_restart_kernel<<<(N + 255) / 256, 256, 0, s>>>(c, hr1.status, hr1.iters, iters1, N);
             L1_LAUNCH_CHECK(h);

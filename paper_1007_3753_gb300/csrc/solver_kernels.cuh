@@ -427,13 +427,18 @@ __global__ void ctrl_palm_kernel(Cols c, PalmParams p, const double* part_A, int
         c.mu[j] = (float)((tn - 1.0) / tnn);
         const bool finite = isfinite(d2) && isfinite(w2);
         if (p.mode == L1_QP_LAMBDA) {
-            // FISTA of Eq. 18: one loop, the outer rule applies to x_k
+            // FISTA of Eq. 18: one loop, the outer rule applies to x_k; with
+            // continuation (R17, growth > 1) lambda = 1/xi falls by the factor
+            // 1/growth per step down to its target 1/xicap, and the rule
+            // applies once it is there
             c.iters[j] = tot;
             const double rel = rel_change(sqrt(d2), sqrt(w2));
             c.rel[j] = rel;
+            const bool at_target = !(p.growth > 1.0f) || c.xi[j] >= c.xicap[j];
             if (!finite) { c.status[j] = L1_NONFINITE; c.active[j] = 0; }
-            else if (rel < tol) { c.status[j] = L1_CONVERGED; c.active[j] = 0; }
+            else if (at_target && rel < tol) { c.status[j] = L1_CONVERGED; c.active[j] = 0; }
             else if (tot >= max_iter) { c.status[j] = L1_MAX_ITER; c.active[j] = 0; }
+            if (!at_target) c.xi[j] = fminf(c.xi[j] * p.growth, c.xicap[j]);
         } else {
             const double d = sqrt(d2), base = sqrt(w2);
             const bool inner_done = d == 0.0 || (base > 0.0 && d <= inner_tol * base) || l >= inner_max;

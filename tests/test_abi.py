@@ -126,6 +126,10 @@ def test_refused_combinations_before_any_cuda_call(lib):
     assert setup(l1.CAB, solver=l1.PALM, cg_steps=1) == U
     assert setup(l1.CAB, engine=l1.ENGINE_SIMT, cg_steps=1) == U
     assert setup(l1.CAB, precision=l1.A_BF16, cg_steps=1) == U
+    # FISTA with continuation (R17): (QP_lambda) only
+    assert setup(l1.QP_LAMBDA, lambda_=0.1, lambda0=-1.0) == I
+    assert setup(l1.QP_LAMBDA, lambda_=0.1, lambda0=1.0, cont_rho=1.5) == I
+    assert setup(l1.P1, lambda0=1.0) == U
     assert setup(l1.P1, solver=7) == I
     assert setup(l1.P1, precision=9) == I
     assert setup(l1.P1, engine=9) == I

@@ -581,3 +581,59 @@ def test_split_autotuner_records_choices_and_keeps_parity(l1):
     ex.check()
     s.close()
     s0.close()
+
+
+def test_qp_fista_with_continuation_matches_oracle(l1):
+    """FISTA with fixed-point continuation (reading R17) for a batch of
+    (QP_lambda) problems on one Gaussian dictionary: lambda falls by 0.95 per
+    step from lambda_0 = max_j ||A^T b_j||_inf to lambda = 1e-3 lambda_0.
+    After the same number of steps (tol = 0) and at the stopping tolerance
+    (stop within one step of the oracle's) the GPU follows orc_fista_cont;
+    it stops in fewer steps than plain FISTA at the same lambda."""
+    pr = synthetic.p1_instance(200, 400, 20, seed=0)
+    A = pr["A"]
+    g = np.random.default_rng(5)
+    N = 6
+    X0 = np.zeros((400, N))
+    for j in range(N):
+        X0[g.choice(400, 20, replace=False), j] = g.choice([-1.0, 1.0], 20)
+    B = A @ X0
+    lam0 = float(np.max(np.abs(A.T @ B)))
+    lam = 1e-3 * lam0
+    L = oracle.lipschitz(A)
+    s = l1.Solver(_dev(A), mode=l1.QP_LAMBDA, lam=lam, lipschitz=L, lam0=lam0)
+    x, _, res = s.solve(_dev(B), tol=0.0, max_iter=120)
+    x = x.cpu().numpy()
+    ex = Errs("FISTA with continuation, 120 steps")
+    for j in range(N):
+        w, _ = oracle.fista_cont(A, B[:, j], lam, lam0=lam0, L=L, tol=0.0, max_iter=120)
+        ex.add(x[:, j], w)
+    ex.check()
+    tol = 1e-6
+    x, _, res = s.solve(_dev(B), tol=tol, max_iter=20000)
+    x = x.cpu().numpy()
+    assert (res["status"] == l1.CONVERGED).all()
+    s_plain = l1.Solver(_dev(A), mode=l1.QP_LAMBDA, lam=lam, lipschitz=L)
+    _, _, res_plain = s_plain.solve(_dev(B), tol=tol, max_iter=20000)
+    print("steps: continuation", res["iters"], "plain", res_plain["iters"])
+    assert np.all(res["iters"] < res_plain["iters"])
+
+    # at the stopping tolerance: every column stops within one step of the
+    # oracle and agrees with the oracle's iterate at its own stop (the
+    # objective here is (QP_lambda)'s, 1/2 ||b - A x||^2 + lambda ||x||_1)
+    ex = Errs("FISTA with continuation at tol 1e-6")
+    stops = []
+    for j in range(N):
+        w, st = oracle.fista_cont(A, B[:, j], lam, lam0=lam0, L=L, tol=tol, max_iter=20000)
+        kg = int(res["iters"][j])
+        stops.append(kg - st["iters"])
+        if kg != st["iters"]:
+            w, _ = oracle.fista_cont(A, B[:, j], lam, lam0=lam0, L=L, tol=0.0, max_iter=kg)
+        ex.add(x[:, j], w)
+        F = 0.5 * np.sum((B[:, j] - A @ w) ** 2) + lam * np.abs(w).sum()
+        ex.obj.append(abs(res["primal_obj"][j] - F) / F)
+    print("GPU stop - oracle stop", stops)
+    assert max(abs(d) for d in stops) <= 1
+    ex.check()
+    s.close()
+    s_plain.close()
