@@ -7,7 +7,7 @@ double, no BLAS) through ctypes.  It shares no code with the CUDA library in
 ``synthetic``.
 
 Every entry point cites the passage of the paper it restates; the readings of
-ambiguous passages (R1-R11) are listed at the top of ``l1_oracle.c``.
+ambiguous passages (R1-R18) are listed at the top of ``l1_oracle.c``.
 
 Parity pins (tests/test_oracle_pins.py) tie each function to something other
 than itself: brute-force LP vertex enumeration and HiGHS on the LP of Eq. 10,
@@ -93,6 +93,9 @@ def lib() -> C.CDLL:
             L.orc_fista_cont.restype = C.c_int
             L.orc_fista_cont.argtypes = [dp, C.c_int, C.c_int, dp, C.c_double, C.c_double, C.c_double,
                                          C.c_double, C.c_double, C.c_int, dp, C.POINTER(Stats)]
+            L.orc_amp.restype = C.c_int
+            L.orc_amp.argtypes = [dp, C.c_int, C.c_int, dp, C.c_double, C.c_double, C.c_int,
+                                  dp, dp, dp, C.POINTER(Stats)]
             L.orc_palm.restype = C.c_int
             L.orc_palm.argtypes = [dp, C.c_int, C.c_int, dp, C.POINTER(PalmOpts), dp, dp, dp,
                                    C.POINTER(Stats)]
@@ -165,6 +168,23 @@ def fista_cont(A, b, lam: float, lam0: float, rho: float = 0.95, L: float | None
     _check(lib().orc_fista_cont(_p(A), m, n, _p(b), lam0, lam, rho, L, tol, max_iter, _p(x), C.byref(st)),
            "fista_cont")
     return x, st.as_dict()
+
+
+def amp(A, b, tau0: float = 0.0, tol: float = 1e-10, max_iter: int = 10000):
+    """Approximate message passing for P1 (§IV, reading R18): x_0 = 0, z_0 = b,
+    tau_0 = ||A^T b||_inf / 2 unless tau0 > 0.  Returns (x, z, tau, stats):
+    z and tau are those of the last x-step; stats["converged"] is 1 (R6 met),
+    0 (max_iter) or -1 (an iterate stopped being finite)."""
+    A = _f64(A, True)
+    b = _f64(b)
+    m, n = A.shape
+    x = np.zeros(n)
+    z = np.zeros(m)
+    tau = C.c_double(0.0)
+    st = Stats()
+    _check(lib().orc_amp(_p(A), m, n, _p(b), tau0, tol, max_iter, _p(x), _p(z), C.byref(tau), C.byref(st)),
+           "amp")
+    return x, z, tau.value, st.as_dict()
 
 
 def palm(A, b, mode: int = MODE_CAB, tol: float = 1e-10, max_outer: int = 10000,

@@ -58,6 +58,14 @@
  *       lambda_{k+1} = max(rho lambda_k, lambda) with rho = 0.95; t and the
  *       extrapolation carry over when lambda changes; the stopping rule (R6
  *       on x) is applied only once lambda_k has reached lambda.
+ *   R18 AMP (§IV, the message-passing iteration for P1): x_0 = 0, z_0 = b,
+ *       delta = m/n; the paper gives no initial threshold, and tau_0 must lie
+ *       below ||A^T b||_inf (else x_1 = 0, the average derivative is 0 and
+ *       tau stays 0), so tau_0 = ||A^T b||_inf / 2 by default; the average
+ *       derivative of soft(., tau) at v is the fraction of entries with
+ *       |v_i| > tau; the rule R6 on x is applied after each x-step, and a
+ *       stopped iteration keeps z_k and tau_k (the ones that produced the
+ *       returned x); an iterate that is not finite stops it (converged = -1).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -259,6 +267,73 @@ int orc_fista_cont(const double* A, int m, int n, const double* b, double lambda
         st->param = lambda / L;
     }
     free(y); free(xp); free(r); free(g);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------- AMP */
+
+/* Approximate message passing for P1 (§IV, reading R18):
+ *   x_{k+1} = soft(A^T z_k + x_k, tau_k)
+ *   eta_k   = average over i of d soft(v, tau_k)/dv at v = A^T z_k + x_k
+ *   z_{k+1} = b - A x_{k+1} + (eta_k / delta) z_k
+ *   tau_{k+1} = (tau_k / delta) eta_k,          delta = m / n.
+ * tau0 <= 0 takes ||A^T b||_inf / 2.  On return z and *tau hold the z_k and
+ * tau_k of the last x-step (NULL to skip). */
+int orc_amp(const double* A, int m, int n, const double* b, double tau0, double tol, int max_iter,
+            double* x, double* z_out, double* tau_out, orc_stats* st) {
+    if (!A || !b || !x || m <= 0 || n <= 0 || max_iter < 0) return ORC_ERR_ARG;
+    double* z = (double*)zalloc(m);
+    double* v = (double*)zalloc(n);
+    double* xn = (double*)zalloc(n);
+    double* r = (double*)zalloc(m);
+    if (!z || !v || !xn || !r) { free(z); free(v); free(xn); free(r); return ORC_ERR_NOMEM; }
+    const double delta = (double)m / (double)n;
+    memset(x, 0, sizeof(double) * n);
+    memcpy(z, b, sizeof(double) * m);
+    double tau = tau0;
+    if (!(tau > 0.0)) {
+        mat_tvec(A, m, n, b, v);
+        double vmax = 0.0;
+        for (int j = 0; j < n; ++j) vmax = fabs(v[j]) > vmax ? fabs(v[j]) : vmax;
+        tau = 0.5 * vmax;
+    }
+    double rel = INFINITY;
+    int k = 0, conv = 0;
+    for (k = 1; k <= max_iter; ++k) {
+        mat_tvec(A, m, n, z, v);
+        for (int j = 0; j < n; ++j) v[j] += x[j];             /* v = A^T z_k + x_k */
+        int above = 0;
+        for (int j = 0; j < n; ++j) {
+            xn[j] = soft(v[j], tau);
+            if (fabs(v[j]) > tau) ++above;
+        }
+        const double eta = (double)above / (double)n;
+        double d2 = 0.0;
+        for (int j = 0; j < n; ++j) d2 += (xn[j] - x[j]) * (xn[j] - x[j]);
+        rel = rel_change(sqrt(d2), nrm2(x, n));
+        memcpy(x, xn, sizeof(double) * n);
+        if (!isfinite(d2) || !isfinite(tau)) { conv = -1; break; }
+        if (rel < tol) { conv = 1; break; }
+        if (k == max_iter) break;
+        mat_vec(A, m, n, x, r);
+        int finite = 1;
+        for (int i = 0; i < m; ++i) {
+            z[i] = b[i] - r[i] + (eta / delta) * z[i];
+            if (!isfinite(z[i])) finite = 0;
+        }
+        tau = tau / delta * eta;
+        if (!finite) { conv = -1; break; }
+    }
+    if (z_out) memcpy(z_out, z, sizeof(double) * m);
+    if (tau_out) *tau_out = tau;
+    if (st) {
+        st->iters = k > max_iter ? max_iter : k;
+        st->inner_total = st->iters;
+        st->converged = conv;
+        st->rel_change = rel;
+        st->param = tau;
+    }
+    free(z); free(v); free(xn); free(r);
     return ORC_OK;
 }
 

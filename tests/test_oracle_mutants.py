@@ -66,6 +66,17 @@ MUTANTS = [
      "lam = rho * lam > lambda ? rho * lam : lambda;", "lam = rho * lam;"),
     ("fista_cont_stops_early", "R17 the rule applies once lambda_k = lambda",
      "if (lam <= lambda && rel < tol) { conv = 1; break; }", "if (rel < 1e3 * tol) { conv = 1; break; }"),
+    # AMP, §IV / reading R18
+    ("amp_no_onsager", "§IV z-step: the term (eta/delta) z_k",
+     "z[i] = b[i] - r[i] + (eta / delta) * z[i];", "z[i] = b[i] - r[i];"),
+    ("amp_delta_inverted", "§IV delta = m/n",
+     "const double delta = (double)m / (double)n;", "const double delta = (double)n / (double)m;"),
+    ("amp_tau_without_delta", "§IV tau_{k+1} = (tau_k / delta) eta_k",
+     "tau = tau / delta * eta;", "tau = tau * eta;"),
+    ("amp_v_sign", "§IV x-step soft(A^T z + x, tau)",
+     "for (int j = 0; j < n; ++j) v[j] += x[j];", "for (int j = 0; j < n; ++j) v[j] -= x[j];"),
+    ("amp_derivative_everywhere", "R18 average derivative of soft(., tau)",
+     "if (fabs(v[j]) > tau) ++above;", "++above;"),
     # PALM, Algorithm 1 / Eq. 33 / reading R10
     ("palm_e_multiplier_sign", "Algorithm 1 e-step",
      "e_new[i] = soft(b[i] - Ax[i] + theta[i] / xi, 1.0 / xi);",

@@ -741,3 +741,61 @@ def test_fista_continuation_reaches_the_lasso_solution():
     assert np.max(np.abs(c)) <= lam * (1 + 1e-3)
     assert np.max(np.abs(c[S] - lam * np.sign(xc[S]))) <= 1e-3 * lam
     assert np.linalg.norm(xc - xq) <= 1e-6 * np.linalg.norm(xq)
+
+
+def test_amp_recovers_the_planted_vector_of_the_p1_instances():
+    """§IV (approximate message passing) and §VI-A: on Gaussian dictionaries
+    with unit columns AMP reaches the planted sparse x0 -- the unique P1
+    minimiser there -- to near machine precision (relative error below
+    1e-10), in a hundred or so iterations, on the three §VI-A sizes (m = 800;
+    n = 1000, d = 100 and 200; n = 2000, d = 100; nonzeros uniform in
+    [-10, 10]).  On a small instance the minimiser is also taken from the LP
+    of Eq. 10 (HiGHS), independently of x0."""
+    from scipy.optimize import linprog
+    for m, n, d, seed in ((800, 1000, 100, 3), (800, 1000, 200, 4), (800, 2000, 100, 5)):
+        pr = synthetic.p1_instance(m, n, d, seed=seed, entries="uniform10")
+        x, z, tau, st = oracle.amp(pr["A"], pr["b"], tol=1e-12, max_iter=1000)
+        err = np.linalg.norm(x - pr["x0"]) / np.linalg.norm(pr["x0"])
+        assert st["converged"] == 1 and st["iters"] <= 250, (m, n, d, st)
+        assert err <= 1e-10, (m, n, d, err)
+        assert 0.0 < tau < 1e-9
+    pr = synthetic.p1_instance(60, 120, 6, seed=11, entries="uniform10")
+    A, b = pr["A"], pr["b"]
+    n = A.shape[1]
+    lp = linprog(np.ones(2 * n), A_eq=np.hstack([A, -A]), b_eq=b, bounds=(0, None), method="highs",
+                 options={"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10})
+    x_lp = lp.x[:n] - lp.x[n:]
+    x, _, _, st = oracle.amp(A, b, tol=1e-12, max_iter=1000)
+    assert st["converged"] == 1
+    assert np.linalg.norm(x - x_lp) <= 1e-7 * np.linalg.norm(x_lp)
+
+
+def test_amp_diverges_on_the_cross_and_bouquet_dictionary():
+    """§VI-B: AMP assumes a Gaussian dictionary and does not converge on the
+    face model; on B = [A I] of the cross-and-bouquet model its iterate grows
+    until it is no longer finite (converged = -1), while on a Gaussian
+    dictionary of the same shape it converges."""
+    p = synthetic.cab_problem(256, 8, 12, 2, corrupt=0.2, seed=23)
+    B = np.hstack([p["A"], np.eye(256)])
+    for j in range(2):
+        _, _, _, st = oracle.amp(B, p["B"][:, j], tol=1e-10, max_iter=5000)
+        assert st["converged"] == -1, st
+    pr = synthetic.p1_instance(256, B.shape[1], 12, seed=2)
+    _, _, _, st = oracle.amp(pr["A"], pr["b"], tol=1e-10, max_iter=5000)
+    assert st["converged"] == 1, st
+
+
+def test_amp_is_equivariant():
+    """AMP commutes with the symmetries of P1: scaling b by 2 scales x, z and
+    tau by 2 exactly (the default tau_0 of reading R18 scales with b), and a
+    permutation of the columns of A permutes x (up to the order of the
+    sums)."""
+    pr = synthetic.p1_instance(120, 300, 15, seed=9)
+    A, b = pr["A"], pr["b"]
+    x, z, tau, st = oracle.amp(A, b, tol=1e-6, max_iter=40)
+    x2, z2, tau2, st2 = oracle.amp(A, 2.0 * b, tol=1e-6, max_iter=40)
+    assert np.array_equal(x2, 2.0 * x) and np.array_equal(z2, 2.0 * z) and tau2 == 2.0 * tau
+    assert st2["iters"] == st["iters"]
+    perm = np.random.default_rng(4).permutation(A.shape[1])
+    xp, _, _, _ = oracle.amp(A[:, perm], b, tol=1e-6, max_iter=40)
+    assert np.allclose(xp, x[perm], rtol=0, atol=1e-9 * np.abs(x).max())
