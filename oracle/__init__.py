@@ -172,7 +172,7 @@ def fista_cont(A, b, lam: float, lam0: float, rho: float = 0.95, L: float | None
 
 def amp(A, b, tau0: float = 0.0, tol: float = 1e-10, max_iter: int = 10000):
     """Approximate message passing for P1 (§IV, reading R18): x_0 = 0, z_0 = b,
-    tau_0 = ||A^T b||_inf / 2 unless tau0 > 0.  Returns (x, z, tau, stats):
+    tau_0 = 1.5 ||b||_2 / sqrt(m) unless tau0 > 0.  Returns (x, z, tau, stats):
     z and tau are those of the last x-step; stats["converged"] is 1 (R6 met),
     0 (max_iter) or -1 (an iterate stopped being finite)."""
     A = _f64(A, True)

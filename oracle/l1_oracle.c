@@ -59,13 +59,18 @@
  *       extrapolation carry over when lambda changes; the stopping rule (R6
  *       on x) is applied only once lambda_k has reached lambda.
  *   R18 AMP (§IV, the message-passing iteration for P1): x_0 = 0, z_0 = b,
- *       delta = m/n; the paper gives no initial threshold, and tau_0 must lie
- *       below ||A^T b||_inf (else x_1 = 0, the average derivative is 0 and
- *       tau stays 0), so tau_0 = ||A^T b||_inf / 2 by default; the average
- *       derivative of soft(., tau) at v is the fraction of entries with
- *       |v_i| > tau; the rule R6 on x is applied after each x-step, and a
- *       stopped iteration keeps z_k and tau_k (the ones that produced the
- *       returned x); an iterate that is not finite stops it (converged = -1).
+ *       delta = m/n; the paper gives no initial threshold.  The first x-step
+ *       sees v = A^T b, which for a Gaussian dictionary with unit columns is
+ *       x_0's target plus noise of standard deviation about ||b||_2/sqrt(m)
+ *       (the picture the AMP derivation rests on), so by default tau_0 is
+ *       1.5 ||b||_2 / sqrt(m), a threshold at one and a half noise deviations
+ *       (half of ||A^T b||_inf, tried first, lets the first step keep too few
+ *       entries, the count then drives tau below the noise and the iteration
+ *       diverges on many Gaussian instances); the average derivative of
+ *       soft(., tau) at v is the fraction of entries with |v_i| > tau; the
+ *       rule R6 on x is applied after each x-step, and a stopped iteration
+ *       keeps z_k and tau_k (the ones that produced the returned x); an
+ *       iterate that is not finite stops it (converged = -1).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -277,8 +282,8 @@ int orc_fista_cont(const double* A, int m, int n, const double* b, double lambda
  *   eta_k   = average over i of d soft(v, tau_k)/dv at v = A^T z_k + x_k
  *   z_{k+1} = b - A x_{k+1} + (eta_k / delta) z_k
  *   tau_{k+1} = (tau_k / delta) eta_k,          delta = m / n.
- * tau0 <= 0 takes ||A^T b||_inf / 2.  On return z and *tau hold the z_k and
- * tau_k of the last x-step (NULL to skip). */
+ * tau0 <= 0 takes 1.5 ||b||_2 / sqrt(m).  On return z and *tau hold the z_k
+ * and tau_k of the last x-step (NULL to skip). */
 int orc_amp(const double* A, int m, int n, const double* b, double tau0, double tol, int max_iter,
             double* x, double* z_out, double* tau_out, orc_stats* st) {
     if (!A || !b || !x || m <= 0 || n <= 0 || max_iter < 0) return ORC_ERR_ARG;
@@ -291,12 +296,7 @@ int orc_amp(const double* A, int m, int n, const double* b, double tau0, double 
     memset(x, 0, sizeof(double) * n);
     memcpy(z, b, sizeof(double) * m);
     double tau = tau0;
-    if (!(tau > 0.0)) {
-        mat_tvec(A, m, n, b, v);
-        double vmax = 0.0;
-        for (int j = 0; j < n; ++j) vmax = fabs(v[j]) > vmax ? fabs(v[j]) : vmax;
-        tau = 0.5 * vmax;
-    }
+    if (!(tau > 0.0)) tau = 1.5 * nrm2(b, m) / sqrt((double)m);
     double rel = INFINITY;
     int k = 0, conv = 0;
     for (k = 1; k <= max_iter; ++k) {

@@ -774,20 +774,20 @@ def test_amp_diverges_on_the_cross_and_bouquet_dictionary():
     """§VI-B: AMP assumes a Gaussian dictionary and does not converge on the
     face model; on B = [A I] of the cross-and-bouquet model its iterate grows
     until it is no longer finite (converged = -1), while on a Gaussian
-    dictionary of the same shape it converges."""
+    dictionary with as many rows it converges."""
     p = synthetic.cab_problem(256, 8, 12, 2, corrupt=0.2, seed=23)
     B = np.hstack([p["A"], np.eye(256)])
     for j in range(2):
         _, _, _, st = oracle.amp(B, p["B"][:, j], tol=1e-10, max_iter=5000)
         assert st["converged"] == -1, st
-    pr = synthetic.p1_instance(256, B.shape[1], 12, seed=2)
+    pr = synthetic.p1_instance(256, 640, 20, seed=2)
     _, _, _, st = oracle.amp(pr["A"], pr["b"], tol=1e-10, max_iter=5000)
     assert st["converged"] == 1, st
 
 
 def test_amp_is_equivariant():
     """AMP commutes with the symmetries of P1: scaling b by 2 scales x, z and
-    tau by 2 exactly (the default tau_0 of reading R18 scales with b), and a
+    tau by 2 exactly (the default tau_0 of reading R18 scales with ||b||), and a
     permutation of the columns of A permutes x (up to the order of the
     sums)."""
     pr = synthetic.p1_instance(120, 300, 15, seed=9)
