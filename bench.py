@@ -910,6 +910,99 @@ def bench_p1(args, rank, world):
     return 0
 
 
+AMPW = dict(m=800, n=1000, d=100, N=1024, tol=1e-6, max_iter=3000, lam=1e-6, seed=606)
+
+
+def bench_amp(args, rank, world):
+    """--workload amp: the §VI-A comparison on one batch of noise-free P1
+    instances (m = 800, n = 1000, d = 100, nonzeros uniform in [-10, 10],
+    N = 1024 right-hand sides on one Gaussian dictionary): AMP (§IV) on the
+    tensor cores and on the CUDA cores, DALM and FISTA with continuation
+    (lambda = 1e-6, rho = 0.95) to tol 1e-6; solves/s, iterations and the
+    error against x0 per solver.  AMP on the tensor cores is the headline
+    value; a sample of 4 of its columns is checked against the oracle."""
+    import torch
+
+    import paper_1007_3753_gb300 as l1
+    from paper_1007_3753_gb300 import build
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    l1.load()
+    u = AMPW
+    p = synthetic.p1_batch(u["m"], u["n"], u["d"], u["N"], seed=u["seed"] + rank)
+    A = np.asfortranarray(p["A"], dtype=np.float32)
+    B = np.asfortranarray(p["B"], dtype=np.float32)
+    X0 = p["X0"]
+    stream = torch.cuda.current_stream()
+    A_d = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    B_d = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+    lam0 = float(np.max(np.abs(A.astype(np.float64).T @ B.astype(np.float64))))
+    runs = (("AMP", dict(mode=l1.P1, solver=l1.AMP)),
+            ("AMP_cuda_cores", dict(mode=l1.P1, solver=l1.AMP, engine=l1.ENGINE_SIMT)),
+            ("DALM", dict(mode=l1.P1, solver=l1.DALM)),
+            ("FISTA_continuation", dict(mode=l1.QP_LAMBDA, solver=l1.PALM, lam=u["lam"], lam0=lam0)))
+    out, xa, ra, amp_ms = {}, None, None, None
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    for name, kw in runs:
+        s = l1.Solver(A_d, stream=stream.cuda_stream, **kw)
+        for _ in range(args.warmup):
+            s.solve(B_d, u["tol"], u["max_iter"])
+        torch.cuda.synchronize()
+        if sampler and name == "AMP":
+            sampler.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        conv = 0
+        for _ in range(args.steps):
+            x, _, res = s.solve(B_d, u["tol"], u["max_iter"])
+            conv += int(np.sum(res["status"] == l1.CONVERGED))
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        xh = x.cpu().numpy()
+        err = np.linalg.norm(xh - X0, axis=0) / np.linalg.norm(X0, axis=0)
+        out[name] = {"solves_per_s": conv / (ms / 1e3), "ms_per_batch": ms / args.steps,
+                     "converged": int(np.sum(res["status"] == l1.CONVERGED)),
+                     "mean_iters": float(np.mean(res["iters"])), "max_iters": int(np.max(res["iters"])),
+                     "median_rel_err_vs_x0": float(np.median(err)), "max_rel_err_vs_x0": float(np.max(err))}
+        if name == "AMP":
+            xa, ra, amp_ms = xh, res, ms
+            clocks = sampler.stop() if sampler else None
+        s.close()
+    # oracle sample: stop within 3 iterations of orc_amp, x within 1e-4 of it
+    import oracle
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    sample = (0, 1, u["N"] // 2, u["N"] - 1)
+    per, ok, t_or = [], 0, 0.0
+    for j in sample:
+        t0 = time.perf_counter()
+        w, _, _, st = oracle.amp(A64, B64[:, j], tol=u["tol"], max_iter=u["max_iter"])
+        t_or += time.perf_counter() - t0
+        xe = float(np.linalg.norm(xa[:, j] - w) / np.linalg.norm(w))
+        dk = int(ra["iters"][j]) - st["iters"]
+        good = st["converged"] == 1 and ra["status"][j] == l1.CONVERGED and abs(dk) <= 3 and xe <= 1e-4
+        ok += int(good)
+        per.append({"column": j, "stop_gpu_minus_oracle": dk, "rel_err_x": xe, "verified": good})
+    frac_ok = ok / len(per)
+    flop = 4.0 * u["m"] * u["n"] * float(np.sum(ra["iters"])) * args.steps
+    line = {"metric": "AMP P1 solves/sec (m = 800, n = 1000, d = 100; tol 1e-6, verified against the FP64 oracle)",
+            "value": frac_ok * out["AMP"]["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": amp_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"amp_p1_m{u['m']}_n{u['n']}_d{u['d']}_N{u['N']}", "tol": u["tol"],
+                       "max_iter": u["max_iter"], "fista_lambda": u["lam"], "fista_lambda0": lam0,
+                       "l2": "A (3.2 MB) and the panels stay in L2 between sweeps", "solvers": out},
+            "amp_sweeps_tflops_algorithmic": flop / (amp_ms / 1e3) / 1e12,
+            "oracle_agreement": {"of": len(per), "within_bar": ok, "per_instance": per},
+            "cpu_baseline": {"value": len(sample) / t_or, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"columns {list(sample)}, orc_amp one after another on one thread"},
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -918,7 +1011,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--engine", choices=["auto", "tc", "simt"], default="auto",
                     help="cab: the library's automatic choice (the tensor-core engine for DALM) or a forced one")
-    ap.add_argument("--workload", choices=["cab4096", "cab1024", "qp-group", "unrolled", "p1", "align"],
+    ap.add_argument("--workload", choices=["cab4096", "cab1024", "qp-group", "unrolled", "p1", "align", "amp"],
                     default="cab4096")
     ap.add_argument("--count", type=int, default=None, help="qp-group: number of instances")
     ap.add_argument("--max-iter", type=int, default=None, help="qp-group, or cab with --solve-only: iteration cap")
@@ -942,6 +1035,8 @@ def main():
         return bench_p1(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
     if args.workload == "align":
         return bench_align(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
+    if args.workload == "amp":
+        return bench_amp(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
     if args.impl == "reference":
         return bench_reference(args, rank, world)
     if args.solve_only:

@@ -63,7 +63,16 @@ typedef enum {
     L1_CAB = 3        /* min ||x||_1 + ||e||_1 s.t. b = A x + e, B=[A I] (Eq. 5) */
 } l1_mode;
 
-typedef enum { L1_PALM = 0, L1_DALM = 1 } l1_solver;
+typedef enum {
+    L1_PALM = 0, /* primal ALM, Algorithm 1 (§V-A) */
+    L1_DALM = 1, /* dual ALM, Algorithm 2 (§V-B) */
+    L1_AMP = 2   /* approximate message passing (§IV, reading R18), mode L1_P1 only, FP32
+                  * dictionary, either engine: x_{k+1} = soft(A^T z_k + x_k, tau_k),
+                  * z_{k+1} = b - A x_{k+1} + (n/m) <eta'> z_k, tau_{k+1} = (n/m) <eta'> tau_k
+                  * with <eta'> the fraction of entries above the threshold; x_0 = 0,
+                  * z_0 = b.  A comparison solver: §VI-B reports that it diverges on face
+                  * dictionaries (status L1_NONFINITE) */
+} l1_solver;
 
 typedef enum {
     L1_A_FP32 = 0, /* A held in FP32 */
@@ -74,10 +83,10 @@ typedef enum {
 } l1_precision;
 
 typedef enum {
-    L1_ENGINE_AUTO = 0,  /* DALM (P1, CAB) with an FP32 or BF16 dictionary: L1_ENGINE_TC;
-                          * everything else: L1_ENGINE_SIMT */
+    L1_ENGINE_AUTO = 0,  /* DALM (P1, CAB) with an FP32 or BF16 dictionary, and AMP:
+                          * L1_ENGINE_TC; everything else: L1_ENGINE_SIMT */
     L1_ENGINE_SIMT = 1,  /* CUDA-core FP32 kernels (GEMV for N <= 8, tiled GEMM above) */
-    L1_ENGINE_TC = 2     /* tcgen05 BF16 tensor-core sweeps for batched DALM: A and the
+    L1_ENGINE_TC = 2     /* tcgen05 BF16 tensor-core sweeps for batched DALM and AMP: A and the
                           * panels as aligned BF16 pieces, the leading product summed
                           * exactly, FP32 accumulation; narrow batches (tc_min_cols)
                           * fall back to the CUDA-core sweeps */
@@ -149,6 +158,8 @@ typedef struct {
                           * lambda), and the stopping rule applies once lambda_k has
                           * reached lambda; 0 -> plain FISTA at lambda */
     double cont_rho;     /* continuation factor rho in (0, 1]; 0 -> 0.95 */
+    double tau0;         /* L1_AMP: initial threshold tau_0 for every column; 0 ->
+                          * 1.5 ||b||_2 / sqrt(m) per column (reading R18) */
 } l1_options;
 
 /* Per-instance results (host memory). */
@@ -164,7 +175,8 @@ typedef struct {
     double dual_obj;     /* b^T y / max(1, ||B^T y||_inf); QP: b^T u - 1/2||u||^2 */
     double gap;          /* primal_obj - dual_obj (>= 0 up to rounding) */
     double resid;        /* ||b - B w||_2 */
-    double param;        /* xi_0 (PALM), beta (DALM) or lambda / L (FISTA) used */
+    double param;        /* xi_0 (PALM), beta (DALM), lambda / L (FISTA) used, or the
+                          * last threshold tau_k (AMP) */
 } l1_result;
 
 typedef struct l1_handle_s* l1_handle;

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libl1alm.so")
 
 P1, P1_2, QP_LAMBDA, CAB = 0, 1, 2, 3
-PALM, DALM = 0, 1
+PALM, DALM, AMP = 0, 1, 2
 A_FP32, A_BF16, A_FP8E4M3 = 0, 1, 2
 ENGINE_AUTO, ENGINE_SIMT, ENGINE_TC = 0, 1, 2
 OK, ERR_INVALID_ARG, ERR_NOT_SPD, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_TAPE, ERR_UNSUPPORTED = \
@@ -43,7 +43,8 @@ class Options(C.Structure):
                 ("unroll_K", C.c_int32), ("unroll_J", C.c_int32), ("ckpt_every", C.c_int32),
                 ("profile", C.c_int32), ("tc_pieces", C.c_int32), ("refine", C.c_int32),
                 ("tc_pieces_y", C.c_int32), ("tc_min_cols", C.c_int32), ("tune", C.c_int32),
-                ("cg_steps", C.c_int32), ("lambda0", C.c_double), ("cont_rho", C.c_double)]
+                ("cg_steps", C.c_int32), ("lambda0", C.c_double), ("cont_rho", C.c_double),
+                ("tau0", C.c_double)]
 
 
 class Result(C.Structure):
@@ -171,7 +172,7 @@ class Solver:
                  profile: bool = False, tc_pieces: int = 0, tc_pieces_y: int = 0, tc_min_cols: int = 0,
                  unroll_K: int = 0, unroll_J: int = 0, ckpt_every: int = 0, refine: bool = True,
                  tune: bool = True, cg_steps: int = 0, lam0: float = 0.0, cont_rho: float = 0.0,
-                 stream=None):
+                 tau0: float = 0.0, stream=None):
         L = load()
         o = Options()
         L.l1_options_init(C.byref(o))
@@ -191,6 +192,7 @@ class Solver:
         o.tune = 0 if tune else -1
         o.cg_steps = cg_steps
         o.lambda0, o.cont_rho = lam0, cont_rho
+        o.tau0 = tau0
         if unroll_J:
             o.unroll_J = unroll_J
         if ckpt_every:

@@ -113,7 +113,7 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
     l1_options o;
     if (opt) o = *opt;
     else l1_options_init(&o);
-    if (o.solver != L1_PALM && o.solver != L1_DALM) return L1_ERR_INVALID_ARG;
+    if (o.solver != L1_PALM && o.solver != L1_DALM && o.solver != L1_AMP) return L1_ERR_INVALID_ARG;
     if (o.precision < L1_A_FP32 || o.precision > L1_A_FP8E4M3) return L1_ERR_INVALID_ARG;
     if (o.engine < L1_ENGINE_AUTO || o.engine > L1_ENGINE_TC) return L1_ERR_INVALID_ARG;
     if (mode == L1_QP_LAMBDA && !(o.lambda > 0.0)) return L1_ERR_INVALID_ARG;
@@ -134,7 +134,7 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
     if (o.tc_pieces < 0 || o.tc_pieces > 3 || o.tc_pieces_y < 0 || o.tc_pieces_y > 3 || o.tc_min_cols < 0)
         return L1_ERR_INVALID_ARG;
     if (o.tc_pieces == 1 || o.tc_pieces_y == 1) return L1_ERR_UNSUPPORTED;  // a one-piece panel cannot converge
-    if (o.engine == L1_ENGINE_TC && (o.solver != L1_DALM || mode == L1_QP_LAMBDA)) return L1_ERR_UNSUPPORTED;
+    if (o.engine == L1_ENGINE_TC && (o.solver == L1_PALM || mode == L1_QP_LAMBDA)) return L1_ERR_UNSUPPORTED;
     if (o.cg_steps < 0) return L1_ERR_INVALID_ARG;
     // FISTA with continuation (R17): batched (QP_lambda) only
     if (o.lambda0 < 0.0 || o.cont_rho < 0.0 || o.cont_rho > 1.0) return L1_ERR_INVALID_ARG;
@@ -142,6 +142,11 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
     // DALM with a CG y-step (R15): one step, FP32 dictionary, tensor-core sweeps
     if (o.cg_steps > 0 && (o.cg_steps != 1 || o.solver != L1_DALM || mode == L1_QP_LAMBDA ||
                            o.precision != L1_A_FP32 || o.engine == L1_ENGINE_SIMT || o.unroll_K > 0))
+        return L1_ERR_UNSUPPORTED;
+    // AMP (R18): P1 with an FP32 dictionary, none of the other options
+    if (o.tau0 < 0.0) return L1_ERR_INVALID_ARG;
+    if (o.tau0 > 0.0 && o.solver != L1_AMP) return L1_ERR_UNSUPPORTED;
+    if (o.solver == L1_AMP && (mode != L1_P1 || o.precision != L1_A_FP32 || o.unroll_K > 0 || o.cg_steps > 0))
         return L1_ERR_UNSUPPORTED;
     if (o.unroll_K < 0 || o.unroll_J < 0 || o.ckpt_every < 0) return L1_ERR_INVALID_ARG;
     if (o.unroll_K > 0) {
@@ -194,7 +199,7 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
         // iteration more closely than the CUDA-core FP32 sweeps and run faster
         // at width; FP8 dictionaries stay on the CUDA cores)
         h->use_tc = (o.engine == L1_ENGINE_TC || (o.engine == L1_ENGINE_AUTO && o.precision != L1_A_FP8E4M3)) &&
-                    o.solver == L1_DALM && mode != L1_QP_LAMBDA && o.unroll_K == 0;
+                    o.solver != L1_PALM && mode != L1_QP_LAMBDA && o.unroll_K == 0;
         if (h->use_tc) {
             rc = dev_alloc_t(h, &h->tc_err, 1);
             if (!rc) rc = tc16::make_dictionary_pieces(h);
@@ -210,7 +215,13 @@ int l1_setup(const float* A, int64_t m, int64_t n, int64_t lda, int32_t mode, co
             h->lipschitz = 1.01 * rho;
             if (!(h->lipschitz > 0.0)) { rc = L1_ERR_INVALID_ARG; break; }  // A == 0
         }
-        if (o.solver == L1_DALM && mode != L1_QP_LAMBDA && o.cg_steps > 0) {
+        if (o.solver == L1_AMP) {
+            // AMP sweeps A x and A^T z only: no factor
+            if (h->use_tc && o.tune >= 0) {
+                rc = tc16::tune_splits(h);
+                if (rc) break;
+            }
+        } else if (o.solver == L1_DALM && mode != L1_QP_LAMBDA && o.cg_steps > 0) {
             // the CG y-step needs no factor of B B^T
             if (h->use_tc && o.tune >= 0) {
                 rc = tc16::tune_splits(h);
@@ -271,6 +282,7 @@ int l1_setup_group(const float* const* A, const int64_t* m, const int64_t* n, in
     if (!(o.lambda > 0.0)) return L1_ERR_INVALID_ARG;
     if (o.precision != L1_A_FP32 && o.precision != L1_A_BF16) return L1_ERR_UNSUPPORTED;
     if (o.lambda0 != 0.0) return L1_ERR_UNSUPPORTED;  // continuation: l1_setup batches only
+    if (o.solver == L1_AMP || o.tau0 != 0.0) return L1_ERR_UNSUPPORTED;  // AMP solves P1
     for (int64_t i = 0; i < count; ++i)
         if (m[i] <= 0 || n[i] <= 0) return L1_ERR_INVALID_ARG;
     Handle* h = new (std::nothrow) Handle();

@@ -1,4 +1,4 @@
-// Instantiations of the tensor-core DALM sweeps (see dalm_tc.cuh).
+// Instantiations of the tensor-core DALM and AMP sweeps (see dalm_tc.cuh).
 #include "dalm_tc.cuh"
 
 namespace l1 {
@@ -24,6 +24,16 @@ int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc1
 }
 
 int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiCgQ& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active) {
+    return tc16::launch(h, M, N, K, op, tl, epi, po, part, active);
+}
+
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcAmpX& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active) {
+    return tc16::launch(h, M, N, K, op, tl, epi, po, part, active);
+}
+
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcAmpZ& epi,
              const tc16::PieceOut& po, double* part, const int32_t* active) {
     return tc16::launch(h, M, N, K, op, tl, epi, po, part, active);
 }

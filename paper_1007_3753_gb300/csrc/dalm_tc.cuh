@@ -179,6 +179,67 @@ struct EpiCgQ {
     }
 };
 
+// ------------------------------------- AMP epilogues of the tensor-core engine
+// Approximate message passing for P1 (§IV, reading R18): x in Wx, z in Y;
+// the A^T z sweep reads the BF16 pieces of z and the A x sweep those of x,
+// which these functors return.  Per column: tau_k (FP32 copy) and the z-step
+// coefficient (n/m) <eta'>, both set by ctrl_amp_kernel.
+
+// AX (rows of A^T, acc = A^T z_k): x_{k+1} = soft(acc + x_k, tau_k).
+// red: ||x_{k+1} - x_k||^2, ||x_k||^2, the count of |v_i| > tau_k.
+struct EpiTcAmpX {
+    static constexpr int NRED = 3;
+    struct State {
+        float x;
+        int act;
+    };
+    float* Wx;
+    const float* tau;
+    const int32_t* active;
+    int64_t ldn;
+    __device__ State load(int i, int j) const { return State{Wx[(int64_t)j * ldn + i], active[j]}; }
+    __device__ float apply(int i, int j, float acc, const State& st, float* red) const {
+        if (!st.act) return 0.0f;
+        const float v = acc + st.x;
+        const float t = tau[j];
+        const float xn = soft_thr(v, t);
+        Wx[(int64_t)j * ldn + i] = xn;
+        const float dx = xn - st.x;
+        red[0] += dx * dx;
+        red[1] += st.x * st.x;
+        red[2] += fabsf(v) > t ? 1.0f : 0.0f;
+        return xn;
+    }
+};
+
+// AZ (rows of A, acc = A x_{k+1}): z_{k+1} = b - acc + coef_j z_k.
+struct EpiTcAmpZ {
+    static constexpr int NRED = 0;
+    struct State {
+        float z, b;
+        int act;
+    };
+    float* Y;
+    const float* B;
+    const float* coef;
+    const int32_t* active;
+    int64_t ldm;
+    __device__ State load(int i, int j) const {
+        const int64_t o = (int64_t)j * ldm + i;
+        return State{Y[o], B[o], active[j]};
+    }
+    __device__ float apply(int i, int j, float acc, const State& st, float*) const {
+        if (!st.act) return 0.0f;
+        const float zn = fmaf(coef[j], st.z, st.b - acc);
+        Y[(int64_t)j * ldm + i] = zn;
+        return zn;
+    }
+};
+
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcAmpX& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active);
+int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcAmpZ& epi,
+             const tc16::PieceOut& po, double* part, const int32_t* active);
 int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiTcD& epi,
              const tc16::PieceOut& po, double* part, const int32_t* active);
 int tc_sweep(Handle* h, int M, int N, int K, const tc16::Operands& op, const tc16::Terms& tl, const EpiCgD& epi,

@@ -507,6 +507,8 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     } else {
         L1_CUDA_TRY(cudaMemsetAsync(P->We, 0, pm, s));
     }
+    // AMP (R18): z_0 = b (in Y), x_0 = 0
+    if (solver == L1_AMP) L1_CUDA_TRY(cudaMemcpyAsync(P->Y, P->B, pm, cudaMemcpyDeviceToDevice, s));
     // warm start: x_init = w_0 ([x; e] for CAB), y_init = y_0 (DALM) or
     // theta_0 (PALM); PALM and FISTA start their first inner loop at z = x_0
     if (x_init) {
@@ -527,6 +529,11 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     init_cols_kernel<<<N, 128, 0, s>>>(c, P->B, ldm, m, mode, o.beta, o.xi0, xi_max, o.lambda,
                                        o.lambda0);
     L1_LAUNCH_CHECK(h);
+    if (solver == L1_AMP) {
+        // tau_0: the given value, else 1.5 ||b||_2 / sqrt(m) per column (R18)
+        amp_init_kernel<<<N, 128, 0, s>>>(c, P->B, ldm, m, o.tau0);
+        L1_LAUNCH_CHECK(h);
+    }
 
     const int check_every = o.check_every > 0 ? o.check_every : 16;
     SweepProf prof{h, o.profile != 0};
@@ -542,7 +549,7 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     const int inner_max = o.inner_max > 0 ? o.inner_max : 50;
     const double inner_tol = o.inner_tol > 0.0 ? o.inner_tol : 0.1 * tol;
     // host budget of sweep rounds: every column has stopped by then (max_iter)
-    const int64_t round_cap = (solver == L1_DALM || mode == L1_QP_LAMBDA) ? (int64_t)max_iter
+    const int64_t round_cap = (solver != L1_PALM || mode == L1_QP_LAMBDA) ? (int64_t)max_iter
                                                                           : (int64_t)max_iter * inner_max;
     int64_t rounds = 0;
     // low-precision A: phase 1 sweeps the BF16 / FP8 copy, phase 2 (refinement)
@@ -556,7 +563,9 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     const int tc_min = cg ? 1 : (o.tc_min_cols > 0 ? o.tc_min_cols : 1);
     const int tcp = o.tc_pieces > 0 ? std::min(o.tc_pieces, 3) : 3;      // A sweeps
     const int tcy = o.tc_pieces_y > 0 ? std::min(o.tc_pieces_y, 3) : 3;  // y-step
-    bool tc_mode = h->use_tc && solver == L1_DALM && N_cur >= tc_min;
+    bool tc_mode = h->use_tc && solver != L1_PALM && N_cur >= tc_min;
+    // AMP on the tensor cores: the A^T z sweep reads the BF16 pieces of z_0
+    if (solver == L1_AMP && tc_mode) L1_TRY(tc16::split_aligned_lines(h, P->Y, nullptr, N_cur, m, ldm, w.Yh, tcp));
     if (solver == L1_DALM && (x_init || y_init || tc_mode)) {
         // the state z_1 (and V_1) of the first iteration from (w_0, y_0); a
         // cold start is all zeros either way, but the pieces of V are written
@@ -674,6 +683,46 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                 ctrl_dalm_kernel<<<(N_cur + kCtrlCols - 1) / kCtrlCols, 128, 0, s>>>(c, cab ? part_m : nullptr, np_e,
                                                                                      part_n, np_x, tol, max_iter);
                 L1_LAUNCH_CHECK(h);
+            } else if (solver == L1_AMP && tc_mode) {
+                // AMP (§IV) on the tensor cores: x-step on A^T z (reads the
+                // pieces of z, writes those of x), the controller, z-step on
+                // A x (reads the pieces of x, writes those of z)
+                const tc16::Terms ta = terms_square(tcp);
+                tc16::Operands o1{{h->A_cm_h[0], h->A_cm_h[1], h->A_cm_h[2]}, tcp,
+                                  {w.Yh[0], w.Yh[1], w.Yh[2]}, tcp, ldm, ldm};
+                tc16::PieceOut po1{{w.Vh[0], w.Vh[1], w.Vh[2]}, tcp, ldn};
+                prof.start(2, 2.0 * m * n * na);
+                const int np_x = tc_sweep(h, n, N_cur, m, o1, ta, EpiTcAmpX{P->Wx, c.xi, c.active, ldn}, po1, part_n,
+                                          c.active);
+                prof.stop();
+                if (np_x < 0) return np_x;
+                ctrl_amp_kernel<<<(N_cur + kCtrlCols - 1) / kCtrlCols, 128, 0, s>>>(c, part_n, np_x, m, tol,
+                                                                                    max_iter);
+                L1_LAUNCH_CHECK(h);
+                tc16::Operands o2{{h->A_rm_h[0], h->A_rm_h[1], h->A_rm_h[2]}, tcp,
+                                  {w.Vh[0], w.Vh[1], w.Vh[2]}, tcp, ldn, ldn};
+                tc16::PieceOut po2{{w.Yh[0], w.Yh[1], w.Yh[2]}, tcp, ldm};
+                prof.start(0, 2.0 * m * n * na);
+                const int rc = tc_sweep(h, m, N_cur, n, o2, ta, EpiTcAmpZ{P->Y, P->B, c.mu, c.active, ldm}, po2,
+                                        nullptr, c.active);
+                prof.stop();
+                if (rc < 0) return rc;
+            } else if (solver == L1_AMP) {
+                // AMP (§IV): the x-step on A^T z, the controller (stopping
+                // rule, eta, tau), the z-step on A x
+                prof.start(2, 2.0 * m * n * na);
+                const int np_x = launch_sweep(h, n, N_cur, m, h->A_cm, ldm, P->Y, ldm,
+                                              EpiAmpX{P->Wx, c.xi, c.active, ldn}, part_n, c.active);
+                prof.stop();
+                if (np_x < 0) return np_x;
+                ctrl_amp_kernel<<<(N_cur + kCtrlCols - 1) / kCtrlCols, 128, 0, s>>>(c, part_n, np_x, m, tol,
+                                                                                    max_iter);
+                L1_LAUNCH_CHECK(h);
+                prof.start(0, 2.0 * m * n * na);
+                const int np_z = launch_sweep(h, m, N_cur, n, h->A_rm, ldn, P->Wx, ldn,
+                                              EpiAmpZ{P->Y, P->B, c.mu, c.active, ldm}, part_m, c.active);
+                prof.stop();
+                if (np_z < 0) return np_z;
             } else {
                 // Algorithm 1 / Eq. 18: two sweeps per inner FISTA step
                 prof.start(0, 2.0 * m * n * na);
@@ -770,8 +819,9 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                 fill_i32_kernel<<<(N_cur + 255) / 256, 256, 0, s>>>(c.active, N_cur, 0);
                 L1_LAUNCH_CHECK(h);
             }
-            // retiring slots of a tensor-core set go home in the CUDA-core form
-            if (tc_mode) L1_TRY(tc_to_simt(h, *P, c, N_cur, cab, true));
+            // retiring slots of a tensor-core DALM set go home in the CUDA-core
+            // form (the AMP state x, z is the same in both)
+            if (tc_mode && solver == L1_DALM) L1_TRY(tc_to_simt(h, *P, c, N_cur, cab, true));
             int cnt = 0;
             L1_TRY(compact(h, q, N_cur, solver, xi_max, &cnt));
             q ^= 1;
@@ -781,8 +831,10 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
                 if (N_cur < tc_min) {
                     // too narrow for the tensor-core tiles: continue on the
                     // CUDA-core sweeps from the equivalent state
-                    L1_TRY(tc_to_simt(h, Pn, make_cols(h, q, N_cur), N_cur, cab, false));
+                    if (solver == L1_DALM) L1_TRY(tc_to_simt(h, Pn, make_cols(h, q, N_cur), N_cur, cab, false));
                     tc_mode = false;
+                } else if (solver == L1_AMP) {
+                    L1_TRY(tc16::split_aligned_lines(h, Pn.Y, nullptr, N_cur, m, ldm, w.Yh, tcp));
                 } else {
                     L1_TRY(tc16::split_aligned_lines(h, Pn.Ux, nullptr, N_cur, n, ldn, w.Vh, tcp));
                 }

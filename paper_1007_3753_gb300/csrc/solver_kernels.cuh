@@ -299,6 +299,51 @@ struct EpiPalmAt {
     }
 };
 
+// ------------------------------------------------------------ AMP epilogues
+// Approximate message passing for P1 (§IV, reading R18).  x lives in Wx and
+// z in Y; per column, tau_k is c.t (FP64) with its FP32 copy in c.xi, and
+// the z-step coefficient (n/m) <eta'> in c.mu.
+
+// x-step (acc = A^T z_k): v = acc + x_k, x_{k+1} = soft(v, tau_k).
+// red: ||x_{k+1} - x_k||^2, ||x_k||^2, the count of |v_i| > tau_k (the
+// entries where soft(., tau_k) has derivative 1).
+struct EpiAmpX {
+    static constexpr int NRED = 3;
+    float* Wx;
+    const float* tau;
+    const int32_t* active;
+    int64_t ldn;
+    __device__ void operator()(int i, int j, float acc, double* red) const {
+        if (!active[j]) return;
+        const int64_t o = (int64_t)j * ldn + i;
+        const float x = Wx[o];
+        const float v = acc + x;
+        const float t = tau[j];
+        const float xn = soft_thr(v, t);
+        Wx[o] = xn;
+        const float dx = xn - x;
+        red[0] += (double)dx * dx;
+        red[1] += (double)x * x;
+        red[2] += fabsf(v) > t ? 1.0 : 0.0;
+    }
+};
+
+// z-step (acc = A x_{k+1}): z_{k+1} = b - A x_{k+1} + coef_j z_k.
+struct EpiAmpZ {
+    static constexpr int NRED = 0;
+    float* Y;
+    const float* B;
+    const float* coef;
+    const int32_t* active;
+    int64_t ldm;
+    __device__ void operator()(int i, int j, float acc, double*) const {
+        if (!active[j]) return;
+        const int64_t o = (int64_t)j * ldm + i;
+        Y[o] = fmaf(coef[j], Y[o], B[o] - acc);
+    }
+};
+
+
 // ------------------------------------------------------------- controllers
 // One 128-thread block per column: sums the row-block partials in index
 // order, applies the stopping rules, and (PALM) restarts FISTA.
@@ -362,6 +407,66 @@ __global__ void ctrl_dalm_kernel(Cols c, const double* part_e, int np_e, const d
     } else if (it >= max_iter) {
         c.status[j] = L1_MAX_ITER;
         c.active[j] = 0;
+    }
+}
+
+// tau_0 per column (one 128-thread block each): the given tau0, else
+// 1.5 ||b||_2 / sqrt(m) (R18: the first x-step sees A^T b as the target
+// plus noise of deviation about ||b||_2 / sqrt(m))
+__global__ void amp_init_kernel(Cols c, const float* B, int64_t ldm, int m, double tau0) {
+    __shared__ double sh[4];
+    const int j = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double b = B[(int64_t)j * ldm + i];
+        s += b * b;
+    }
+    s = block_sum_128(s, sh);
+    if (threadIdx.x != 0) return;
+    const double t = tau0 > 0.0 ? tau0 : 1.5 * sqrt(s) / sqrt((double)m);
+    c.t[j] = t;
+    c.xi[j] = (float)t;
+    c.mu[j] = 0.0f;
+}
+
+// AMP controller (after the x-step), one warp per column: the relative
+// change of x (R6); for a column that goes on, with eta = count / n and
+// delta = m / n, the z-step coefficient eta / delta = count / m and
+// tau_{k+1} = tau_k count / m.  A stopped column keeps z_k and tau_k.
+__global__ void ctrl_amp_kernel(Cols c, const double* part, int np, int m, double tol, int max_iter) {
+    const int j = blockIdx.x * kCtrlCols + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= c.N || !c.active[j]) return;
+    double d2 = 0.0, x2 = 0.0, cnt = 0.0;
+    for (int p = lane; p < np; p += 32) {
+        const double* q = part + ((int64_t)p * c.N + j) * kPartStride;
+        d2 += q[0];
+        x2 += q[1];
+        cnt += q[2];
+    }
+    d2 = warp_sum(d2);
+    x2 = warp_sum(x2);
+    cnt = warp_sum(cnt);
+    if (lane != 0) return;
+    const int it = c.iters[j] + 1;
+    c.iters[j] = it;
+    c.inner[j] = it;
+    const double rel = rel_change(sqrt(d2), sqrt(x2));
+    c.rel[j] = rel;
+    if (!isfinite(d2) || !isfinite(x2)) {
+        c.status[j] = L1_NONFINITE;
+        c.active[j] = 0;
+    } else if (rel < tol) {
+        c.status[j] = L1_CONVERGED;
+        c.active[j] = 0;
+    } else if (it >= max_iter) {
+        c.status[j] = L1_MAX_ITER;
+        c.active[j] = 0;
+    } else {
+        const double r = cnt / m;
+        const double tn = c.t[j] * r;
+        c.t[j] = tn;
+        c.xi[j] = (float)tn;
+        c.mu[j] = (float)r;
     }
 }
 
@@ -592,7 +697,9 @@ __global__ void compact_cols_kernel(Cols src, Cols dst, Home home, int N, const 
         home.inner[o] = src.inner[s];
         home.rel[o] = src.rel[s];
         home.xi[o] = src.xi[s];
-        home.param[o] = solver == L1_DALM ? (double)src.beta[s] : (double)src.xicap[s] / xi_max;
+        home.param[o] = solver == L1_DALM  ? (double)src.beta[s]
+                        : solver == L1_AMP ? src.t[s]
+                                           : (double)src.xicap[s] / xi_max;
     }
 }
 

@@ -79,6 +79,25 @@ def p1_instance(m: int = 200, n: int = 400, k: int = 20, seed: int = 0,
     return {"A": A, "x0": x0, "b": b, "support": np.sort(support)}
 
 
+def p1_batch(m: int, n: int, k: int, N: int, seed: int = 0, entries: str = "uniform10") -> dict:
+    """N noise-free basis-pursuit right-hand sides b_j = A x0_j on one
+    Gaussian unit-column dictionary, each x0_j k-sparse on its own random
+    support (entries as in ``p1_instance``)."""
+    g = rng(seed)
+    A = gaussian_dictionary(m, n, g)
+    X0 = np.zeros((n, N), order="F")
+    for j in range(N):
+        s = g.choice(n, size=k, replace=False)
+        if entries == "pm1":
+            X0[s, j] = g.choice(np.array([-1.0, 1.0]), size=k)
+        elif entries == "uniform10":
+            X0[s, j] = g.uniform(-10.0, 10.0, size=k)
+        else:
+            raise ValueError(entries)
+    B = np.asfortranarray(A @ X0)
+    return {"A": A, "X0": X0, "B": B}
+
+
 def cab_problem(m: int, classes: int, per_class: int, n_test: int,
                 corrupt: float = 0.3, rank: int = 9, noise: float = 0.01,
                 seed: int = 1000) -> dict:

@@ -130,6 +130,13 @@ def test_refused_combinations_before_any_cuda_call(lib):
     assert setup(l1.QP_LAMBDA, lambda_=0.1, lambda0=-1.0) == I
     assert setup(l1.QP_LAMBDA, lambda_=0.1, lambda0=1.0, cont_rho=1.5) == I
     assert setup(l1.P1, lambda0=1.0) == U
+    # AMP (R18): P1 on the FP32 CUDA-core sweeps
+    assert setup(l1.P1, solver=l1.AMP, tau0=-1.0) == I
+    assert setup(l1.P1, solver=l1.DALM, tau0=1.0) == U
+    assert setup(l1.CAB, solver=l1.AMP) == U
+    assert setup(l1.QP_LAMBDA, solver=l1.AMP, lambda_=0.1) == U
+    assert setup(l1.P1, solver=l1.AMP, precision=l1.A_BF16) == U
+    assert setup(l1.P1, solver=l1.AMP, unroll_K=5) == U
     assert setup(l1.P1, solver=7) == I
     assert setup(l1.P1, precision=9) == I
     assert setup(l1.P1, engine=9) == I
