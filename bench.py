@@ -364,9 +364,11 @@ def bench_ours(args, rank, world):
     # that times every sweep with CUDA events (the roofline), the others on
     # the one without events
     s = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec,
-                  tune=not args.no_tune, stream=stream.cuda_stream)
+                  tune=not args.no_tune, tc_pieces=args.pieces, tc_pieces_y=args.pieces_y,
+                  stream=stream.cuda_stream)
     sp = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec,
-                   tune=not args.no_tune, profile=True, stream=stream.cuda_stream)
+                   tune=not args.no_tune, tc_pieces=args.pieces, tc_pieces_y=args.pieces_y, profile=True,
+                   stream=stream.cuda_stream)
     setup_ms = s.info()["setup_ms"]
     tc = l1.load() is not None and engine != l1.ENGINE_SIMT and args.precision != "fp8"
     tol, max_iter = cfg["tol"], cfg["max_iter"]
@@ -543,6 +545,7 @@ def bench_ours(args, rank, world):
             "data": "synthetic",
             "config": config_dict(cfg, {"parallelism": f"replicas{world}" if world > 1 else "single",
                                         "engine": "tc" if tc else "simt", "precision": args.precision,
+                                        "tc_pieces": [args.pieces or 3, args.pieces_y or 3] if tc else None,
                                         "setup_ms": setup_ms, "mean_iters": statistics.mean(iters),
                                         "tiles_autotuned": [[e["M"], e["K"], e["tiles"], e["ksplit"], e["deferred"],
                                                              e["bn"]] for e in s.tuning()],
@@ -1024,6 +1027,12 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="cab: the fixed tile rule instead of the setup-time autotuner (for runs under a profiler, "
                          "whose per-launch overhead distorts the tuner's timings)")
+    ap.add_argument("--pieces", type=int, default=0,
+                    help="cab, tensor cores: BF16 pieces of A and the panels in the A sweeps (2 or 3; 0: the "
+                         "library's default, 3)")
+    ap.add_argument("--pieces-y", type=int, default=0,
+                    help="cab, tensor cores: BF16 pieces of (B B^T)^-1 and d in the y-step (2 or 3; 0: the "
+                         "library's default, 3)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1062,7 +1071,7 @@ def solve_once(args):
     A_d = torch.from_numpy(np.ascontiguousarray(A.T, dtype=np.float32)).cuda().t()
     B_d = torch.from_numpy(np.ascontiguousarray(B.T, dtype=np.float32)).cuda().t()
     s = l1.Solver(A_d, mode=l1.CAB, solver=l1.DALM, class_offsets=off, engine=engine, precision=prec,
-                  tune=not args.no_tune)
+                  tune=not args.no_tune, tc_pieces=args.pieces, tc_pieces_y=args.pieces_y)
     max_iter = args.max_iter or cfg["max_iter"]
     t0 = time.perf_counter()
     _, _, res = s.solve(B_d, cfg["tol"], max_iter)
