@@ -973,6 +973,27 @@ def bench_amp(args, rank, world):
             xa, ra, amp_ms = xh, res, ms
             clocks = sampler.stop() if sampler else None
         s.close()
+    # roofline of AMP's dominant sweep: one more solve on a handle that times
+    # every sweep with CUDA events (tensor cores, three BF16 pieces)
+    sp = l1.Solver(A_d, mode=l1.P1, solver=l1.AMP, profile=True, stream=stream.cuda_stream)
+    i0 = sp.info()
+    sp.solve(B_d, u["tol"], u["max_iter"])
+    torch.cuda.synchronize()
+    i1 = sp.info()
+    sp.close()
+    kinds = {0: "A_x (z-step)", 2: "At_z (x-step)"}
+    d_ms = {k: i1["sweep_ms"][k] - i0["sweep_ms"][k] for k in kinds}
+    d_fl = {k: i1["sweep_flop"][k] - i0["sweep_flop"][k] for k in kinds}
+    d_ln = {k: i1["sweep_launches"][k] - i0["sweep_launches"][k] for k in kinds}
+    kd = max(kinds, key=lambda k: d_ms[k])
+    ach = d_fl[kd] / (d_ms[kd] / 1e3) / 1e12 if d_ms[kd] > 0 else 0.0
+    peak = measured_peaks()["bf16_tflops_sustained"]
+    roofline = {"bound": "tensor", "kernel": f"sweep {kinds[kd]} (tc16::sweep_kernel, 3 x 3 BF16 pieces)",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_note": "of measured bf16_tflops_sustained; achieved counts 2*M*K*(columns of the panel set)",
+                "executed_tflops": 6 * ach, "executed_frac": 6 * ach / peak, "launches": d_ln[kd],
+                "avg_launch_us": 1e3 * d_ms[kd] / max(1, d_ln[kd]),
+                "share_of_sweep_time": d_ms[kd] / max(1e-9, sum(d_ms.values()))}
     # oracle sample: stop within 3 iterations of orc_amp, x within 1e-4 of it
     import oracle
     A64, B64 = A.astype(np.float64), B.astype(np.float64)
@@ -996,7 +1017,7 @@ def bench_amp(args, rank, world):
             "config": {"workload": f"amp_p1_m{u['m']}_n{u['n']}_d{u['d']}_N{u['N']}", "tol": u["tol"],
                        "max_iter": u["max_iter"], "fista_lambda": u["lam"], "fista_lambda0": lam0,
                        "l2": "A (3.2 MB) and the panels stay in L2 between sweeps", "solvers": out},
-            "amp_sweeps_tflops_algorithmic": flop / (amp_ms / 1e3) / 1e12,
+            "amp_sweeps_tflops_algorithmic": flop / (amp_ms / 1e3) / 1e12, "roofline": roofline,
             "oracle_agreement": {"of": len(per), "within_bar": ok, "per_instance": per},
             "cpu_baseline": {"value": len(sample) / t_or, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": f"columns {list(sample)}, orc_amp one after another on one thread"},

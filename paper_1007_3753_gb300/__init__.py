@@ -124,11 +124,23 @@ def load() -> C.CDLL:
 
 
 def _ptr(a):
-    """Address of a torch tensor (device or host) or numpy array."""
+    """Address of a float32 torch tensor (device or host) or numpy array.
+
+    Every buffer of the C ABI holds FP32 values: another dtype would make the
+    library read or write past the end of the buffer, and a CUDA tensor on a
+    device other than the current one would be dereferenced as a peer
+    pointer, so both are refused here, before any call."""
     if a is None:
         return None
     if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float32:
+            raise TypeError(f"expected a float32 tensor, got {a.dtype}")
+        if a.is_cuda and a.device.index is not None and a.device.index != torch.cuda.current_device():
+            raise ValueError(f"tensor on cuda:{a.device.index} but cuda:{torch.cuda.current_device()} is current")
         return C.c_void_p(a.data_ptr())
+    if a.dtype != np.float32:
+        raise TypeError(f"expected a float32 array, got {a.dtype}")
     return C.c_void_p(a.ctypes.data)
 
 

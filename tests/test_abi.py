@@ -192,3 +192,20 @@ def test_product_path_has_no_cpu_fallback():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "l1_oracle" not in src, f
+
+
+def test_buffers_other_than_float32_are_refused_before_any_call(lib):
+    """Every buffer of the C ABI holds FP32: the binding refuses tensors and
+    arrays of another dtype before the call (the library would otherwise read
+    past the end of a BF16 buffer)."""
+    torch = pytest.importorskip("torch")
+    for dt in (torch.bfloat16, torch.float16, torch.float64):
+        with pytest.raises(TypeError):
+            l1.Solver(torch.zeros((8, 4), dtype=dt).t(), mode=l1.P1, solver=l1.DALM)
+        with pytest.raises(TypeError):
+            l1._ptr(torch.zeros(4, dtype=dt))
+    for dt in (np.float64, np.float16, np.int32):
+        with pytest.raises(TypeError):
+            l1._ptr(np.zeros(4, dtype=dt))
+    assert l1._ptr(np.zeros(4, dtype=np.float32)) is not None
+    assert l1._ptr(torch.zeros(4, dtype=torch.float32)) is not None
