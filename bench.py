@@ -972,6 +972,7 @@ def bench_amp(args, rank, world):
         if name == "AMP":
             xa, ra, amp_ms = xh, res, ms
             clocks = sampler.stop() if sampler else None
+            amp_tiles = [[e["M"], e["K"], e["tiles"], e["ksplit"], e["deferred"], e["bn"]] for e in s.tuning()]
         s.close()
     # roofline of AMP's dominant sweep: one more solve on a handle that times
     # every sweep with CUDA events (tensor cores, three BF16 pieces)
@@ -1016,7 +1017,8 @@ def bench_amp(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"amp_p1_m{u['m']}_n{u['n']}_d{u['d']}_N{u['N']}", "tol": u["tol"],
                        "max_iter": u["max_iter"], "fista_lambda": u["lam"], "fista_lambda0": lam0,
-                       "l2": "A (3.2 MB) and the panels stay in L2 between sweeps", "solvers": out},
+                       "l2": "A (3.2 MB) and the panels stay in L2 between sweeps", "solvers": out,
+                       "amp_tiles_autotuned": amp_tiles},
             "amp_sweeps_tflops_algorithmic": flop / (amp_ms / 1e3) / 1e12, "roofline": roofline,
             "oracle_agreement": {"of": len(per), "within_bar": ok, "per_instance": per},
             "cpu_baseline": {"value": len(sample) / t_or, "unit": "solves/s", "cores": 1, "kind": "oracle",
