@@ -76,3 +76,14 @@ def test_verify_columns_counts_only_columns_within_the_bar():
     d = bench.verify_columns(cols, x2, its2, obj, lab2, lambda j: stops[j], at, lambda j: labels[j])
     assert d["within_bar"] == 1 and not d["per_instance"][1]["verified"]
     assert d["per_instance"][2]["rel_err_x"] is None and d["labels_equal"] == 3
+
+
+def test_reference_arm_of_the_other_workloads_says_unavailable():
+    """The oracle arm is timed on the cross-and-bouquet workloads; on the
+    others --impl reference prints its one-line reason and exits 0."""
+    for w in ("qp-group", "unrolled", "p1", "align", "amp"):
+        out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", w,
+                              "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+        assert out.returncode == 0, out.stderr[-2000:]
+        d = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+        assert d["impl"] == "reference" and w in d["unavailable"]
