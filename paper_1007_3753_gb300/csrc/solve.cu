@@ -309,7 +309,7 @@ static int ensure_workspace(Handle* h, int N) {
         // the tensor-core sweeps' FP32 tile sums (split-K slices, deferred
         // epilogues): every output tile of the widest sweep at this width
         const size_t tm = (size_t)(std::max(m, n) + 127) / 128, tn = (size_t)(N + 127) / 128;
-        const size_t need = std::max((size_t)(h->sms > 0 ? h->sms : 152), tm * tn) * 128 * 128;
+        const size_t need = std::max((size_t)tc16::kSplitWaves * (h->sms > 0 ? h->sms : 152), tm * tn) * 128 * 128;
         if (need > h->tc_wk_elems) {
             dev_free(h, h->tc_wk);
             h->tc_wk = nullptr;

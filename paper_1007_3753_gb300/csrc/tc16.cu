@@ -73,8 +73,8 @@ int make_dictionary_pieces(Handle* h) {
         L1_TRY(dev_alloc_t(h, &h->A_cm_h[p], (size_t)h->ldm * n));
     }
     const int sms = h->sms > 0 ? h->sms : 152;
-    L1_TRY(dev_alloc_t(h, &h->tc_wk, (size_t)sms * 128 * 128));
-    h->tc_wk_elems = (size_t)sms * 128 * 128;
+    L1_TRY(dev_alloc_t(h, &h->tc_wk, (size_t)kSplitWaves * sms * 128 * 128));
+    h->tc_wk_elems = (size_t)kSplitWaves * sms * 128 * 128;
     // A u: K = n along the rows of A; A^T y: K = m along the columns of A
     L1_TRY(split_aligned_lines(h, h->A_rm, nullptr, m, n, h->ldn, h->A_rm_h, kMaxPieces));
     L1_TRY(split_aligned_lines(h, h->A_cm, nullptr, n, m, h->ldm, h->A_cm_h, kMaxPieces));
@@ -199,14 +199,16 @@ int tune_splits(Handle* h) {
                 const EpiTune epi{S, Mp, (int64_t)Mp * Nt};
                 const PieceOut po{{P[0], P[1], P[2]}, 3, Mp};
                 // candidates: 128-wide tiles fused, deferred, and split-K with
-                // each distinct slice count that keeps at most one CTA per SM;
+                // each distinct slice count up to four waves of one CTA per SM
+                // (a narrow batch of 32 row tiles fills 128 of 152 SMs with
+                // four slices; nine slices run 288 CTAs in two waves);
                 // 64-wide tiles deferred and split the same way
                 std::vector<Split> cands = {Split{1, 0, 128}, Split{1, 1, 128}};
                 for (int bn : {128, 64}) {
                     const int tb = tm * ((N + bn - 1) / bn);
                     if (bn == 64) cands.push_back(Split{1, 1, 64});
                     int last = 1;
-                    for (int ks = 2; ks <= std::min(16, chunks) && ks * tb <= sms; ++ks) {
+                    for (int ks = 2; ks <= std::min(16, chunks) && ks * tb <= kSplitWaves * sms; ++ks) {
                         const Split c = normalise(h, Split{ks, 1, bn}, sh.M, N, sh.K);
                         if (c.ks > 1 && c.bn == bn && c.ks != last) {
                             cands.push_back(c);

@@ -82,6 +82,9 @@ struct Split {
     int ks, defer, bn;
 };
 
+// split-K slices may fill up to this many waves of one CTA per SM
+constexpr int kSplitWaves = 4;
+
 inline Split normalise(const Handle* h, Split want, int M, int N, int K) {
     const int chunks = (K + kChunk - 1) / kChunk;
     const int bn = want.bn == 64 ? 64 : 128;
@@ -96,7 +99,8 @@ inline Split normalise(const Handle* h, Split want, int M, int N, int K) {
 
 // The autotuner's choice for (M, K) at the batch's count of 128-wide tiles
 // (tune_splits): the entry of that count, else of the nearest smaller one
-// (its slice count capped at one CTA per SM).  Without one (tuning off, or a
+// (its slice count capped so that the CTAs fill no more waves of one CTA per
+// SM than the entry's did).  Without one (tuning off, or a
 // shape it did not time): 128-wide tiles, the epilogue deferred, and enough
 // K slices to give every SM a CTA when a quarter of them has a tile.
 inline Split split_choice(const Handle* h, int M, int N, int K) {
@@ -109,7 +113,9 @@ inline Split split_choice(const Handle* h, int M, int N, int K) {
     if (near) {
         const int bn = (*near)[5];
         const int tb = tm * ((N + bn - 1) / bn);
-        return normalise(h, Split{std::min((*near)[3], std::max(1, sms / tb)), (*near)[4], bn}, M, N, K);
+        const int tb_e = (*near)[2] * (128 / bn);  // the entry's tiles of width bn
+        const int waves = std::max(1, ((*near)[3] * tb_e + sms - 1) / sms);
+        return normalise(h, Split{std::min((*near)[3], std::max(1, waves * sms / tb)), (*near)[4], bn}, M, N, K);
     }
     const int chunks = (K + kChunk - 1) / kChunk;
     if (4 * tiles > sms || chunks < 4) return normalise(h, Split{1, 1, 128}, M, N, K);

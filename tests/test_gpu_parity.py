@@ -566,7 +566,8 @@ def test_split_autotuner_records_choices_and_keeps_parity(l1):
         assert 1 <= e["ksplit"] <= 16 and e["us"] >= 0 and e["deferred"] in (0, 1) and e["bn"] in (64, 128)
         assert e["ksplit"] == 1 or e["deferred"] == 1
         assert e["bn"] == 128 or e["deferred"] == 1
-        assert e["ksplit"] * e["tiles"] * (128 // e["bn"]) <= sms or e["ksplit"] == 1
+        # split-K slices fill at most four waves of one CTA per SM
+        assert e["ksplit"] * e["tiles"] * (128 // e["bn"]) <= 4 * sms or e["ksplit"] == 1
     s0 = l1.Solver(_dev(A), mode=l1.CAB, solver=l1.DALM, engine=l1.ENGINE_TC, tc_min_cols=1, tune=False)
     assert s0.tuning() == []
     iters = 120
