@@ -246,6 +246,73 @@ def palm_align(B, b, tol: float = 1e-10, max_outer: int = 100000, xi0: float = 0
     return w, e, th, st.as_dict()
 
 
+def warp_jacobian(img, tau, rows: int, cols: int):
+    """b = y o tau and its Jacobian J = d(y o tau)/d tau (§II-B), reading R19.
+
+    tau = (a, b, tx, ty) is a similarity: canonical pixel (u, v) (column u <
+    cols, row v < rows, index v*cols + u) lies at x = a u - b v + tx,
+    y = b u + a v + ty of the query image img (H x W, img[y, x]).  y o tau is
+    the bilinear interpolant of img there, the point first clamped to
+    [0, W-1] x [0, H-1]; the cell is the one whose lower corner is
+    (min(floor(x), W-2), min(floor(y), H-2)).  Its derivative in x (in y)
+    is the interpolant's slope in that cell, and 0 where x (y) was clamped.
+    Returns (b (m,), J (m, 4)) in FP64."""
+    img = np.asarray(img, dtype=np.float64)
+    H, W = img.shape
+    a, bb, tx, ty = (float(t) for t in tau)
+    vv, uu = np.mgrid[0:rows, 0:cols].astype(np.float64)
+    u, v = uu.ravel(), vv.ravel()
+    x = a * u - bb * v + tx
+    y = bb * u + a * v + ty
+    xc = np.clip(x, 0.0, W - 1.0)
+    yc = np.clip(y, 0.0, H - 1.0)
+    x0 = np.minimum(np.floor(xc), W - 2).astype(np.int64)
+    y0 = np.minimum(np.floor(yc), H - 2).astype(np.int64)
+    fx, fy = xc - x0, yc - y0
+    p00, p01 = img[y0, x0], img[y0, x0 + 1]
+    p10, p11 = img[y0 + 1, x0], img[y0 + 1, x0 + 1]
+    val = (1.0 - fy) * ((1.0 - fx) * p00 + fx * p01) + fy * ((1.0 - fx) * p10 + fx * p11)
+    gx = np.where((x >= 0.0) & (x <= W - 1.0), (1.0 - fy) * (p01 - p00) + fy * (p11 - p10), 0.0)
+    gy = np.where((y >= 0.0) & (y <= H - 1.0), (1.0 - fx) * (p10 - p00) + fx * (p11 - p01), 0.0)
+    # dx/dtau = (u, -v, 1, 0), dy/dtau = (v, u, 0, 1)
+    J = np.stack([gx * u + gy * v, -gx * v + gy * u, gx, gy], axis=1)
+    return val, J
+
+
+def corner_shift(dtau, rows: int, cols: int) -> float:
+    """Largest displacement of the four corners of the canonical frame under
+    the linear change dtau of the similarity parameters (reading R19's step
+    size): max over corners (u, v) of |(da u - db v + dtx, db u + da v + dty)|."""
+    da, db, dtx, dty = (float(t) for t in dtau)
+    best = 0.0
+    for u, v in ((0, 0), (cols - 1, 0), (0, rows - 1), (cols - 1, rows - 1)):
+        best = max(best, float(np.hypot(da * u - db * v + dtx, db * u + da * v + dty)))
+    return best
+
+
+def align_images(A, img, tau, rows: int, cols: int, tol: float = 1e-3, max_outer: int = 5000,
+                 tau_tol: float = 0.05, max_align: int = 30):
+    """The face-alignment loop of §II-B for one query (reading R19): from
+    tau, repeat b = y o tau, J = d(y o tau)/d tau, w = [x; dtau] from the
+    convex step min ||e||_1 s.t. b = [A, -J] w + e (``palm_align``, R16, to
+    the relative change tol), tau <- tau + dtau, until the step moves no
+    corner of the canonical frame by tau_tol pixels or more (converged) or
+    max_align steps were taken.  Returns (tau, steps, converged)."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[1]
+    tau = np.array(tau, dtype=np.float64)
+    for k in range(1, max_align + 1):
+        b, J = warp_jacobian(img, tau, rows, cols)
+        w, _, _, st = palm_align(np.hstack([A, -J]), b, tol=tol, max_outer=max_outer)
+        dtau = w[n:n + 4]
+        if not np.all(np.isfinite(dtau)):
+            return tau, k, False
+        tau = tau + dtau
+        if corner_shift(dtau, rows, cols) < tau_tol:
+            return tau, k, True
+    return tau, max_align, False
+
+
 def classify(A, offsets, b, x, e=None):
     """Per-class residual argmin and SCI argmax (§II-A, Eq. 40).
 

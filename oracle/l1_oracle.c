@@ -71,6 +71,14 @@
  *       rule R6 on x is applied after each x-step, and a stopped iteration
  *       keeps z_k and tau_k (the ones that produced the returned x); an
  *       iterate that is not finite stops it (converged = -1).
+ *   R19 The image side of the alignment loop of §II-B (restated in numpy in
+ *       oracle/__init__.py): tau is a similarity (a, b, tx, ty) mapping the
+ *       canonical pixel (u, v) to (a u - b v + tx, b u + a v + ty); y o tau is
+ *       the bilinear interpolant of the query, the point clamped to the image;
+ *       J is the interpolant's slope in its cell (0 where clamped) times the
+ *       derivative of the point in tau; no intensity normalisation; the loop
+ *       adds dtau (the last four entries of w) to tau and stops once dtau
+ *       moves no corner of the canonical frame by tau_tol pixels or more.
  */
 #include <math.h>
 #include <stdlib.h>

@@ -26,6 +26,16 @@ pixels is replaced by uniform noise):
   N(0,1) x0, b = A x0 + N(0, 0.01^2).
 * ``unrolled_instance`` -- unrolled PALM differentiation: Gaussian
   unit-column A, k-sparse N(0,1) targets, b = A x_target + N(0, 0.01^2).
+* ``p1_batch`` -- N noise-free P1 right-hand sides on one Gaussian dictionary.
+* ``alignment_images`` -- the alignment experiment of §VI-C on synthetic
+  faces (Multi-PIE is not available): per task a smooth "face" (a sum of
+  Gaussian blobs on the 40 x 30 canonical frame), n = 7 training images under
+  different smooth illuminations, and an 80 x 60 query image showing the
+  face under a random mix of those illuminations at a known similarity
+  transformation, with a block of 10 % of the face area replaced by noise
+  (the paper's occluding baboon block); the starting transformation is the
+  true one moved by 4 pixels along x (translation) or rotated by 15 degrees
+  about the frame centre (rotation).
 """
 from __future__ import annotations
 
@@ -39,6 +49,8 @@ __all__ = [
     "qp_group_sizes",
     "qp_instance",
     "unrolled_instance",
+    "p1_batch",
+    "alignment_images",
 ]
 
 
@@ -174,3 +186,73 @@ def unrolled_instance(m: int = 1024, n: int = 2048, N: int = 256, k: int = 50,
         X[s, j] = g.standard_normal(k)
     B = np.asfortranarray(A @ X + noise * g.standard_normal((m, N)))
     return {"A": A, "X_target": X, "B": B}
+
+
+def _similarity_inverse(tau, x, y):
+    """Canonical coordinates (u, v) that the similarity tau = (a, b, tx, ty)
+    maps to image coordinates (x, y) = (a u - b v + tx, b u + a v + ty)."""
+    a, b, tx, ty = tau
+    d = a * a + b * b
+    xx, yy = x - tx, y - ty
+    return (a * xx + b * yy) / d, (-b * xx + a * yy) / d
+
+
+def alignment_images(count: int, kind: str = "translation", rows: int = 40, cols: int = 30, n_train: int = 7,
+                     H: int = 80, W: int = 60, occlusion: float = 0.1, seed: int = 7000) -> dict:
+    """``count`` alignment tasks (§II-B, §VI-C), each with its own subject.
+
+    Returns A (count, rows*cols, n_train; pixel (v, u) of the canonical frame
+    at index v*cols + u), img (count, H, W; row-major, pixel (y, x) at
+    [y, x]), tau_true and tau_init (count, 4) as (a, b, tx, ty): canonical
+    pixel (u, v) lies at (a u - b v + tx, b u + a v + ty) in the query image.
+    The true transformation is the identity similarity centring the frame
+    in the query image.  ``kind``: "translation" (4 pixels along x) or
+    "rotation" (15 degrees about the frame centre)."""
+    g = rng(seed)
+    m = rows * cols
+    vv, uu = np.mgrid[0:rows, 0:cols].astype(np.float64)
+    u, v = uu.ravel(), vv.ravel()
+    yq, xq = np.mgrid[0:H, 0:W].astype(np.float64)
+    A = np.zeros((count, m, n_train))
+    img = np.zeros((count, H, W))
+    t_true = np.array([1.0, 0.0, (W - cols) / 2.0, (H - rows) / 2.0])
+    tau_true = np.tile(t_true, (count, 1))
+    tau_init = np.zeros((count, 4))
+    side = int(round(np.sqrt(occlusion * m)))
+    for k in range(count):
+        nb = 24
+        bu, bv = g.uniform(2, cols - 2, nb), g.uniform(2, rows - 2, nb)
+        bs, ba = g.uniform(1.8, 4.0, nb), g.uniform(0.3, 1.0, nb)
+        lin = g.uniform(-0.6, 0.6, (n_train, 2))
+        lu, lv = g.uniform(0, cols, n_train), g.uniform(0, rows, n_train)
+        ls, la = g.uniform(10, 20, n_train), g.uniform(0.3, 1.0, n_train)
+
+        def face(pu, pv):
+            out = 0.2 + np.zeros(np.broadcast(pu, pv).shape)
+            for j in range(nb):
+                out = out + ba[j] * np.exp(-((pu - bu[j]) ** 2 + (pv - bv[j]) ** 2) / (2 * bs[j] ** 2))
+            return out
+
+        def light(l, pu, pv):
+            return (1 + lin[l, 0] * (pu - cols / 2) / cols + lin[l, 1] * (pv - rows / 2) / rows
+                    + la[l] * np.exp(-((pu - lu[l]) ** 2 + (pv - lv[l]) ** 2) / (2 * ls[l] ** 2)))
+
+        fa = face(u, v)
+        for l in range(n_train):
+            A[k, :, l] = fa * light(l, u, v)
+        c = g.dirichlet(np.ones(n_train))
+        pu, pv = _similarity_inverse(t_true, xq, yq)
+        img[k] = face(pu, pv) * sum(c[l] * light(l, pu, pv) for l in range(n_train))
+        oy = int(g.integers(int(t_true[3]), int(t_true[3]) + rows - side))
+        ox = int(g.integers(int(t_true[2]), int(t_true[2]) + cols - side))
+        img[k, oy:oy + side, ox:ox + side] = g.uniform(0.0, 1.0, (side, side))
+        if kind == "translation":
+            tau_init[k] = t_true + np.array([0.0, 0.0, 4.0, 0.0])
+        elif kind == "rotation":
+            th = np.deg2rad(15.0)
+            a, b = np.cos(th), np.sin(th)
+            cu, cv = (cols - 1) / 2.0, (rows - 1) / 2.0
+            tau_init[k] = [a, b, t_true[2] + cu - (a * cu - b * cv), t_true[3] + cv - (b * cu + a * cv)]
+        else:
+            raise ValueError(kind)
+    return {"A": A, "img": img, "tau_true": tau_true, "tau_init": tau_init, "rows": rows, "cols": cols}
