@@ -913,6 +913,101 @@ def bench_p1(args, rank, world):
     return 0
 
 
+ALIGNIMG = dict(per_kind=512, rows=40, cols=30, tol=1e-3, max_outer=5000, tau_tol=0.05, max_align=30, seed=7500)
+
+
+def bench_align_images(args, rank, world):
+    """--workload align-images: the face-alignment loop of §II-B / §VI-C
+    (l1_align_images) on synthetic faces, 512 tasks perturbed by 4 pixels of
+    translation and 512 by 15 degrees of rotation, each with 7 training
+    images of 40 x 30 and an 80 x 60 query with 10 % occluded; one step
+    aligns all 1024 tasks.  A task succeeds when its final similarity moves
+    no corner of the frame by a pixel or more from the true one; value =
+    successful tasks per second.  The oracle loop on 4 tasks is the CPU
+    baseline and checks the GPU's answers."""
+    import torch
+
+    import paper_1007_3753_gb300 as l1
+    from paper_1007_3753_gb300 import build
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    l1.load()
+    u = ALIGNIMG
+    rows, cols = u["rows"], u["cols"]
+    ds = [synthetic.alignment_images(u["per_kind"], kind, rows=rows, cols=cols, seed=u["seed"] + 10 * rank + i)
+          for i, kind in enumerate(("translation", "rotation"))]
+    img = torch.from_numpy(np.ascontiguousarray(np.concatenate([d["img"] for d in ds]), dtype=np.float32)).cuda()
+    A = torch.from_numpy(np.ascontiguousarray(np.concatenate([np.transpose(d["A"], (0, 2, 1)) for d in ds]),
+                                              dtype=np.float32)).cuda()
+    t_init = np.concatenate([d["tau_init"] for d in ds])
+    t_true = np.concatenate([d["tau_true"] for d in ds])
+    count = len(t_init)
+    t0_d = torch.from_numpy(t_init).cuda()
+    tau = torch.empty_like(t0_d)
+    stream = torch.cuda.current_stream()
+    kw = dict(tol=u["tol"], max_outer=u["max_outer"], tau_tol=u["tau_tol"], max_align=u["max_align"])
+    for _ in range(args.warmup):
+        tau.copy_(t0_d)
+        l1.align_images(img, A, tau, rows, cols, **kw)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms_all = []
+    for _ in range(args.steps):
+        tau.copy_(t0_d)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        res = l1.align_images(img, A, tau, rows, cols, **kw)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms_all.append(ev0.elapsed_time(ev1))
+    clocks = sampler.stop() if sampler else None
+    tg = tau.cpu().numpy()
+
+    def shift(dt):
+        return max(float(np.hypot(dt[0] * cu - dt[1] * cv + dt[2], dt[1] * cu + dt[0] * cv + dt[3]))
+                   for cu, cv in ((0, 0), (cols - 1, 0), (0, rows - 1), (cols - 1, rows - 1)))
+
+    ok = np.array([shift(tg[k] - t_true[k]) < 1.0 for k in range(count)])
+    half = u["per_kind"]
+    total_ms = sum(ms_all)
+    # the oracle on 4 tasks, one host thread: timing and a check of the GPU's answers
+    import oracle
+    per, agree, t_or = [], 0, 0.0
+    sample = (0, 1, half, half + 1)
+    Ah = np.concatenate([d["A"] for d in ds]).astype(np.float32).astype(np.float64)
+    imh = np.concatenate([d["img"] for d in ds]).astype(np.float32).astype(np.float64)
+    for k in sample:
+        t0 = time.perf_counter()
+        to, steps, conv = oracle.align_images(Ah[k], imh[k], t_init[k], rows, cols, **kw)
+        t_or += time.perf_counter() - t0
+        dk = shift(tg[k] - to)
+        same = (shift(to - t_true[k]) < 1.0) == bool(ok[k]) and (dk <= 0.1 or not ok[k])
+        agree += int(same)
+        per.append({"task": k, "gpu_minus_oracle_px": dk, "steps_gpu": int(res["iters"][k]), "steps_oracle": steps,
+                    "agrees": same})
+    line = {"metric": "face-alignment tasks/sec (success: final similarity within 1 px of the truth)",
+            "value": float(ok.sum()) * args.steps / (total_ms / 1e3), "unit": "tasks/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 pixels and products, f64 coordinates and w-step", "data": "synthetic",
+            "config": {"workload": f"align_images_{rows}x{cols}_n7_count{count}", "tol": u["tol"],
+                       "tau_tol_px": u["tau_tol"], "max_align": u["max_align"],
+                       "success_translation": float(ok[:half].mean()), "success_rotation": float(ok[half:].mean()),
+                       "mean_steps_translation": float(res["iters"][:half].mean()),
+                       "mean_steps_rotation": float(res["iters"][half:].mean()),
+                       "status_counts": {str(s_): int((res["status"] == s_).sum()) for s_ in (0, 1, 2)}},
+            "oracle_agreement": {"of": len(per), "agree": agree, "per_task": per},
+            "cpu_baseline": {"value": len(sample) / t_or, "unit": "tasks/s", "cores": 1, "kind": "oracle",
+                             "sample": f"tasks {list(sample)}, oracle.align_images one after another on one thread"},
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 AMPW = dict(m=800, n=1000, d=100, N=1024, tol=1e-6, max_iter=3000, lam=1e-6, seed=606)
 
 
@@ -1037,7 +1132,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--engine", choices=["auto", "tc", "simt"], default="auto",
                     help="cab: the library's automatic choice (the tensor-core engine for DALM) or a forced one")
-    ap.add_argument("--workload", choices=["cab4096", "cab1024", "qp-group", "unrolled", "p1", "align", "amp"],
+    ap.add_argument("--workload", choices=["cab4096", "cab1024", "qp-group", "unrolled", "p1", "align", "amp",
+                                           "align-images"],
                     default="cab4096")
     ap.add_argument("--count", type=int, default=None, help="qp-group: number of instances")
     ap.add_argument("--max-iter", type=int, default=None, help="qp-group, or cab with --solve-only: iteration cap")
@@ -1069,6 +1165,8 @@ def main():
         return bench_align(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
     if args.workload == "amp":
         return bench_amp(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
+    if args.workload == "align-images":
+        return bench_align_images(args, rank, world) if args.impl == "ours" else unavailable_reference(args)
     if args.impl == "reference":
         return bench_reference(args, rank, world)
     if args.solve_only:

@@ -369,7 +369,8 @@ L1_API int l1_solve_plain(l1_handle h, const float* b, double tol, int32_t max_i
  * are tiled.  For each sweep shape and timed batch width it tried 128-wide
  * output tiles with the epilogue fused into the sweep or deferred to a second
  * kernel that reads the tile's FP32 sums, split-K with every slice count that
- * keeps one CTA per multiprocessor, and 64-wide tiles (deferred, split-K),
+ * fills at most four waves of one CTA per multiprocessor, and 64-wide tiles
+ * (deferred, split-K),
  * and kept the fastest (the simplest within 2 %).  Writes up to cap entries
  * of 7 int32 each to out (host): the sweep's output rows M, its depth K, the
  * batch width as a count of 128 x 128 output tiles, the number of K slices, 1
@@ -407,6 +408,57 @@ L1_API int l1_tuning(l1_handle h, int32_t* out, int32_t cap);
 L1_API int l1_align_batch(const float* B, int64_t m, int64_t p, int64_t ldB, int64_t strideB, const float* b,
                           int64_t strideb, int64_t count, double tol, int32_t max_outer, double xi0, void* stream,
                           float* w, float* e, l1_result* res);
+
+/*
+ * l1_align_warp -- the image side of the alignment loop (§II-B, reading R19):
+ * for each task k < count, the warped query b_k = y_k o tau_k and the negated
+ * Jacobian -d(y_k o tau_k)/d tau_k on the rows x cols canonical frame.
+ * tau_k = (a, b, tx, ty) is a similarity: canonical pixel (u, v) (column u,
+ * row v, vector index v cols + u) lies at x = a u - b v + tx, y = b u + a v
+ * + ty of the query image.  y o tau is the bilinear interpolant of the query
+ * at that point clamped to [0, W-1] x [0, H-1] (cell with lower corner
+ * (min(floor x, W-2), min(floor y, H-2))); its derivative in x (in y) is the
+ * interpolant's slope in that cell, 0 where x (y) was clamped.  Coordinates
+ * and weights FP64, pixels and outputs FP32.
+ *   img     device, query k at img + k img_stride, row-major H x W (H, W >= 2)
+ *   tau     device, 4 doubles per task
+ *   B       device, task k at B + k strideB, column-major with leading
+ *           dimension ldB >= rows cols; columns col0 .. col0 + 3 receive -J
+ *           (strideB >= ldB (col0 + 4))
+ *   b       device, task k at b + k strideb (strideb >= rows cols)
+ *   active  device, count flags, or NULL: tasks with a zero flag are skipped
+ * Enqueued on stream, no synchronisation.  count <= 65535.
+ * Errors: L1_ERR_INVALID_ARG (null pointers, sizes, strides), L1_ERR_CUDA.
+ */
+L1_API int l1_align_warp(const float* img, int64_t H, int64_t W, int64_t img_stride, const double* tau,
+                         int64_t count, int32_t rows, int32_t cols, int32_t col0, void* stream, float* B, int64_t ldB,
+                         int64_t strideB, float* b, int64_t strideb, const int32_t* active);
+
+/*
+ * l1_align_images -- the face-alignment loop of §II-B (reading R19) for count
+ * tasks: task k aligns its query image to its subject's n training images
+ * by repeating b = y o tau, J = d(y o tau)/d tau (l1_align_warp), the convex
+ * step min ||e||_1 s.t. b = [A_k, -J] w + e (l1_align_batch to the relative
+ * change tol, at most max_outer iterations), tau <- tau + dtau with dtau the
+ * last four entries of w, until dtau moves no corner of the canonical frame
+ * by tau_tol pixels or more (status L1_CONVERGED), after max_align steps
+ * (L1_MAX_ITER), or when a step is not finite or its B^T B is singular
+ * (L1_NONFINITE).
+ *   img     device, query k at img + k img_stride, row-major H x W
+ *   A       device, task k's training images at A + k A_stride, column-major
+ *           (rows cols) x n, pixel (u, v) at row v cols + u; n + 4 <= 32 and
+ *           n + 4 < rows cols
+ *   tau     device, 4 doubles per task: the starting transformation in, the
+ *           final one out
+ *   iters, status  host, count each: alignment steps taken, final status
+ * Allocates its work buffers (count ((n + 6) rows cols + n + 4) floats) and
+ * synchronises the stream once per step.
+ * Errors: L1_ERR_INVALID_ARG, L1_ERR_OOM, L1_ERR_CUDA.
+ */
+L1_API int l1_align_images(const float* img, int64_t H, int64_t W, int64_t img_stride, const float* A, int32_t n,
+                           int64_t A_stride, int32_t rows, int32_t cols, int64_t count, double* tau, double tol,
+                           int32_t max_outer, double tau_tol, int32_t max_align, void* stream, int32_t* iters,
+                           int32_t* status);
 
 /* Set the stream later calls enqueue on. */
 L1_API int l1_set_stream(l1_handle h, void* stream);

@@ -30,7 +30,8 @@ CONVERGED, MAX_ITER, NONFINITE = 0, 1, 2
 # every symbol include/l1alm.h declares
 EXPORTS = ("l1_options_init", "l1_setup", "l1_setup_group", "l1_group_load", "l1_solve_batch",
            "l1_backward", "l1_set_stream", "l1_get_info", "l1_destroy", "l1_status_string",
-           "l1_last_error", "l1_lipschitz_static", "l1_solve_plain", "l1_tuning", "l1_align_batch")
+           "l1_last_error", "l1_lipschitz_static", "l1_solve_plain", "l1_tuning", "l1_align_batch",
+           "l1_align_warp", "l1_align_images")
 
 
 class Options(C.Structure):
@@ -119,6 +120,11 @@ def load() -> C.CDLL:
     L.l1_align_batch.argtypes = [vp, i64, i64, i64, i64, vp, i64, i64, dbl, i32, dbl, vp, vp, vp,
                                  C.POINTER(Result)]
     L.l1_align_batch.restype = C.c_int
+    L.l1_align_warp.argtypes = [vp, i64, i64, i64, vp, i64, i32, i32, i32, vp, vp, i64, i64, vp, i64, vp]
+    L.l1_align_warp.restype = C.c_int
+    L.l1_align_images.argtypes = [vp, i64, i64, i64, vp, i32, i64, i32, i32, i64, vp, dbl, i32, dbl, i32, vp,
+                                  C.POINTER(i32), C.POINTER(i32)]
+    L.l1_align_images.restype = C.c_int
     _lib = L
     return L
 
@@ -479,6 +485,66 @@ def align_batch(B, b, tol: float = 1e-6, max_outer: int = 10000, xi0: float = 0.
     _check(load().l1_align_batch(_ptr(B), m, p, m, m * p, _ptr(b), m, count, float(tol), int(max_outer),
                                  float(xi0), st, _ptr(w), _ptr(e), res), "l1_align_batch")
     return w, e, results_to_dict(res)
+
+
+def _cuda_tensor(t, dtype, name: str, dims: int):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda:
+        raise TypeError(f"{name} must be a {dtype} CUDA tensor")
+    if t.dim() != dims:
+        raise ValueError(f"{name} must have {dims} dimensions")
+    if t.device.index is not None and t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index} but cuda:{torch.cuda.current_device()} is current")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def align_warp(img, tau, rows: int, cols: int, stream=None):
+    """l1_align_warp: b = y o tau and J = d(y o tau)/d tau on the rows x cols
+    canonical frame (§II-B, reading R19) for each task.
+
+    ``img``: CUDA float32 (count, H, W); ``tau``: CUDA float64 (count, 4) as
+    (a, b, tx, ty).  Returns (b of shape (count, rows*cols), J of shape
+    (count, 4, rows*cols))."""
+    import torch
+    pi = _cuda_tensor(img, torch.float32, "align_warp: img", 3)
+    pt = _cuda_tensor(tau, torch.float64, "align_warp: tau", 2)
+    count, H, W = img.shape
+    if tau.shape != (count, 4):
+        raise ValueError("align_warp: tau must be (count, 4)")
+    m = rows * cols
+    B = torch.empty((count, 4, m), dtype=torch.float32, device=img.device)
+    b = torch.empty((count, m), dtype=torch.float32, device=img.device)
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    _check(load().l1_align_warp(pi, H, W, H * W, pt, count, rows, cols, 0, st, _ptr(B), m, 4 * m, _ptr(b), m, None),
+           "l1_align_warp")
+    return b, -B
+
+
+def align_images(img, A, tau, rows: int, cols: int, tol: float = 1e-3, max_outer: int = 5000,
+                 tau_tol: float = 0.05, max_align: int = 30, stream=None):
+    """l1_align_images: the face-alignment loop of §II-B (reading R19).
+
+    ``img``: CUDA float32 (count, H, W) query images; ``A``: CUDA float32
+    (count, n, rows*cols), task k's training image j at A[k, j]; ``tau``:
+    CUDA float64 (count, 4), the starting transformations, overwritten with
+    the final ones.  Returns {"iters", "status"} as numpy arrays."""
+    import torch
+    pi = _cuda_tensor(img, torch.float32, "align_images: img", 3)
+    pa = _cuda_tensor(A, torch.float32, "align_images: A", 3)
+    pt = _cuda_tensor(tau, torch.float64, "align_images: tau", 2)
+    count, H, W = img.shape
+    if A.shape[0] != count or A.shape[2] != rows * cols or tau.shape != (count, 4):
+        raise ValueError("align_images: A must be (count, n, rows*cols) and tau (count, 4)")
+    n = A.shape[1]
+    iters = (C.c_int32 * count)()
+    status = (C.c_int32 * count)()
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    _check(load().l1_align_images(pi, H, W, H * W, pa, n, n * rows * cols, rows, cols, count, pt, float(tol),
+                                  int(max_outer), float(tau_tol), int(max_align), st, iters, status),
+           "l1_align_images")
+    return {"iters": np.array(iters[:], dtype=np.int32), "status": np.array(status[:], dtype=np.int32)}
 
 
 def _colmajor(t):

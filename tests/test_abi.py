@@ -209,3 +209,36 @@ def test_buffers_other_than_float32_are_refused_before_any_call(lib):
             l1._ptr(np.zeros(4, dtype=dt))
     assert l1._ptr(np.zeros(4, dtype=np.float32)) is not None
     assert l1._ptr(torch.zeros(4, dtype=torch.float32)) is not None
+
+
+def test_alignment_loop_argument_checks(lib):
+    """l1_align_warp and l1_align_images refuse null pointers, too-small
+    images, strides and sizes before any CUDA call (host pointers serve as
+    stand-ins: nothing is dereferenced)."""
+    I = l1.ERR_INVALID_ARG
+    img = np.zeros(16, dtype=np.float32)
+    tau = np.zeros(4, dtype=np.float64)
+    B = np.zeros(64, dtype=np.float32)
+    b = np.zeros(16, dtype=np.float32)
+    pi, pt, pB, pb = img.ctypes.data, tau.ctypes.data, B.ctypes.data, b.ctypes.data
+    # l1_align_warp(img, H, W, img_stride, tau, count, rows, cols, col0, stream, B, ldB, strideB, b, strideb, active)
+    assert lib.l1_align_warp(None, 4, 4, 16, pt, 1, 2, 2, 0, None, pB, 4, 16, pb, 4, None) == I
+    assert lib.l1_align_warp(pi, 1, 4, 16, pt, 1, 2, 2, 0, None, pB, 4, 16, pb, 4, None) == I   # H < 2
+    assert lib.l1_align_warp(pi, 4, 4, 15, pt, 1, 2, 2, 0, None, pB, 4, 16, pb, 4, None) == I   # img_stride
+    assert lib.l1_align_warp(pi, 4, 4, 16, pt, 0, 2, 2, 0, None, pB, 4, 16, pb, 4, None) == I   # count
+    assert lib.l1_align_warp(pi, 4, 4, 16, pt, 70000, 2, 2, 0, None, pB, 4, 16, pb, 4, None) == I
+    assert lib.l1_align_warp(pi, 4, 4, 16, pt, 1, 2, 2, 0, None, pB, 3, 16, pb, 4, None) == I   # ldB < m
+    assert lib.l1_align_warp(pi, 4, 4, 16, pt, 1, 2, 2, 1, None, pB, 4, 16, pb, 4, None) == I   # strideB
+    assert lib.l1_align_warp(pi, 4, 4, 16, pt, 1, 2, 2, 0, None, pB, 4, 16, pb, 3, None) == I   # strideb
+    it = (C.c_int32 * 1)()
+    stt = (C.c_int32 * 1)()
+    # l1_align_images(img, H, W, img_stride, A, n, A_stride, rows, cols, count, tau, tol, max_outer,
+    #                 tau_tol, max_align, stream, iters, status)
+    A = np.zeros(64, dtype=np.float32)
+    pA = A.ctypes.data
+    assert lib.l1_align_images(pi, 4, 4, 16, None, 2, 32, 4, 4, 1, pt, 1e-3, 10, 1e-2, 5, None, it, stt) == I
+    assert lib.l1_align_images(pi, 4, 4, 16, pA, 29, 16 * 29, 4, 4, 1, pt, 1e-3, 10, 1e-2, 5, None, it, stt) == I
+    assert lib.l1_align_images(pi, 4, 4, 16, pA, 2, 31, 4, 4, 1, pt, 1e-3, 10, 1e-2, 5, None, it, stt) == I
+    assert lib.l1_align_images(pi, 4, 4, 16, pA, 2, 32, 4, 4, 1, pt, -1.0, 10, 1e-2, 5, None, it, stt) == I
+    assert lib.l1_align_images(pi, 4, 4, 16, pA, 2, 32, 4, 4, 1, pt, 1e-3, 10, 1e-2, 0, None, it, stt) == I
+    assert lib.l1_align_images(pi, 4, 4, 16, pA, 2, 32, 4, 4, 1, pt, 1e-3, 10, 1e-2, 5, None, None, stt) == I

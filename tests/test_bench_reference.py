@@ -81,7 +81,7 @@ def test_verify_columns_counts_only_columns_within_the_bar():
 def test_reference_arm_of_the_other_workloads_says_unavailable():
     """The oracle arm is timed on the cross-and-bouquet workloads; on the
     others --impl reference prints its one-line reason and exits 0."""
-    for w in ("qp-group", "unrolled", "p1", "align", "amp"):
+    for w in ("qp-group", "unrolled", "p1", "align", "amp", "align-images"):
         out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", w,
                               "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300, cwd=ROOT)
         assert out.returncode == 0, out.stderr[-2000:]
