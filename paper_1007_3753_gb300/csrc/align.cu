@@ -38,9 +38,11 @@ __global__ void __launch_bounds__(kAThreads) align_kernel(const float* __restric
                                                           int64_t strideB, const float* __restrict__ b,
                                                           int64_t strideb, double tol, int max_outer, double xi0,
                                                           float* __restrict__ w_out, float* __restrict__ e_out,
-                                                          AlignOut* __restrict__ out) {
+                                                          AlignOut* __restrict__ out,
+                                                          const int32_t* __restrict__ active) {
     extern __shared__ __align__(16) unsigned char asm_raw[];
     const int k = blockIdx.x, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (active != nullptr && !active[k]) return;  // the whole CTA, before any barrier
     double* G = reinterpret_cast<double*>(asm_raw);
     double* Gi = G + kAMaxP * kAMaxP;
     double* rhs = Gi + kAMaxP * kAMaxP;
@@ -237,9 +239,26 @@ size_t align_smem_bytes(int m, int p) {
 
 using namespace l1;
 
+namespace l1 {
+
+// l1_align_batch over the problems whose flag in active (device, count
+// entries; NULL: all) is set; the others are not touched (their CTAs return
+// at once) and their res entries are zero.
+int align_batch_run(const float* B, int64_t m, int64_t p, int64_t ldB, int64_t strideB, const float* b,
+                    int64_t strideb, int64_t count, double tol, int32_t max_outer, double xi0, void* stream, float* w,
+                    float* e, l1_result* res, const int32_t* active);
+
+}  // namespace l1
+
 extern "C" L1_API int l1_align_batch(const float* B, int64_t m, int64_t p, int64_t ldB, int64_t strideB,
                                      const float* b, int64_t strideb, int64_t count, double tol, int32_t max_outer,
                                      double xi0, void* stream, float* w, float* e, l1_result* res) {
+    return align_batch_run(B, m, p, ldB, strideB, b, strideb, count, tol, max_outer, xi0, stream, w, e, res, nullptr);
+}
+
+int l1::align_batch_run(const float* B, int64_t m, int64_t p, int64_t ldB, int64_t strideB, const float* b,
+                        int64_t strideb, int64_t count, double tol, int32_t max_outer, double xi0, void* stream,
+                        float* w, float* e, l1_result* res, const int32_t* active) {
     if (!B || !b || !w || !e || !res || m <= 0 || p <= 0 || p > kAMaxP || p >= m || ldB < m ||
         strideB < ldB * p || strideb < m || count <= 0 || count > (1 << 30) || max_outer <= 0 || !(tol >= 0.0))
         return L1_ERR_INVALID_ARG;
@@ -257,13 +276,17 @@ extern "C" L1_API int l1_align_batch(const float* B, int64_t m, int64_t p, int64
     int rc = L1_OK;
     std::vector<AlignOut> hout((size_t)count);
     do {
+        if (active != nullptr && cudaMemsetAsync(dout, 0, sizeof(AlignOut) * (size_t)count, s) != cudaSuccess) {
+            rc = L1_ERR_CUDA;
+            break;
+        }
         if (cudaFuncSetAttribute(align_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess) {
             rc = L1_ERR_CUDA;
             break;
         }
         align_kernel<<<(unsigned)count, kAThreads, smem, s>>>(B, (int)m, (int)p, ldB, strideB, b, strideb, tol,
-                                                              max_outer, xi0, w, e, dout);
+                                                              max_outer, xi0, w, e, dout, active);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpyAsync(hout.data(), dout, sizeof(AlignOut) * (size_t)count, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess ||

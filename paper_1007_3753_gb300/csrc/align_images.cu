@@ -20,6 +20,12 @@
 #include "common.cuh"
 
 namespace l1 {
+
+// l1_align_batch restricted to the problems whose device flag is set (align.cu)
+int align_batch_run(const float* B, int64_t m, int64_t p, int64_t ldB, int64_t strideB, const float* b,
+                    int64_t strideb, int64_t count, double tol, int32_t max_outer, double xi0, void* stream, float* w,
+                    float* e, l1_result* res, const int32_t* active);
+
 namespace {
 
 constexpr int kWarpThreads = 256;
@@ -200,9 +206,9 @@ extern "C" L1_API int l1_align_images(const float* img, int64_t H, int64_t W, in
             rc = l1_align_warp(img, H, W, img_stride, tau, count, rows, cols, n, stream, B, ldB, strideB, b, m,
                                d_active);
             if (rc) break;
-            // every task's convex step (finished tasks keep their last B and b;
-            // their answers are ignored)
-            rc = l1_align_batch(B, m, p, ldB, strideB, b, m, count, tol, max_outer, 0.0, stream, w, e, res.data());
+            // the convex steps of the tasks still active
+            rc = align_batch_run(B, m, p, ldB, strideB, b, m, count, tol, max_outer, 0.0, stream, w, e, res.data(),
+                                 d_active);
             if (rc) break;
             for (int64_t k = 0; k < count; ++k) hstep[k] = res[k].status;
             if (cudaMemcpyAsync(d_step, hstep.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s) !=
