@@ -253,20 +253,22 @@ L1_API int l1_group_load(l1_handle h, int64_t first, int64_t k, const float* con
  * column of b (m x N, leading dimension ldb >= m), 1 <= N <= 65535.
  *   tol       stopping tolerance of the relative-change rule (§VI-C); 0 runs
  *             exactly max_iter iterations.
- *   max_iter  cap on outer iterations (PALM) or iterations (DALM, FISTA).
+ *   max_iter  cap on outer iterations (PALM) or iterations (DALM, FISTA, AMP).
  *   x         output, (n + m) x N for CAB ([x; e] per column), n x N otherwise,
  *             leading dimension ldx.
  *   y         optional (NULL) output of the dual iterate, m x N, leading
- *             dimension ldy: DALM's y, PALM's multiplier theta.
+ *             dimension ldy: DALM's y, PALM's multiplier theta, AMP's z_k
+ *             (of the last x-step; the dual_obj and gap results computed
+ *             from it do not certify AMP's answer).
  *   res       host array of N results.
  *   x_init    optional (NULL) warm start, laid out like x (leading dimension
  *             ldxi): DALM's w_1 = [x; e] (Algorithm 2 starts from w_1 = 0
  *             otherwise), PALM's x_1 and, for CAB, e_1 (Algorithm 1 takes
  *             e_1 = b otherwise; the first e-step recomputes e from x_1),
- *             FISTA's x_0 (Eq. 18).
+ *             FISTA's x_0 (Eq. 18), AMP's x_0 (0 otherwise).
  *   y_init    optional (NULL) warm start of the dual iterate, laid out like y
- *             (leading dimension ldyi): DALM's y_1, PALM's theta_1; zero
- *             otherwise.  A DALM solve resumed from the x and y another solve
+ *             (leading dimension ldyi): DALM's y_1, PALM's theta_1, AMP's z_0
+ *             (b otherwise); zero otherwise.  A DALM solve resumed from the x and y another solve
  *             returned continues that solve's iteration: its first z-step
  *             (Eq. 38) is recomputed from (w, y).
  * Each column stops on its own rule and is frozen from then on (per-instance
