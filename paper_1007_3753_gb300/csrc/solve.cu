@@ -507,7 +507,7 @@ int solve_batch(Handle* h, const float* b, int64_t ldb, int N, double tol, int m
     } else {
         L1_CUDA_TRY(cudaMemsetAsync(P->We, 0, pm, s));
     }
-    // AMP (R18): z_0 = b (in Y), x_0 = 0
+    // AMP (R18): z_0 = b (in Y) and x_0 = 0 unless y_init / x_init give them
     if (solver == L1_AMP) L1_CUDA_TRY(cudaMemcpyAsync(P->Y, P->B, pm, cudaMemcpyDeviceToDevice, s));
     // warm start: x_init = w_0 ([x; e] for CAB), y_init = y_0 (DALM) or
     // theta_0 (PALM); PALM and FISTA start their first inner loop at z = x_0
